@@ -1,0 +1,144 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle checks.
+
+This module only *describes workloads*: domain profiles, nodal right-hand
+sides and seeded noise.  It holds none of the solver's arithmetic (no FEM
+matrices, no operator, no preconditioner) and imports neither the CUDA binding
+nor the oracle, so both sides can be fed the same arrays.
+
+Workloads (all on x-normal domains {0 <= x <= 1, g1(x) <= y <= g2(x)}):
+
+* ``config_p1_65``: -Lap u + u = f on g1 = 0, g2 = 1 + 0.25 sin(2 pi x), P1,
+  65 x 65 nodes, zero Dirichlet data; f manufactured from
+  u = sin(pi x) sin(pi y / g2(x)) plus seeded N(0, sigma = 1e-3) noise.
+* ``fourier_f``: f = sum_j a_j / (1 + |m_j|^2) cos(2 pi (m_j . (x, y)) + phi_j) with
+  32 modes, a_j ~ N(0, 1), m_j uniform in {-8..8}^2 \\ {0}, phi_j ~ U[0, 2 pi).
+* ``batch_instances``: gamma ~ U[0, 10], g2 = 1 + a sin(2 pi b x) with
+  a ~ U[0, 0.3], b in {1, 2, 3}, seeded per instance.
+"""
+import math
+import numpy as np
+
+
+class Profile:
+    """g(x) = c0 + c1 x + c2 x^2 + sa sin(2 pi sf x) + ca cos(pi cf x), with g', g''."""
+
+    def __init__(self, c0=0.0, c1=0.0, c2=0.0, sa=0.0, sf=1.0, ca=0.0, cf=1.0):
+        self.c0, self.c1, self.c2 = float(c0), float(c1), float(c2)
+        self.sa, self.sf, self.ca, self.cf = float(sa), float(sf), float(ca), float(cf)
+
+    def g(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        return (self.c0 + self.c1 * x + self.c2 * x * x
+                + self.sa * np.sin(2 * np.pi * self.sf * x) + self.ca * np.cos(np.pi * self.cf * x))
+
+    def dg(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        w1, w2 = 2 * np.pi * self.sf, np.pi * self.cf
+        return (self.c1 + 2 * self.c2 * x + self.sa * w1 * np.cos(w1 * x)
+                - self.ca * w2 * np.sin(w2 * x))
+
+    def d2g(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        w1, w2 = 2 * np.pi * self.sf, np.pi * self.cf
+        return (2 * self.c2 - self.sa * w1 * w1 * np.sin(w1 * x)
+                - self.ca * w2 * w2 * np.cos(w2 * x))
+
+    def is_zero(self):
+        return self.c0 == 0 and self.c1 == 0 and self.c2 == 0 and self.sa == 0 and self.ca == 0
+
+    def __repr__(self):
+        return (f"Profile(c0={self.c0}, c1={self.c1}, c2={self.c2}, sa={self.sa}, sf={self.sf}, "
+                f"ca={self.ca}, cf={self.cf})")
+
+
+ZERO = Profile()
+SIN_TOP = Profile(c0=1.0, sa=0.25, sf=1.0)           # 1 + 0.25 sin(2 pi x)
+
+
+def nodal_xy(g1, g2, n):
+    """Physical coordinates of the n x n mapped nodes: x = s_a, y = g1(s_a) + t_b h(s_a)."""
+    s = np.arange(n, dtype=np.float64) / (n - 1)
+    t = s.copy()
+    lo, hi = g1.g(s), g2.g(s)
+    X = np.repeat(s[:, None], n, axis=1)
+    Y = lo[:, None] + t[None, :] * (hi - lo)[:, None]
+    return X, Y
+
+
+def manufactured_sin_f(g1, g2, n, gamma):
+    """Nodal f = -Lap u + gamma u for u = sin(pi s) sin(pi t), t = (y - g1(x)) / h(x).
+
+    u vanishes on the whole boundary of the domain.  Derivatives in physical
+    coordinates: t_x = -(g1' + t h')/h, t_xx = -(g1'' + 2 t_x h' + t h'')/h,
+    t_y = 1/h, t_yy = 0.
+    """
+    s = np.arange(n, dtype=np.float64) / (n - 1)
+    S = np.repeat(s[:, None], n, axis=1)
+    T = np.repeat(s[None, :], n, axis=0)
+    h = (g2.g(s) - g1.g(s))[:, None]
+    dh = (g2.dg(s) - g1.dg(s))[:, None]
+    d2h = (g2.d2g(s) - g1.d2g(s))[:, None]
+    d1, dd1 = g1.dg(s)[:, None], g1.d2g(s)[:, None]
+    tx = -(d1 + T * dh) / h
+    txx = -(dd1 + 2 * tx * dh + T * d2h) / h
+    ty = 1.0 / h
+    pi = np.pi
+    ss, cs = np.sin(pi * S), np.cos(pi * S)
+    st, ct = np.sin(pi * T), np.cos(pi * T)
+    u = ss * st
+    uxx = (-pi * pi * ss * st + 2 * pi * pi * cs * ct * tx - pi * pi * ss * st * tx * tx
+           + pi * ss * ct * txx)
+    uyy = -pi * pi * ss * st * ty * ty
+    return -(uxx + uyy) + gamma * u, u
+
+
+def fourier_f(g1, g2, n, seed, modes=32, mmax=8):
+    """Seeded sum of random Fourier modes evaluated at the physical nodes."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = rng.standard_normal(modes)
+    m = np.zeros((modes, 2), dtype=np.int64)
+    for j in range(modes):
+        while True:
+            cand = rng.integers(-mmax, mmax + 1, size=2)
+            if cand[0] != 0 or cand[1] != 0:
+                m[j] = cand
+                break
+    phi = rng.uniform(0.0, 2 * np.pi, size=modes)
+    X, Y = nodal_xy(g1, g2, n)
+    F = np.zeros((n, n))
+    for j in range(modes):
+        F += a[j] / (1.0 + float(m[j] @ m[j])) * np.cos(2 * np.pi * (m[j, 0] * X + m[j, 1] * Y) + phi[j])
+    return F
+
+
+def noise(n, seed, sigma):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return sigma * rng.standard_normal((n, n))
+
+
+def config_p1_65(seed=0):
+    """P1, 65 x 65 nodes, gamma = 1, Dirichlet; manufactured f plus N(0, 1e-3) noise."""
+    n, gamma = 65, 1.0
+    f, u = manufactured_sin_f(ZERO, SIN_TOP, n, gamma)
+    return dict(g1=ZERO, g2=SIN_TOP, k=1, n=n, gamma=gamma, bc='dirichlet',
+                F=f + noise(n, seed, 1e-3), u_exact=u)
+
+
+def metric_instance(n=2049, k=2, seed=0, gamma=1.0):
+    """gamma = 1, g2 = 1 + 0.25 sin(2 pi x), Dirichlet, seeded 32-mode Fourier f."""
+    return dict(g1=ZERO, g2=SIN_TOP, k=k, n=n, gamma=gamma, bc='dirichlet',
+                F=fourier_f(ZERO, SIN_TOP, n, seed))
+
+
+def batch_instances(B, n=2049, k=2, seed0=0):
+    """B instances at fixed (n, k): gamma ~ U[0,10], g2 = 1 + a sin(2 pi b x), f seeded."""
+    out = []
+    for i in range(B):
+        rng = np.random.Generator(np.random.PCG64(1000 + seed0 + i))
+        gamma = float(rng.uniform(0.0, 10.0))
+        a = float(rng.uniform(0.0, 0.3))
+        b = int(rng.integers(1, 4))
+        g2 = Profile(c0=1.0, sa=a, sf=b)
+        out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet',
+                        F=fourier_f(ZERO, g2, n, seed0 + i)))
+    return out
