@@ -1,0 +1,193 @@
+/*
+ * mofem.h -- C ABI of libmofem: matrix-oriented FEM (MO-FEM) and the
+ * matrix-oriented preconditioned conjugate gradient (MO-PCG) on one GB300 GPU.
+ *
+ * Method: Frittelli & Sgura, "Matrix-oriented FEM formulation for stationary
+ * and time-dependent PDEs on x-normal domains" (arXiv 2109.01173).
+ *
+ * Problem (Sec. 5, Eq. laplace_equation_xnormal):  -Lap u + gamma u = f on the
+ * x-normal domain {0 <= x <= 1, g1(x) <= y <= g2(x)}, with homogeneous Dirichlet
+ * (gamma >= 0) or Neumann (gamma > 0) boundary conditions, discretised by
+ * degree-k tensor Lagrange elements (k = 1..4) or lumped P1 (k = 0) on the
+ * curvilinear mesh mapped from the unit square (Sec. 2.2, Eq. transformation,
+ * generalised to two profiles).  The unknown is a q x q matrix U[a][b]
+ * (a = node along x, b = node along the mapped y direction), q = n - 2 for
+ * Dirichlet and q = n for Neumann (Eq. variable_dimension), n = nodes per
+ * direction.  The discrete system is the multiterm Sylvester equation
+ *     L(U) = sum_i S_i U T_i^T = B          (Sec. 5, Eq. laplace_cap-shaped-domain_sylvester)
+ * with banded 1D factors S_i, T_i (Sec. 3.2, Eq. kronecker_mass_distorted).
+ *
+ * Conventions (all entry points):
+ *  - Matrix arguments are DEVICE pointers owned by the caller, row-major, with
+ *    leading dimension `ld` (elements).  For a batched handle the instances are
+ *    stored back to back with a batch stride of `ld * rows` elements.  The
+ *    library never frees caller memory.
+ *  - The handle owns every buffer it allocates (1D tables, eigenvector
+ *    matrices, workspaces) and frees them in mofem_destroy.
+ *  - Calls are stream-ordered on `stream`.  Argument errors are returned
+ *    synchronously.  mofem_pcg_solve and mofem_imex_step synchronise `stream`
+ *    before they return (their outer refinement loop reads a status word).
+ *  - No exception crosses the ABI; a handle must not be used from two host
+ *    threads at once.
+ */
+#ifndef MOFEM_H
+#define MOFEM_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MOFEM_OK = 0,
+    MOFEM_ERR_INVALID_ARG = 1,   /* bad size, degree, profile (h <= 0), singular Neumann with gamma = 0 */
+    MOFEM_ERR_CUDA = 2,          /* a CUDA runtime / library call failed */
+    MOFEM_ERR_EIG = 3,           /* the generalized eigensolver reported failure */
+    MOFEM_ERR_NONFINITE = 4,     /* NaN or Inf in an input or a recurrence scalar */
+    MOFEM_ERR_BREAKDOWN = 5,     /* <Q, L(Q)> <= 0 in PCG */
+    MOFEM_ERR_NOT_CONVERGED = 6, /* max_iter reached; the iterate is kept */
+    MOFEM_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+    MOFEM_ERR_OOM = 8,           /* device allocation failed */
+    MOFEM_ERR_UNSUPPORTED = 9    /* valid request this build does not implement */
+} mofem_status;
+
+typedef enum { MOFEM_BC_DIRICHLET = 0, MOFEM_BC_NEUMANN = 1 } mofem_bc;
+
+/* Arithmetic of the iteration.  FP64: every step in double (preconditioner
+ * GEMMs through cuBLAS DGEMM).  MIXED_*: operator apply and vectors in FP32,
+ * preconditioner GEMMs on tcgen05 tensor cores in TF32 or BF16 with FP32
+ * accumulation, CG scalars and dot products accumulated in FP64, and FP64
+ * true-residual iterative refinement around the inner FP32 solve. */
+typedef enum { MOFEM_FP64 = 0, MOFEM_MIXED_TF32 = 1, MOFEM_MIXED_BF16 = 2 } mofem_precision;
+
+/* Second pencil of the two-term Sylvester preconditioner (see mofem_precond). */
+typedef enum { MOFEM_PENCIL_AVERAGED = 0, MOFEM_PENCIL_DOMINANT = 1 } mofem_pencil;
+
+/* Domain profile y = g(x) on [0, 1]: host callbacks for g and g', called during
+ * setup only (at the quadrature points). */
+typedef struct {
+    double (*g)(double x, void* ctx);
+    double (*dg)(double x, void* ctx);
+    void* ctx;
+} mofem_profile;
+
+typedef struct {
+    int quad_points;       /* Gauss-Legendre points per element for P_k; 0 -> k + 3 */
+    mofem_pencil pencil;   /* default MOFEM_PENCIL_AVERAGED */
+    int max_outer;         /* refinement steps of the mixed form; 0 -> 20 */
+    double inner_rtol;     /* residual reduction asked of each inner FP32 solve; 0 -> 1e-4 */
+    int flags;             /* MOFEM_FLAG_* */
+} mofem_opts;
+
+#define MOFEM_FLAG_HOST_LOOP 1   /* drive the inner iteration from the host (one graph launch
+                                    per iteration) instead of a device-side conditional loop */
+#define MOFEM_FLAG_FIXED_ITERS 2 /* run exactly max_iter inner iterations (timing runs) */
+
+typedef struct {
+    int status;            /* mofem_status of the whole (batched) solve */
+    int iterations;        /* total inner PCG iterations (max over instances) */
+    int outer_steps;       /* FP64 refinement steps (mixed form); 1 for FP64 */
+    int batch;
+    double rel_residual;   /* max over instances of ||B - L(U)||_F / ||B||_F, FP64, recomputed at exit */
+    double ms_total;       /* device time of the solve (CUDA events) */
+} mofem_solve_info;
+
+typedef struct mofem_ctx* mofem_handle;
+
+/* Setup (Sec. 3, Sec. 4; paper Eqs. newmatrix_1..7, kronecker_mass_distorted,
+ * diagonalisation_1).  Builds the banded 1D factors of the operator, the RHS
+ * mass factors, and the generalized eigendecompositions (FP64, on the GPU)
+ *   E1 Q1 = E2 Q1 diag(lambda),  Q1^T E2 Q1 = I,
+ *   F2 Q2 = F1 Q2 diag(mu),      Q2^T F1 Q2 = I,
+ * of the preconditioner pencils E1 = K_s[h] + gamma M_s[h], F1 = M_t,
+ * E2 = M_s[e2], F2 = K_t (e2 per mofem_opts.pencil).
+ * k: 1..4 (P_k) or 0 (lumped P1).  n_nodes: nodes per direction, (n-1) % max(k,1) == 0.
+ * Returns MOFEM_ERR_INVALID_ARG if h = g2 - g1 <= 0 at a quadrature point, if
+ * k or n is invalid, or for Neumann with gamma <= 0 (singular, Sec. 4).
+ * opts may be NULL (defaults).  *out receives the handle. */
+mofem_status mofem_setup(const mofem_profile* g1, const mofem_profile* g2, int k, int n_nodes,
+                         double gamma, mofem_bc bc, const mofem_opts* opts,
+                         cudaStream_t stream, mofem_handle* out);
+
+/* Batched setup: `batch` independent instances sharing k, n_nodes and bc, each
+ * with its own profiles g1[i], g2[i] and gamma[i].  The t-direction factors and
+ * Q2 are shared; Q1, lambda and the s-direction factors are per instance. */
+mofem_status mofem_setup_batched(int batch, const mofem_profile* g1, const mofem_profile* g2,
+                                 int k, int n_nodes, const double* gamma, mofem_bc bc,
+                                 const mofem_opts* opts, cudaStream_t stream, mofem_handle* out);
+
+/* Dimensions of a handle (any pointer may be NULL). */
+mofem_status mofem_get_dims(mofem_handle h, int* batch, int* n_nodes, int* q, int* n_terms);
+
+/* Operator apply Y = L(X) = sum_i S_i X T_i^T for every instance (Sec. 5,
+ * operator L~; Eq. laplace_cap-shaped-domain_sylvester).  X, Y: q x q per
+ * instance, leading dimension ld >= q, batch stride ld*q.  FP64 -> double
+ * arrays; MIXED_* -> float arrays (FP32 arithmetic).  X and Y must not overlap. */
+mofem_status mofem_apply(mofem_handle h, const void* X, void* Y, int ld, mofem_precision prec,
+                         cudaStream_t stream);
+
+/* Right-hand side B = M_s[h]_(int,all) F M_t_(int,all)^T (Sec. 5, operator R~):
+ * the mass matrix applied to the nodal values F (n x n per instance, ld = n,
+ * boundary nodes included).  B: q x q, ld_b >= q.  FP64. */
+mofem_status mofem_rhs(mofem_handle h, const double* F, double* B, int ld_b, cudaStream_t stream);
+
+/* Preconditioner Z = P^{-1}(R): the solution of E1 Z F1^T + E2 Z F2^T = R by the
+ * reduced approach (Sec. 4, Eq. reduced_formula_for_u):
+ *   Z = Q1 ((Q1^T R Q2) ./ (lambda_a + mu_b)) Q2^T.
+ * FP64 -> double arrays, four DGEMMs.  MIXED_TF32 / MIXED_BF16 -> float arrays,
+ * four tcgen05 GEMMs with operands rounded to TF32 / BF16 and FP32 accumulation. */
+mofem_status mofem_precond(mofem_handle h, const void* R, void* Z, int ld, mofem_precision prec,
+                           cudaStream_t stream);
+
+/* Solve L(U) = B with B = mofem_rhs(F) for every instance by MO-PCG (Sec. 5,
+ * Eqs. laplace_xnormal_pcg, laplace_xnormal_pcg_iteration with the standard PCG
+ * recurrences) until ||B - L(U)||_F <= rtol ||B||_F, checked on the FP64 true
+ * residual.  F: n x n per instance (ld n), FP64.  U: q x q per instance (ld q),
+ * FP64, in: initial guess, out: solution.  MIXED_*: flexible PCG in FP32 inside
+ * FP64 iterative refinement.  max_iter bounds the inner iterations of each
+ * refinement step (FP64: of the whole solve).  Synchronises `stream`.
+ * info may be NULL. */
+mofem_status mofem_pcg_solve(mofem_handle h, const double* F, double* U, double rtol, int max_iter,
+                             mofem_precision prec, mofem_solve_info* info, cudaStream_t stream);
+
+/* One IMEX Euler step of u_t - d_u Lap u = f (Sec. 6, Eqs.
+ * semilinear_heat_equation_fully_discrete_sylvester_pk and _R_pk): solves
+ * (M~ + d_u tau A~) U_np1 = M~ (U_n + tau F_n).  The handle must have been set up
+ * with gamma = 1 / (d_u tau) (the step is the elliptic solve scaled by d_u tau).
+ * U_n, U_np1: q x q (ld q) per instance, FP64; F_n: n x n nodal f(U_n) (ld n),
+ * FP64 (boundary entries of U_n are zero under Dirichlet).  Initial guess U_n;
+ * stops when ||R_s||_F <= tau ||R_0||_F (Sec. 6 stopping rule).  Synchronises. */
+mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const double* U_n,
+                             const double* F_n, double* U_np1, mofem_precision prec,
+                             mofem_solve_info* info, cudaStream_t stream);
+
+/* Release every buffer the handle owns. */
+mofem_status mofem_destroy(mofem_handle h);
+
+/* Human-readable name of a status code (static storage). */
+const char* mofem_status_string(mofem_status s);
+
+/* Text of the last error recorded on this host thread (static storage, "" if none). */
+const char* mofem_last_error(void);
+
+/* Host-only copy of the setup tables of one instance, computed exactly as
+ * mofem_setup computes them but without touching the GPU (for checking the
+ * assembly on machines without one).  Banded tables are diagonal-major:
+ * tab[term][j][r] = M_term[r][r + off + j - K], K = max(k,1), j = 0..2K,
+ * rows r = 0..q-1 of the trimmed matrix.
+ *   S, T: [n_terms][2K+1][q] (n_terms <= 8; 5 when g1' = 0 at every quadrature
+ *         point, else 8, in the order of the eight-term expansion: mass/stiffness,
+ *         M[(1+g1'^2)/h] (x) K_t, [M[2g1'h'/h] (x) K_t[t]], M[h'^2/h] (x) K_t[t^2],
+ *         [-G[g1'] (x) C_t^T, -G[g1']^T (x) C_t], -G[h'] (x) C_t[t]^T, -G[h']^T (x) C_t[t]);
+ *   Srh, Trh: [2K+1][q], the RHS mass factors (rows trimmed, columns = all n nodes).
+ * Any output pointer may be NULL. */
+mofem_status mofem_host_tables(const mofem_profile* g1, const mofem_profile* g2, int k, int n_nodes,
+                               double gamma, mofem_bc bc, const mofem_opts* opts, int* n_terms, int* q,
+                               double* S, double* T, double* Srh, double* Trh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOFEM_H */

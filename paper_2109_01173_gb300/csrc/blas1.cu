@@ -1,0 +1,411 @@
+// BLAS-1 and control kernels of the device-resident MO-PCG (Sec. 5, Eq.
+// laplace_xnormal_pcg_iteration with the standard PCG recurrences):
+//   alpha = <R, Z> / <Q, L(Q)>,  U += alpha Q,  R -= alpha L(Q)          (k_update)
+//   stop / breakdown / non-finite tests on FP64 sums                     (k_control)
+// plus the small helpers of setup and refinement (conversions, transposes,
+// Hadamard divide of the FP64 preconditioner, FP64 correction, norms).
+//
+// Every Frobenius inner product is accumulated in FP64: each CTA writes one
+// partial and consumers sum the partials in a fixed order, so results are
+// bitwise reproducible run to run.  Internal q x q matrices are stored with a
+// padded leading dimension ld (multiple of 64) whose padding columns hold zeros,
+// so the elementwise kernels stream them as flat arrays of 16-byte vectors.
+#include "internal.h"
+
+#include <cuda_bf16.h>
+
+namespace {
+
+constexpr int UPD_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_partials(const double* p, int n) {
+    double s = 0.0;
+    for (int i = threadIdx.x & 31; i < n; i += 32) s += p[i];
+    return warp_sum(s);
+}
+
+// Block-wide fixed-order sum of one double per thread; result valid in thread 0.
+template <int NTH>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < NTH / 32; ++w) s += sh[w];
+    }
+    __syncthreads();
+    return s;
+}
+
+struct UpdArgs {
+    void* U; void* R; const void* Q; const void* LQ; const void* Zold; void* Rop;
+    long long bs;        // batch stride (elements) = q * ld
+    long long nvec;      // vectors per instance
+    const double* qlq; int n_qlq;
+    const double* rz; int n_rz;
+    double* rr_part; double* rzo_part; int n_upd;
+    const PcgScalars* sc;
+    int flex;
+};
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+__device__ __forceinline__ void axpy_v(float4& u, const float4& q, float a) {
+    u.x = fmaf(a, q.x, u.x); u.y = fmaf(a, q.y, u.y); u.z = fmaf(a, q.z, u.z); u.w = fmaf(a, q.w, u.w);
+}
+__device__ __forceinline__ void axpy_v(double2& u, const double2& q, double a) {
+    u.x = fma(a, q.x, u.x); u.y = fma(a, q.y, u.y);
+}
+__device__ __forceinline__ double dot_v(const float4& a, const float4& b) {
+    return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+}
+__device__ __forceinline__ double dot_v(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+
+// ROP: 0 = no operand copy, 1 = BF16 copy of R for the tensor-core GEMM.
+template <typename T, int ROP>
+__global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
+    using V = typename Vec<T>::type;
+    __shared__ double sh[UPD_THREADS / 32];
+    __shared__ double alpha_s;
+    const int inst = blockIdx.y;
+    if (g.sc && !g.sc[inst].active) return;
+    if (threadIdx.x < 32) {
+        double qlq = warp_sum_partials(g.qlq + (size_t)inst * g.n_qlq, g.n_qlq);
+        double rz = warp_sum_partials(g.rz + (size_t)inst * g.n_rz, g.n_rz);
+        double al = rz / qlq;
+        if (!(qlq > 0.0) || !isfinite(al)) al = 0.0;   // flagged by k_control
+        if (threadIdx.x == 0) alpha_s = al;
+    }
+    __syncthreads();
+    const T alpha = (T)alpha_s;
+    V* U = reinterpret_cast<V*>(reinterpret_cast<T*>(g.U) + (size_t)inst * g.bs);
+    V* R = reinterpret_cast<V*>(reinterpret_cast<T*>(g.R) + (size_t)inst * g.bs);
+    const V* Q = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Q) + (size_t)inst * g.bs);
+    const V* LQ = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.LQ) + (size_t)inst * g.bs);
+    const V* Zo = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Zold) + (size_t)inst * g.bs);
+    double rr = 0.0, rzo = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nvec;
+         i += (long long)gridDim.x * blockDim.x) {
+        V u = U[i], r = R[i];
+        const V qv = Q[i], lq = LQ[i];
+        axpy_v(u, qv, alpha);
+        axpy_v(r, lq, -alpha);
+        U[i] = u;
+        R[i] = r;
+        rr += dot_v(r, r);
+        if (g.flex) rzo += dot_v(r, Zo[i]);
+        if constexpr (ROP == 1) {
+            static_assert(Vec<T>::W == 4, "BF16 operand copy is produced by the FP32 update only");
+            __nv_bfloat162 lo = __floats2bfloat162_rn(r.x, r.y);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(r.z, r.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<unsigned*>(&lo);
+            pk.y = *reinterpret_cast<unsigned*>(&hi);
+            reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(g.Rop) + (size_t)inst * g.bs)[i] = pk;
+        }
+    }
+    double s1 = block_sum<UPD_THREADS>(rr, sh);
+    double s2 = block_sum<UPD_THREADS>(rzo, sh);
+    if (threadIdx.x == 0) {
+        g.rr_part[(size_t)inst * g.n_upd + blockIdx.x] = s1;
+        if (g.rzo_part) g.rzo_part[(size_t)inst * g.n_upd + blockIdx.x] = s2;
+    }
+}
+
+struct CtlArgs {
+    PcgScalars* sc;
+    const double* rr; int n_rr;
+    const double* qlq; int n_qlq;
+    int batch, max_iter, fixed;
+    cudaGraphConditionalHandle cond;
+    int has_cond;
+};
+
+__global__ void __launch_bounds__(256) k_control(CtlArgs g) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int inst = warp; inst < g.batch; inst += nw) {
+        PcgScalars* s = g.sc + inst;
+        if (!s->active) continue;
+        double rr = warp_sum_partials(g.rr + (size_t)inst * g.n_rr, g.n_rr);
+        double qlq = warp_sum_partials(g.qlq + (size_t)inst * g.n_qlq, g.n_qlq);
+        if (lane == 0) {
+            int it = s->iters + 1;
+            s->iters = it;
+            s->rr = rr;
+            int act = 1;
+            if (!isfinite(rr) || !isfinite(qlq)) {
+                s->status |= DEV_ERR_NONFINITE;
+                act = 0;
+            } else if (!(qlq > 0.0)) {
+                s->status |= DEV_ERR_BREAKDOWN;
+                act = 0;
+            } else if (!g.fixed && rr <= s->tol2) {
+                act = 0;
+            } else if (it >= g.max_iter) {
+                act = 0;
+            }
+            s->active = act;
+            if (act) atomicOr(&any, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && g.has_cond) cudaGraphSetConditional(g.cond, any ? 1u : 0u);
+}
+
+// Start of an inner solve: rr0 = ||R0||^2, stop threshold tol2 = rtol^2 * ref2
+// (ref2 = rr0 when no reference is given), counters.  One warp per instance.
+struct InitArgs {
+    PcgScalars* sc;
+    const double* rr; int n_rr;   // partials of ||R0||^2
+    const double* ref2;           // [batch] or nullptr
+    int batch;
+    double rtol;
+};
+
+__global__ void k_init(InitArgs g) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int inst = warp; inst < g.batch; inst += nw) {
+        double rr = warp_sum_partials(g.rr + (size_t)inst * g.n_rr, g.n_rr);
+        if (lane == 0) {
+            PcgScalars* s = g.sc + inst;
+            const double ref = g.ref2 ? g.ref2[inst] : rr;
+            s->rr0 = rr;
+            s->rr = rr;
+            s->tol2 = g.rtol * g.rtol * ref;
+            s->iters = 0;
+            s->status = isfinite(rr) ? 0 : DEV_ERR_NONFINITE;
+            s->active = (rr > s->tol2 && isfinite(rr)) ? 1 : 0;
+        }
+    }
+}
+
+// IMEX right-hand side in nodal form: Fbar = gam * (pad(U_n) + tau F_n), n x n
+// per instance; U_n is q x q (boundary nodes zero under Dirichlet).
+__global__ void k_imex_rhs(const double* Un, const double* Fn, double* Fbar, int n, int q, int off, double gam,
+                           double tau) {
+    const int inst = blockIdx.z, r = blockIdx.y;
+    const double* fn = Fn + (size_t)inst * n * n + (size_t)r * n;
+    double* fb = Fbar + (size_t)inst * n * n + (size_t)r * n;
+    const int ur = r - off;
+    for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < n; cc += gridDim.x * blockDim.x) {
+        const int uc = cc - off;
+        double u = 0.0;
+        if (ur >= 0 && ur < q && uc >= 0 && uc < q) u = Un[(size_t)inst * q * q + (size_t)ur * q + uc];
+        fb[cc] = gam * (u + tau * fn[cc]);
+    }
+}
+
+// Dot-product partials <A, B> over a flat [batch][nvec] range.
+template <typename T>
+__global__ void __launch_bounds__(UPD_THREADS) k_dot(const T* A, const T* B, long long bs, long long n,
+                                                    double* part, int nblk) {
+    __shared__ double sh[UPD_THREADS / 32];
+    const int inst = blockIdx.y;
+    A += (size_t)inst * bs;
+    B += (size_t)inst * bs;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)A[i] * (double)B[i];
+    double s = block_sum<UPD_THREADS>(acc, sh);
+    if (threadIdx.x == 0) part[(size_t)inst * nblk + blockIdx.x] = s;
+}
+
+// kinds: 0 float, 1 double, 2 bf16
+template <typename S, typename D>
+__global__ void k_convert(const S* src, long long s_bs, int s_ld, D* dst, long long d_bs, int d_ld, int rows, int cols) {
+    const int inst = blockIdx.z;
+    const int r = blockIdx.y;
+    src += (size_t)inst * s_bs + (size_t)r * s_ld;
+    dst += (size_t)inst * d_bs + (size_t)r * d_ld;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+        if constexpr (std::is_same<D, __nv_bfloat16>::value) dst[c] = __float2bfloat16_rn((float)src[c]);
+        else dst[c] = (D)src[c];
+    }
+}
+
+__global__ void k_transpose64(const double* src, long long s_bs, double* dst, long long d_bs, int n, int s_ld, int d_ld) {
+    __shared__ double tile[32][33];
+    const int inst = blockIdx.z;
+    src += (size_t)inst * s_bs;
+    dst += (size_t)inst * d_bs;
+    int x = blockIdx.x * 32 + threadIdx.x, y0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        int y = y0 + j;
+        if (x < n && y < n) tile[j][threadIdx.x] = src[(size_t)y * s_ld + x];
+    }
+    __syncthreads();
+    x = blockIdx.y * 32 + threadIdx.x;
+    y0 = blockIdx.x * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        int y = y0 + j;
+        if (x < n && y < n) dst[(size_t)y * d_ld + x] = tile[threadIdx.x][j];
+    }
+}
+
+__global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const double* lam, long long lam_bs,
+                                 const double* mu) {
+    const int inst = blockIdx.z, i = blockIdx.y;
+    const double li = lam[(size_t)inst * lam_bs + i];
+    double* row = W + (size_t)inst * bs + (size_t)i * ld;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) row[j] /= (li + mu[j]);
+}
+
+__global__ void k_axpy_into64(double* U, long long u_bs, int u_ld, const float* d, long long d_bs, int d_ld, int q) {
+    const int inst = blockIdx.z, r = blockIdx.y;
+    double* u = U + (size_t)inst * u_bs + (size_t)r * u_ld;
+    const float* dv = d + (size_t)inst * d_bs + (size_t)r * d_ld;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q; c += gridDim.x * blockDim.x) u[c] += (double)dv[c];
+}
+
+// Sum of squares per instance, fixed order: one CTA per instance.
+__global__ void __launch_bounds__(256) k_sumsq64(const double* A, long long bs, int ld, int rows, int cols, double* out) {
+    __shared__ double sh[8];
+    const int inst = blockIdx.x;
+    const double* a = A + (size_t)inst * bs;
+    double acc = 0.0;
+    for (int r = 0; r < rows; ++r)
+        for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+            double v = a[(size_t)r * ld + c];
+            acc += v * v;
+        }
+    double s = block_sum<256>(acc, sh);
+    if (threadIdx.x == 0) out[inst] = s;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* R, const void* Q, const void* LQ,
+                               const void* Zold, void* Rop, int rop_kind, const double* rz_partials, int flex,
+                               cudaStream_t st) {
+    UpdArgs g;
+    g.U = U; g.R = R; g.Q = Q; g.LQ = LQ; g.Zold = Zold; g.Rop = Rop;
+    g.bs = (long long)c->q * c->ld;
+    g.nvec = g.bs / (fp64 ? 2 : 4);
+    g.qlq = c->part.qlq; g.n_qlq = c->part.n_apply;
+    g.rz = rz_partials; g.n_rz = c->part.n_rz;
+    g.rr_part = c->part.rr; g.rzo_part = c->part.rzo; g.n_upd = c->part.n_upd;
+    g.sc = c->d_sc;
+    g.flex = flex;
+    dim3 grid(c->part.n_upd, c->batch);
+    if (fp64) k_update<double, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+    else if (rop_kind == 1) k_update<float, 1><<<grid, UPD_THREADS, 0, st>>>(g);
+    else k_update<float, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_pcg_control(const mofem_ctx* c, int max_iter, bool fixed, const cudaGraphConditionalHandle* cond,
+                                cudaStream_t st) {
+    CtlArgs g;
+    g.sc = c->d_sc;
+    g.rr = c->part.rr; g.n_rr = c->part.n_upd;
+    g.qlq = c->part.qlq; g.n_qlq = c->part.n_apply;
+    g.batch = c->batch; g.max_iter = max_iter; g.fixed = fixed ? 1 : 0;
+    g.has_cond = cond ? 1 : 0;
+    if (cond) g.cond = *cond;
+    else g.cond = 0;
+    k_control<<<1, 256, 0, st>>>(g);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
+                             cudaStream_t st) {
+    InitArgs g;
+    g.sc = c->d_sc;
+    g.rr = rr_partials; g.n_rr = n_rr;
+    g.ref2 = ref2;
+    g.batch = c->batch;
+    g.rtol = rtol;
+    k_init<<<1, 256, 0, st>>>(g);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_imex_rhs(const double* Un, const double* Fn, double* Fbar, int n, int q, int off, double gam,
+                             double tau, int batch, cudaStream_t st) {
+    dim3 grid((n + 255) / 256, n, batch);
+    k_imex_rhs<<<grid, 256, 0, st>>>(Un, Fn, Fbar, n, q, off, gam, tau);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_dot_partials(const void* A, const void* B, bool fp64, long long bs, long long n, int batch,
+                                 double* part, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, batch);
+    if (fp64) k_dot<double><<<grid, UPD_THREADS, 0, st>>>((const double*)A, (const double*)B, bs, n, part, nblk);
+    else k_dot<float><<<grid, UPD_THREADS, 0, st>>>((const float*)A, (const float*)B, bs, n, part, nblk);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_convert(const void* src, int sk, long long s_bs, int s_ld, void* dst, int dk, long long d_bs,
+                            int d_ld, int rows, int cols, int batch, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || batch <= 0) return MOFEM_OK;
+    dim3 grid((cols + 255) / 256, rows, batch);
+#define CONV(S, D) k_convert<S, D><<<grid, 256, 0, st>>>((const S*)src, s_bs, s_ld, (D*)dst, d_bs, d_ld, rows, cols)
+    if (sk == 0 && dk == 0) CONV(float, float);
+    else if (sk == 0 && dk == 1) CONV(float, double);
+    else if (sk == 0 && dk == 2) CONV(float, __nv_bfloat16);
+    else if (sk == 1 && dk == 0) CONV(double, float);
+    else if (sk == 1 && dk == 1) CONV(double, double);
+    else if (sk == 1 && dk == 2) CONV(double, __nv_bfloat16);
+    else return MOFEM_ERR_UNSUPPORTED;
+#undef CONV
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_transpose64(const double* src, long long s_bs, double* dst, long long d_bs, int n, int ld,
+                                int batch, cudaStream_t st) {
+    // src: n x n with leading dimension n (dense); dst: leading dimension ld
+    dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
+    k_transpose64<<<grid, dim3(32, 8), 0, st>>>(src, s_bs, dst, d_bs, n, n, ld);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
+                                   int n, int batch, cudaStream_t st) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32, batch);
+    k_transpose64<<<grid, dim3(32, 8), 0, st>>>(src, s_bs, dst, d_bs, n, s_ld, d_ld);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_hadamard_div64(double* W, long long bs, int ld, int q, const double* lam, long long lam_bs,
+                                   const double* mu, int batch, cudaStream_t st) {
+    dim3 grid((q + 255) / 256, q, batch);
+    k_hadamard_div64<<<grid, 256, 0, st>>>(W, bs, ld, q, lam, lam_bs, mu);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const float* dU, long long d_bs, int d_ld,
+                                int q, int batch, cudaStream_t st) {
+    dim3 grid((q + 255) / 256, q, batch);
+    k_axpy_into64<<<grid, 256, 0, st>>>(U64, u_bs, u_ld, dU, d_bs, d_ld, q);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_sumsq64(const double* A, long long bs, int ld, int rows, int cols, int batch, double* out,
+                            cudaStream_t st) {
+    k_sumsq64<<<batch, 256, 0, st>>>(A, bs, ld, rows, cols, out);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}

@@ -1,0 +1,137 @@
+// extern "C" entry points of libmofem (declared in include/mofem.h): argument
+// validation, handle lifetime, dispatch to the setup, kernels and solver.
+#include "internal.h"
+
+#include <cmath>
+#include <new>
+
+namespace {
+
+mofem_opts default_opts(const mofem_opts* o) {
+    mofem_opts d{};
+    if (o) d = *o;
+    if (d.max_outer <= 0) d.max_outer = 20;
+    if (!(d.inner_rtol > 0.0)) d.inner_rtol = 1e-4;
+    return d;
+}
+
+bool valid_precision(mofem_precision p) {
+    return p == MOFEM_FP64 || p == MOFEM_MIXED_TF32 || p == MOFEM_MIXED_BF16;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mofem_status_string(mofem_status s) {
+    switch (s) {
+        case MOFEM_OK: return "MOFEM_OK";
+        case MOFEM_ERR_INVALID_ARG: return "MOFEM_ERR_INVALID_ARG";
+        case MOFEM_ERR_CUDA: return "MOFEM_ERR_CUDA";
+        case MOFEM_ERR_EIG: return "MOFEM_ERR_EIG";
+        case MOFEM_ERR_NONFINITE: return "MOFEM_ERR_NONFINITE";
+        case MOFEM_ERR_BREAKDOWN: return "MOFEM_ERR_BREAKDOWN";
+        case MOFEM_ERR_NOT_CONVERGED: return "MOFEM_ERR_NOT_CONVERGED";
+        case MOFEM_ERR_TIMEOUT: return "MOFEM_ERR_TIMEOUT";
+        case MOFEM_ERR_OOM: return "MOFEM_ERR_OOM";
+        case MOFEM_ERR_UNSUPPORTED: return "MOFEM_ERR_UNSUPPORTED";
+    }
+    return "MOFEM_ERR_?";
+}
+
+mofem_status mofem_setup_batched(int batch, const mofem_profile* g1, const mofem_profile* g2, int k, int n_nodes,
+                                 const double* gamma, mofem_bc bc, const mofem_opts* opts, cudaStream_t stream,
+                                 mofem_handle* out) {
+    if (!out || !g1 || !g2 || !gamma || batch < 1) return MOFEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (k < 0 || k > 4) return MOFEM_ERR_INVALID_ARG;
+    if (bc != MOFEM_BC_DIRICHLET && bc != MOFEM_BC_NEUMANN) return MOFEM_ERR_INVALID_ARG;
+    const int d = k == 0 ? 1 : k;
+    if (n_nodes < 3 || (n_nodes - 1) % d != 0 || n_nodes > 16385) return MOFEM_ERR_INVALID_ARG;
+    for (int i = 0; i < batch; ++i) {
+        if (!g1[i].g || !g1[i].dg || !g2[i].g || !g2[i].dg) return MOFEM_ERR_INVALID_ARG;
+        if (!std::isfinite(gamma[i]) || gamma[i] < 0.0) return MOFEM_ERR_INVALID_ARG;
+        if (bc == MOFEM_BC_NEUMANN && !(gamma[i] > 0.0)) return MOFEM_ERR_INVALID_ARG;   // singular operator
+    }
+    if (opts && (opts->quad_points < 0 || opts->quad_points > 16)) return MOFEM_ERR_INVALID_ARG;
+    mofem_ctx* c = new (std::nothrow) mofem_ctx();
+    if (!c) return MOFEM_ERR_OOM;
+    c->batch = batch;
+    c->k = k;
+    c->n = n_nodes;
+    c->bc = bc;
+    c->opts = default_opts(opts);
+    c->gamma.assign(gamma, gamma + batch);
+    cudaGetDevice(&c->dev);
+    mofem_status s = mofem_build(c, g1, g2, gamma, stream);
+    if (s == MOFEM_OK) s = solver_init(c, stream);
+    if (s == MOFEM_OK && cudaStreamSynchronize(stream) != cudaSuccess) s = MOFEM_ERR_CUDA;
+    if (s != MOFEM_OK) {
+        mofem_free_extra(c);
+        mofem_free(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return MOFEM_OK;
+}
+
+mofem_status mofem_setup(const mofem_profile* g1, const mofem_profile* g2, int k, int n_nodes, double gamma,
+                         mofem_bc bc, const mofem_opts* opts, cudaStream_t stream, mofem_handle* out) {
+    return mofem_setup_batched(1, g1, g2, k, n_nodes, &gamma, bc, opts, stream, out);
+}
+
+mofem_status mofem_get_dims(mofem_handle h, int* batch, int* n_nodes, int* q, int* n_terms) {
+    if (!h) return MOFEM_ERR_INVALID_ARG;
+    if (batch) *batch = h->batch;
+    if (n_nodes) *n_nodes = h->n;
+    if (q) *q = h->q;
+    if (n_terms) *n_terms = h->NT;
+    return MOFEM_OK;
+}
+
+mofem_status mofem_apply(mofem_handle h, const void* X, void* Y, int ld, mofem_precision prec, cudaStream_t stream) {
+    if (!h || !X || !Y || ld < h->q || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
+    const long long bs = (long long)ld * h->q;
+    return op_apply(h, prec == MOFEM_FP64, X, bs, ld, Y, bs, ld, nullptr, stream);
+}
+
+mofem_status mofem_rhs(mofem_handle h, const double* F, double* B, int ld_b, cudaStream_t stream) {
+    if (!h || !F || !B || ld_b < h->q) return MOFEM_ERR_INVALID_ARG;
+    return op_rhs(h, F, B, (long long)ld_b * h->q, ld_b, stream);
+}
+
+mofem_status mofem_precond(mofem_handle h, const void* R, void* Z, int ld, mofem_precision prec, cudaStream_t stream) {
+    if (!h || !R || !Z || ld < h->q || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
+    const long long bs = (long long)ld * h->q;
+    if (prec == MOFEM_FP64) return precond64(h, (const double*)R, bs, ld, (double*)Z, bs, ld, stream);
+    return precond_tc(h, prec == MOFEM_MIXED_BF16 ? 1 : 0, (const float*)R, bs, ld, (float*)Z, bs, ld, nullptr,
+                      nullptr, stream);
+}
+
+mofem_status mofem_pcg_solve(mofem_handle h, const double* F, double* U, double rtol, int max_iter,
+                             mofem_precision prec, mofem_solve_info* info, cudaStream_t stream) {
+    if (!h || !F || !U || !(rtol > 0.0) || max_iter < 1 || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
+    return solve_elliptic(h, F, U, rtol, max_iter, prec, info, stream);
+}
+
+mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const double* U_n, const double* F_n,
+                             double* U_np1, mofem_precision prec, mofem_solve_info* info, cudaStream_t stream) {
+    if (!h || !U_n || !F_n || !U_np1 || !(d_u > 0.0) || !(tau > 0.0) || !valid_precision(prec))
+        return MOFEM_ERR_INVALID_ARG;
+    const double want = 1.0 / (d_u * tau);
+    for (int i = 0; i < h->batch; ++i)
+        if (std::fabs(h->gamma[i] - want) > 1e-12 * want) return MOFEM_ERR_INVALID_ARG;
+    return solve_imex(h, d_u, tau, U_n, F_n, U_np1, prec, info, stream);
+}
+
+mofem_status mofem_destroy(mofem_handle h) {
+    if (!h) return MOFEM_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    mofem_free_extra(h);
+    mofem_free(h);
+    delete h;
+    return MOFEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,411 @@
+// tcgen05 tensor-core GEMMs of the reduced-approach preconditioner
+// (Sec. 4, Eq. reduced_formula_for_u, applied to the two-term Sylvester
+// preconditioner of MO-PCG):
+//
+//     Z = Q1 ((Q1^T R Q2) ./ (lambda_a + mu_b)) Q2^T
+//
+// computed as four GEMMs, each of the form D = A B^T with both operands
+// "K-major" (row-major, contraction index contiguous) and a transposed store
+// out[n][m] = D[m][n] (coalesced straight out of the 32x32b TMEM layout):
+//   G1: D[a][j] = sum_b R[a][b]   Q2T[j][b]          -> X1T[j][a]   (X1 = R Q2)
+//   G2: D[i][j] = sum_a Q1T[i][a] X1T[j][a]          -> WT[j][i] = D / (lam_i + mu_j)
+//   G3: D[j][a] = sum_i WT[j][i]  Q1[a][i]           -> Y[a][j]     (Y = Q1 W)
+//   G4: D[b][a] = sum_j Q2[b][j]  Y[a][j]            -> Z[a][b]     (Z = Y Q2^T), + <R, Z> partials
+//
+// Kernel: one 128 x 256 output tile per CTA (M = 128 TMEM lanes, N = 256 FP32
+// TMEM columns), 128 threads.  Warp 0 lane 0 issues TMA loads of 128-byte-wide
+// K slices (SWIZZLE_128B) into a 4-stage shared-memory ring; warp 1 lane 0
+// issues tcgen05.mma (kind::f16 with BF16 operands or kind::tf32) and releases
+// stages with tcgen05.commit; warp 2 owns the TMEM allocation; all four warps
+// run the epilogue (tcgen05.ld 32x32b.x32).  Every mbarrier wait is bounded
+// (2 s of %globaltimer); on expiry the CTA records DEV_ERR_TIMEOUT, skips the
+// epilogue, frees its TMEM and exits.  No cluster multicast is used.
+#include "internal.h"
+
+#include <cuda_bf16.h>
+#include <cstdio>
+
+namespace {
+
+constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+
+enum { EPI_STORE = 0, EPI_DIV = 1, EPI_Z = 2 };
+
+struct GemmArgs {
+    void* out; long long out_bs; int out_ld; int out_bf16;
+    int M, N, nk;
+    int a_shared, b_shared;
+    int epi;
+    const float* lam; long long lam_bs; const float* mu;
+    const float* R; long long r_bs; int r_ld;
+    double* rz_part;
+    const PcgScalars* sc;
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase of the given parity; false on timeout.
+__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(a, parity)) {
+        if (gtimer() - t0 > WAIT_LIMIT_NS) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile written by TMA with 128-byte
+// swizzle (8-row x 128-byte atoms, 1024 bytes apart), tcgen05 descriptor version 1.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = fmt (1 BF16 under kind::f16, 2 TF32
+// under kind::tf32), both K-major, N = BN, M = BM.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    if constexpr (KIND == 1) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(1)), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(2)), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
+    const int inst = blockIdx.z;
+    if (g.sc && !g.sc[inst].active) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    __shared__ double red[4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB)) : "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        const int za = g.a_shared ? 0 : inst, zb = g.b_shared ? 0 : inst;
+        for (int kb = 0; kb < g.nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
+                ok = false;
+                break;
+            }
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+            tma_load_3d(sa, &mA, full0 + 8 * s, kb * (128 / (KIND == 1 ? 2 : 4)), m0, za);
+            tma_load_3d(sa + A_BYTES, &mB, full0 + 8 * s, kb * (128 / (KIND == 1 ? 2 : 4)), n0, zb);
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < g.nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(full0 + 8 * s, ph)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)   // 4 x 32-byte K steps per 128-byte slice
+                mma<KIND>(tmem, make_desc(sa + 32 * kk), make_desc(sa + A_BYTES + 32 * kk), (kb | kk) != 0);
+            mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);
+    }
+
+    // ---- epilogue: all 128 threads, thread = TMEM lane = output row m ----
+    ok = mbar_wait(done, 0) && ok;
+    __syncwarp();
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    double acc = 0.0;
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+        const bool m_ok = m < g.M;
+        float lam_m = 0.f;
+        if (g.epi == EPI_DIV && m_ok) lam_m = g.lam[(size_t)inst * g.lam_bs + m];
+        const size_t obase = (size_t)inst * g.out_bs;
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+            const int nb = n0 + c * 32;
+            if (!m_ok) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = nb + j;
+                if (n >= g.N) break;
+                float x = v[j];
+                const size_t o = obase + (size_t)n * g.out_ld + m;
+                if (g.epi == EPI_DIV) x = x / (lam_m + g.mu[n]);
+                if (g.epi == EPI_Z) {
+                    reinterpret_cast<float*>(g.out)[o] = x;
+                    if (g.R) acc += (double)x * (double)g.R[(size_t)inst * g.r_bs + (size_t)n * g.r_ld + m];
+                } else if (g.out_bf16) {
+                    reinterpret_cast<__nv_bfloat16*>(g.out)[o] = __float2bfloat16_rn(x);
+                } else {
+                    reinterpret_cast<float*>(g.out)[o] = x;
+                }
+            }
+        }
+    } else if (threadIdx.x == 0 && g.status) {
+        atomicOr(g.status, DEV_ERR_TIMEOUT);
+    }
+    if (g.epi == EPI_Z && g.rz_part) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) red[warp] = acc;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (g.epi == EPI_Z && g.rz_part && threadIdx.x == 0)
+        g.rz_part[(size_t)inst * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] =
+            red[0] + red[1] + red[2] + red[3];
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 3D tensor map over [batch][rows][cols] (cols contiguous, leading dimension ld),
+// box = 128 bytes of K x box_rows rows x 1 instance, 128-byte swizzle.
+mofem_status make_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
+                      int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        mofem_set_last_error("cuTensorMapEncodeTiled entry point unavailable", __FILE__, __LINE__);
+        return MOFEM_ERR_CUDA;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * esize, (cuuint64_t)rows * ld * esize};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                     const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        mofem_set_last_error(buf, __FILE__, __LINE__);
+        return MOFEM_ERR_CUDA;
+    }
+    return MOFEM_OK;
+}
+
+template <int KIND>
+mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        MOFEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        attr = true;
+    }
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
+    k_gemm<KIND><<<grid, 128, SMEM_BYTES, st>>>(mA, mB, g);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+}  // namespace
+
+mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
+                                   int n, int batch, cudaStream_t st);
+
+int tc_rz_ctas(const mofem_ctx* c) { return ((c->q + BN - 1) / BN) * ((c->q + BM - 1) / BM); }
+
+// Allocate the operand copies of Q1, Q1^T, Q2, Q2^T in the precision `which`
+// (0 TF32 = FP32 storage, 1 BF16), the intermediates, and the tensor maps.
+mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
+    TcPlan& p = c->tc[which];
+    if (p.ready) return MOFEM_OK;
+    const int q = c->q, ld = c->ld, B = c->batch;
+    const int es = which == 1 ? 2 : 4;
+    const int kind = which == 1 ? 2 : 0;   // launch_convert kinds: 0 float, 2 bf16
+    p.esize = es;
+    const size_t per = (size_t)q * ld;
+    MOFEM_CUDA_TRY(cudaMalloc(&p.Q1, per * B * es));
+    MOFEM_CUDA_TRY(cudaMalloc(&p.Q1T, per * B * es));
+    MOFEM_CUDA_TRY(cudaMalloc(&p.Q2, per * es));
+    MOFEM_CUDA_TRY(cudaMalloc(&p.Q2T, per * es));
+    MOFEM_CUDA_TRY(cudaMalloc(&p.Rop, per * B * es));
+    MOFEM_CUDA_TRY(cudaMalloc(&p.X1T, per * B * es));
+    MOFEM_CUDA_TRY(cudaMalloc(&p.WT, per * B * es));
+    MOFEM_CUDA_TRY(cudaMalloc(&p.Y, per * B * es));
+    void* zero[] = {p.Q1, p.Q1T, p.Rop, p.X1T, p.WT, p.Y};
+    for (void* z : zero) MOFEM_CUDA_TRY(cudaMemsetAsync(z, 0, per * B * es, st));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(p.Q2, 0, per * es, st));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(p.Q2T, 0, per * es, st));
+    double* tmp = nullptr;
+    MOFEM_CUDA_TRY(cudaMalloc(&tmp, per * sizeof(double)));
+    MOFEM_TRY(launch_convert(c->Q2_64, 1, per, ld, p.Q2, kind, per, ld, q, q, 1, st));
+    MOFEM_TRY(launch_transpose64_ld(c->Q2_64, per, ld, tmp, per, ld, q, 1, st));
+    MOFEM_TRY(launch_convert(tmp, 1, per, ld, p.Q2T, kind, per, ld, q, q, 1, st));
+    for (int i = 0; i < B; ++i) {
+        const double* q1 = c->Q1_64 + per * i;
+        MOFEM_TRY(launch_convert(q1, 1, per, ld, (char*)p.Q1 + per * i * es, kind, per, ld, q, q, 1, st));
+        MOFEM_TRY(launch_transpose64_ld(q1, per, ld, tmp, per, ld, q, 1, st));
+        MOFEM_TRY(launch_convert(tmp, 1, per, ld, (char*)p.Q1T + per * i * es, kind, per, ld, q, q, 1, st));
+    }
+    MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(tmp);
+    // A maps (box rows BM) and B maps (box rows BN) of the four GEMMs
+    MOFEM_TRY(make_map(&p.mA[0], p.Rop, es, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[0], p.Q2T, es, q, q, 1, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[1], p.Q1T, es, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[1], p.X1T, es, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[2], p.WT, es, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[2], p.Q1, es, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[3], p.Q2, es, q, q, 1, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[3], p.Y, es, q, q, B, ld, BN));
+    p.ready = true;
+    return MOFEM_OK;
+}
+
+// Z = P^{-1}(R) with R already in p.Rop (rounded operand).  R32 (FP32, same
+// layout as Z) feeds the fused <R, Z> partials when rz_partial != nullptr.
+mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z, int z_ld,
+                        long long z_bs, double* rz_partial, const PcgScalars* sc, cudaStream_t st) {
+    const TcPlan& p = c->tc[which];
+    const int q = c->q, ld = c->ld;
+    const int bk = which == 1 ? 64 : 32;
+    GemmArgs g{};
+    g.M = q;
+    g.N = q;
+    g.nk = (q + bk - 1) / bk;
+    g.sc = sc;
+    g.status = c->d_status;
+    g.lam = c->lam32;
+    g.lam_bs = ld;
+    g.mu = c->mu32;
+    g.out_bs = (long long)q * ld;
+    g.out_ld = ld;
+    g.out_bf16 = which == 1;
+    auto run = [&](int i) -> mofem_status {
+        return which == 1 ? launch_gemm<1>(p.mA[i], p.mB[i], g, c->batch, st)
+                          : launch_gemm<0>(p.mA[i], p.mB[i], g, c->batch, st);
+    };
+    // G1: X1T = (R Q2)^T
+    g.out = p.X1T; g.epi = EPI_STORE; g.a_shared = 0; g.b_shared = 1;
+    MOFEM_TRY(run(0));
+    // G2: WT = ((Q1^T X1) ./ (lam + mu))^T
+    g.out = p.WT; g.epi = EPI_DIV; g.a_shared = 0; g.b_shared = 0;
+    MOFEM_TRY(run(1));
+    // G3: Y = Q1 W
+    g.out = p.Y; g.epi = EPI_STORE; g.a_shared = 0; g.b_shared = 0;
+    MOFEM_TRY(run(2));
+    // G4: Z = Y Q2^T (+ <R, Z> partials)
+    g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 1; g.b_shared = 0;
+    g.R = R32; g.r_bs = r_bs; g.r_ld = r_ld; g.rz_part = rz_partial;
+    MOFEM_TRY(run(3));
+    return MOFEM_OK;
+}

@@ -1,0 +1,176 @@
+// Internal declarations shared by the libmofem translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cublas_v2.h>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/mofem.h"
+
+#define MOFEM_MAX_TERMS 8
+
+// Bit flags written by kernels into the device status word (ctx->d_status).
+enum : int {
+    DEV_ERR_TIMEOUT = 1,     // a bounded mbarrier wait gave up (tcgen05 GEMM)
+    DEV_ERR_NONFINITE = 2,   // NaN/Inf met in a recurrence scalar
+    DEV_ERR_BREAKDOWN = 4,   // <Q, L(Q)> <= 0
+};
+
+// Per-instance scalar state of the device-resident PCG (FP64).
+struct PcgScalars {
+    double rz;          // <R, Z> of the current iterate
+    double rz_prev;     // <R, Z> of the previous iterate (flexible beta denominator)
+    double rr0;         // ||R_0||^2 of this (inner) solve
+    double rr;          // ||R||^2 after the last update
+    double tol2;        // stop when rr <= tol2
+    int iters;          // iterations done in this (inner) solve
+    int active;         // 1 while not converged
+    int status;         // DEV_ERR_* bits
+    int pad;
+};
+
+// Fixed partial-sum layout: every reduction writes one double per CTA into a
+// slice of `partials`, later summed in a fixed order (deterministic).
+struct Partials {
+    double* qlq;    // <Q, L(Q)>            [batch][n_apply_ctas]
+    double* rr;     // ||R||^2 after update [batch][n_upd_ctas]
+    double* rzo;    // <R_new, Z_old>       [batch][n_upd_ctas]
+    double* rz;     // <R, Z_new>           [batch][n_rz_ctas]
+    int n_apply, n_upd, n_rz;
+};
+
+struct TcPlan {                 // one tensor-core precision (BF16 or TF32)
+    bool ready = false;
+    int esize = 0;              // operand bytes (2 bf16, 4 tf32)
+    void* Q1 = nullptr;  void* Q1T = nullptr;   // [batch][q][ld] operand copies
+    void* Q2 = nullptr;  void* Q2T = nullptr;   // [q][ld] (shared)
+    void* Rop = nullptr;                        // GEMM1 A operand (R rounded), [batch][q][ld]
+    void* X1T = nullptr; void* WT = nullptr; void* Y = nullptr;  // intermediates
+    CUtensorMap mA[4], mB[4];
+};
+
+struct mofem_ctx {
+    int batch = 1, k = 1, deg = 1, K = 1, P = 3, n = 0, q = 0, nq = 0, NT = 5;
+    mofem_bc bc = MOFEM_BC_DIRICHLET;
+    mofem_opts opts{};
+    int ld = 0;                  // leading dimension of internal q x q matrices (multiple of 64)
+    int off = 1;                 // node index of trimmed row 0 (1 Dirichlet, 0 Neumann)
+    std::vector<double> gamma;   // per instance
+    int dev = 0;
+
+    // banded tables, diagonal-major: tab[term][j][row] = S_term[row][row + j - K]
+    double* S64 = nullptr;  float* S32 = nullptr;   // [batch][NT][P][q]
+    double* T64 = nullptr;  float* T32 = nullptr;   // [NT][P][q]
+    double* Sr64 = nullptr; double* Tr64 = nullptr; // RHS mass factors: [batch][P][q], [P][q] (offset off)
+
+    // preconditioner eigen data (FP64 masters)
+    double* Q1_64 = nullptr;   // [batch][q][ld]  Q1 row-major (columns = eigenvectors)
+    double* Q2_64 = nullptr;   // [q][ld]
+    double* lam64 = nullptr;   // [batch][ld] (padded with 1)
+    double* mu64 = nullptr;    // [ld]
+    float* lam32 = nullptr; float* mu32 = nullptr;
+    TcPlan tc[2];              // [0] TF32, [1] BF16
+
+    // FP64-form workspaces (lazily allocated)
+    double* w64 = nullptr;     // 8 matrices [batch][q][ld]
+    // mixed-form workspaces (lazily allocated)
+    float* w32 = nullptr;      // 7 matrices [batch][q][ld]: U, R, Z, Q0, Q1, LQ, tmp
+    double* Bm64 = nullptr;    // [batch][q][ld] FP64 right-hand side
+    double* R64 = nullptr;     // [batch][q][ld] FP64 true residual
+    double* d_part = nullptr;  // partial sums
+    Partials part{};
+    PcgScalars* d_sc = nullptr;  // [batch]
+    int* d_status = nullptr;     // device error bits
+    double* d_red = nullptr;     // small scratch for reductions [batch * 8]
+
+    cublasHandle_t cublas = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    // captured graphs of one PCG iteration, keyed by precision
+    cudaGraphExec_t it_graph[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t loop_graph[3] = {nullptr, nullptr, nullptr};
+    int it_graph_max_iter[3] = {0, 0, 0};
+};
+
+// ---- error helpers -------------------------------------------------------
+#define MOFEM_CUDA_TRY(x)                                              \
+    do {                                                              \
+        cudaError_t e_ = (x);                                         \
+        if (e_ != cudaSuccess) {                                      \
+            mofem_set_last_error(cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? MOFEM_ERR_OOM : MOFEM_ERR_CUDA; \
+        }                                                             \
+    } while (0)
+
+#define MOFEM_TRY(x)                        \
+    do {                                    \
+        mofem_status s_ = (x);              \
+        if (s_ != MOFEM_OK) return s_;      \
+    } while (0)
+
+void mofem_set_last_error(const char* msg, const char* file, int line);
+
+// ---- setup (setup.cpp) ---------------------------------------------------
+mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_profile* g2,
+                         const double* gamma, cudaStream_t st);
+void mofem_free(mofem_ctx* c);
+
+// ---- kernels (apply.cu) --------------------------------------------------
+// Y = L(X) for every instance; optional fused prologue X = Z + beta X_prev and
+// partial <X, Y>; see apply.cu for the modes.
+enum ApplyMode { APPLY_PLAIN = 0, APPLY_QUPDATE = 1, APPLY_RESIDUAL = 2 };
+
+struct ApplyArgs {
+    const void* X; long long x_bs; int x_ld;     // input; Q_prev in QUPDATE mode
+    void* Y; long long y_bs; int y_ld;           // output
+    const void* Z; void* Xnew;                    // QUPDATE: X := Z + beta X_prev, written to Xnew
+    const void* Bm;                               // RESIDUAL: Y = Bm - L(X)
+    const void* S; long long s_bs;                // S tables [batch][nt][P][rows_out]
+    const void* T;                                // T tables [nt][P][cols_out]
+    int rows_in, cols_in, off, rows_out, cols_out;
+    double* partial;                              // per-CTA FP64 partials or nullptr
+    const PcgScalars* sc;                         // QUPDATE: skip inactive instances, iteration count
+    const double* rz_cur; const double* rz_prev; const double* rzo;   // QUPDATE beta sources
+    int n_rz, n_rzo, flex;
+};
+mofem_status launch_apply(int K, int nt, bool fp64, int mode, const ApplyArgs& a, int batch, cudaStream_t st);
+int apply_rows_per_cta(int K);
+
+// ---- BLAS-1 / control kernels (blas1.cu) ----------------------------------
+mofem_status launch_convert(const void* src, int src_kind, long long s_bs, int s_ld,
+                            void* dst, int dst_kind, long long d_bs, int d_ld,
+                            int rows, int cols, int batch, cudaStream_t st);   // kinds: 0 f32, 1 f64, 2 bf16
+mofem_status launch_transpose64(const double* src, long long s_bs, double* dst, long long d_bs,
+                                int n, int ld, int batch, cudaStream_t st);
+mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs,
+                                   int d_ld, int n, int batch, cudaStream_t st);
+mofem_status launch_hadamard_div64(double* W, long long bs, int ld, int q, const double* lam,
+                                   long long lam_bs, const double* mu, int batch, cudaStream_t st);
+mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const float* dU, long long d_bs,
+                                int d_ld, int q, int batch, cudaStream_t st);
+
+// ---- tensor-core GEMMs (gemm_tc.cu) ------------------------------------------
+// Four GEMMs of the reduced-approach preconditioner on the operand already in
+// plan.Rop; writes Z (FP32) and, if rz_partial, the <R, Z> partials (R32 = R in FP32).
+mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st);
+mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z,
+                        int z_ld, long long z_bs, double* rz_partial, const PcgScalars* sc, cudaStream_t st);
+int tc_rz_ctas(const mofem_ctx* c);
+
+// ---- solver (solver.cu) ------------------------------------------------------
+mofem_status solver_init(mofem_ctx* c, cudaStream_t st);
+mofem_status op_apply(mofem_ctx* c, bool fp64, const void* X, long long x_bs, int x_ld, void* Y, long long y_bs,
+                      int y_ld, double* partial, cudaStream_t st);
+mofem_status op_rhs(mofem_ctx* c, const double* F, double* Bout, long long b_bs, int b_ld, cudaStream_t st);
+mofem_status precond64(mofem_ctx* c, const double* R, long long r_bs, int r_ld, double* Z, long long z_bs,
+                       int z_ld, cudaStream_t st);
+mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs, int r_ld, float* Z,
+                        long long z_bs, int z_ld, double* rz_partial, const PcgScalars* sc, cudaStream_t st);
+mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rtol, int max_iter,
+                            mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
+mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
+                        mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
+void mofem_free_extra(mofem_ctx* c);

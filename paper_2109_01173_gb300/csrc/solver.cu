@@ -1,0 +1,530 @@
+// MO-PCG driver (Sec. 5, Eqs. laplace_xnormal_pcg and
+// laplace_xnormal_pcg_iteration, standard PCG recurrences; Sec. 6 for the IMEX
+// step) on one GPU.
+//
+// One PCG iteration is a fixed sequence of kernels on device-resident data:
+//   apply  : Q = Z + beta Q_prev (fused prologue), L(Q), partial <Q, L(Q)>
+//   update : alpha = <R,Z>/<Q,L(Q)>, U += alpha Q, R -= alpha L(Q), partials
+//            ||R||^2 and <R_new, Z_old>, BF16 copy of R for the GEMMs
+//   control: convergence / breakdown / non-finite tests, sets the graph
+//            conditional
+//   precond: Z = P^{-1}(R) (four tcgen05 GEMMs, or four DGEMMs in the FP64
+//            form), partial <R, Z>
+// Two iterations (ping-pong search-direction buffers) form the body of a CUDA
+// graph conditional WHILE node, so the whole inner solve runs without host
+// round trips.  beta is the flexible (Polak-Ribiere) choice in the mixed form,
+// where the rounded preconditioner is not exactly symmetric, and the
+// Fletcher-Reeves choice in the FP64 form.
+//
+// Mixed form: classical iterative refinement: R64 = B - L64(U64) in FP64, an
+// inner FP32 solve of L(dU) = R64 to a relative reduction eta, U64 += dU,
+// until ||B - L64(U64)||_F <= rtol ||B||_F.
+#include "internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* R, const void* Q, const void* LQ,
+                               const void* Zold, void* Rop, int rop_kind, const double* rz_partials, int flex,
+                               cudaStream_t st);
+mofem_status launch_pcg_control(const mofem_ctx* c, int max_iter, bool fixed, const cudaGraphConditionalHandle* cond,
+                                cudaStream_t st);
+mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
+                             cudaStream_t st);
+mofem_status launch_dot_partials(const void* A, const void* B, bool fp64, long long bs, long long n, int batch,
+                                 double* part, int nblk, cudaStream_t st);
+mofem_status launch_imex_rhs(const double* Un, const double* Fn, double* Fbar, int n, int q, int off, double gam,
+                             double tau, int batch, cudaStream_t st);
+
+namespace {
+
+constexpr int W32_U = 0, W32_R = 1, W32_Z = 2, W32_QA = 3, W32_QB = 4, W32_LQ = 5, W32_N = 6;
+constexpr int W64_U = 0, W64_R = 1, W64_Z = 2, W64_QA = 3, W64_QB = 4, W64_LQ = 5, W64_T1 = 6, W64_T2 = 7, W64_N = 8;
+
+size_t per(const mofem_ctx* c) { return (size_t)c->q * c->ld; }
+float* w32(const mofem_ctx* c, int i) { return c->w32 + per(c) * c->batch * i; }
+double* w64(const mofem_ctx* c, int i) { return c->w64 + per(c) * c->batch * i; }
+
+struct Extra {   // per-handle scratch not in the public struct
+    double* res_part = nullptr;   // [batch][n_apply] residual partials
+    double* bb_part = nullptr;    // [batch][n_rz] partials for ||B||^2
+    double* ref2 = nullptr;       // [batch] reference norm^2 of the stop test
+    double* rz_slots[2] = {nullptr, nullptr};
+    void* cublas_ws = nullptr;
+    cudaStream_t cap = nullptr;
+};
+
+}  // namespace
+
+// Extra scratch lives in a side table keyed by handle (keeps mofem_ctx POD-like).
+#include <map>
+static std::map<const mofem_ctx*, Extra>& extras() {
+    static std::map<const mofem_ctx*, Extra> m;
+    return m;
+}
+
+static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
+    Extra& e = extras()[c];
+    if (c->d_part) return MOFEM_OK;
+    const int B = c->batch;
+    const int TA = apply_rows_per_cta(c->K);
+    c->part.n_apply = ((c->q + 127) / 128) * ((c->q + TA - 1) / TA);
+    long long nvec = (long long)per(c) / 4;
+    c->part.n_upd = (int)std::max(1LL, std::min(128LL, (nvec + 255) / 256));
+    c->part.n_rz = tc_rz_ctas(c);
+    const size_t n_total = (size_t)B * (c->part.n_apply * 2 + c->part.n_upd * 2 + c->part.n_rz * 3) + B;
+    MOFEM_CUDA_TRY(cudaMalloc(&c->d_part, n_total * sizeof(double)));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_part, 0, n_total * sizeof(double), st));
+    double* p = c->d_part;
+    c->part.qlq = p; p += (size_t)B * c->part.n_apply;
+    e.res_part = p; p += (size_t)B * c->part.n_apply;
+    c->part.rr = p; p += (size_t)B * c->part.n_upd;
+    c->part.rzo = p; p += (size_t)B * c->part.n_upd;
+    e.rz_slots[0] = p; p += (size_t)B * c->part.n_rz;
+    e.rz_slots[1] = p; p += (size_t)B * c->part.n_rz;
+    e.bb_part = p; p += (size_t)B * c->part.n_rz;
+    e.ref2 = p;
+    c->part.rz = e.rz_slots[0];
+    MOFEM_CUDA_TRY(cudaMalloc(&c->d_sc, sizeof(PcgScalars) * B));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_sc, 0, sizeof(PcgScalars) * B, st));
+    MOFEM_CUDA_TRY(cudaMalloc(&c->d_status, sizeof(int)));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+    MOFEM_CUDA_TRY(cudaMalloc(&c->Bm64, per(c) * B * sizeof(double)));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->Bm64, 0, per(c) * B * sizeof(double), st));
+    MOFEM_CUDA_TRY(cudaMalloc(&c->R64, per(c) * B * sizeof(double)));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->R64, 0, per(c) * B * sizeof(double), st));
+    MOFEM_CUDA_TRY(cudaStreamCreateWithFlags(&e.cap, cudaStreamNonBlocking));
+    MOFEM_CUDA_TRY(cudaEventCreate(&c->ev0));
+    MOFEM_CUDA_TRY(cudaEventCreate(&c->ev1));
+    return MOFEM_OK;
+}
+
+static mofem_status ensure_w32(mofem_ctx* c, cudaStream_t st) {
+    if (c->w32) return MOFEM_OK;
+    size_t bytes = per(c) * c->batch * W32_N * sizeof(float);
+    MOFEM_CUDA_TRY(cudaMalloc(&c->w32, bytes));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->w32, 0, bytes, st));
+    return MOFEM_OK;
+}
+
+static mofem_status ensure_w64(mofem_ctx* c, cudaStream_t st) {
+    Extra& e = extras()[c];
+    if (c->w64) return MOFEM_OK;
+    size_t bytes = per(c) * c->batch * W64_N * sizeof(double);
+    MOFEM_CUDA_TRY(cudaMalloc(&c->w64, bytes));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->w64, 0, bytes, st));
+    if (!c->cublas) {
+        if (cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) return MOFEM_ERR_CUDA;
+        const size_t ws = 32u << 20;
+        MOFEM_CUDA_TRY(cudaMalloc(&e.cublas_ws, ws));
+        if (cublasSetWorkspace(c->cublas, e.cublas_ws, ws) != CUBLAS_STATUS_SUCCESS) return MOFEM_ERR_CUDA;
+        cublasSetMathMode(c->cublas, CUBLAS_DEFAULT_MATH);
+    }
+    return MOFEM_OK;
+}
+
+void mofem_free_extra(mofem_ctx* c) {
+    auto it = extras().find(c);
+    if (it == extras().end()) return;
+    cudaFree(it->second.cublas_ws);
+    if (it->second.cap) cudaStreamDestroy(it->second.cap);
+    extras().erase(it);
+}
+
+// ---- single operations ---------------------------------------------------------
+static ApplyArgs apply_args_square(const mofem_ctx* c, bool fp64) {
+    ApplyArgs a{};
+    a.S = fp64 ? (const void*)c->S64 : (const void*)c->S32;
+    a.s_bs = (long long)c->NT * c->P * c->q;
+    a.T = fp64 ? (const void*)c->T64 : (const void*)c->T32;
+    a.rows_in = a.cols_in = a.rows_out = a.cols_out = c->q;
+    a.off = 0;
+    return a;
+}
+
+mofem_status op_apply(mofem_ctx* c, bool fp64, const void* X, long long x_bs, int x_ld, void* Y, long long y_bs,
+                      int y_ld, double* partial, cudaStream_t st) {
+    ApplyArgs a = apply_args_square(c, fp64);
+    a.X = X; a.x_bs = x_bs; a.x_ld = x_ld;
+    a.Y = Y; a.y_bs = y_bs; a.y_ld = y_ld;
+    a.partial = partial;
+    return launch_apply(c->K, c->NT, fp64, APPLY_PLAIN, a, c->batch, st);
+}
+
+mofem_status op_rhs(mofem_ctx* c, const double* F, double* Bout, long long b_bs, int b_ld, cudaStream_t st) {
+    ApplyArgs a{};
+    a.X = F; a.x_bs = (long long)c->n * c->n; a.x_ld = c->n;
+    a.Y = Bout; a.y_bs = b_bs; a.y_ld = b_ld;
+    a.S = c->Sr64; a.s_bs = (long long)c->P * c->q; a.T = c->Tr64;
+    a.rows_in = a.cols_in = c->n;
+    a.rows_out = a.cols_out = c->q;
+    a.off = c->off;
+    return launch_apply(c->K, 1, true, APPLY_PLAIN, a, c->batch, st);
+}
+
+static mofem_status op_residual64(mofem_ctx* c, const double* U, long long u_bs, int u_ld, double* R, double* part,
+                                  cudaStream_t st) {
+    ApplyArgs a = apply_args_square(c, true);
+    a.X = U; a.x_bs = u_bs; a.x_ld = u_ld;
+    a.Y = R; a.y_bs = (long long)per(c); a.y_ld = c->ld;
+    a.Bm = c->Bm64;
+    a.partial = part;
+    return launch_apply(c->K, c->NT, true, APPLY_RESIDUAL, a, c->batch, st);
+}
+
+// FP64 reduced-approach preconditioner through cuBLAS (row-major data viewed as
+// column-major transposes): X1 = R Q2, T2 = Q1^T X1, W = T2 ./ (lam + mu), Y = Q1 W, Z = Y Q2^T.
+mofem_status precond64(mofem_ctx* c, const double* R, long long r_bs, int r_ld, double* Z, long long z_bs, int z_ld,
+                       cudaStream_t st) {
+    MOFEM_TRY(ensure_w64(c, st));
+    const int q = c->q, ld = c->ld;
+    const double one = 1.0, zero = 0.0;
+    cublasSetStream(c->cublas, st);
+    double* X1 = w64(c, W64_T1);
+    double* T2 = w64(c, W64_T2);
+    for (int i = 0; i < c->batch; ++i) {
+        const double* Ri = R + r_bs * i;
+        double* Zi = Z + z_bs * i;
+        const double* Q1 = c->Q1_64 + per(c) * i;
+        double* x1 = X1 + per(c) * i;
+        double* t2 = T2 + per(c) * i;
+        cublasStatus_t s1 = cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, q, q, q, &one, c->Q2_64, ld, Ri, r_ld,
+                                        &zero, x1, ld);
+        cublasStatus_t s2 = cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, q, q, q, &one, x1, ld, Q1, ld, &zero, t2, ld);
+        if (s1 != CUBLAS_STATUS_SUCCESS || s2 != CUBLAS_STATUS_SUCCESS) return MOFEM_ERR_CUDA;
+    }
+    MOFEM_TRY(launch_hadamard_div64(T2, per(c), ld, q, c->lam64, ld, c->mu64, c->batch, st));
+    for (int i = 0; i < c->batch; ++i) {
+        double* Zi = Z + z_bs * i;
+        const double* Q1 = c->Q1_64 + per(c) * i;
+        double* x1 = X1 + per(c) * i;   // reuse as Y
+        double* t2 = T2 + per(c) * i;
+        cublasStatus_t s3 = cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_N, q, q, q, &one, t2, ld, Q1, ld, &zero, x1, ld);
+        cublasStatus_t s4 = cublasDgemm(c->cublas, CUBLAS_OP_T, CUBLAS_OP_N, q, q, q, &one, c->Q2_64, ld, x1, ld, &zero,
+                                        Zi, z_ld);
+        if (s3 != CUBLAS_STATUS_SUCCESS || s4 != CUBLAS_STATUS_SUCCESS) return MOFEM_ERR_CUDA;
+    }
+    return MOFEM_OK;
+}
+
+// Tensor-core preconditioner on a user (or internal) FP32 matrix R.
+mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs, int r_ld, float* Z, long long z_bs,
+                        int z_ld, double* rz_partial, const PcgScalars* sc, cudaStream_t st) {
+    MOFEM_TRY(tc_prepare(c, which, st));
+    TcPlan& p = c->tc[which];
+    MOFEM_TRY(launch_convert(R, 0, r_bs, r_ld, p.Rop, which == 1 ? 2 : 0, (long long)per(c), c->ld, c->q, c->q,
+                             c->batch, st));
+    return tc_precond(c, which, R, r_bs, r_ld, Z, z_ld, z_bs, rz_partial, sc, st);
+}
+
+// ---- PCG iteration (captured) -----------------------------------------------------
+static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int max_iter, bool fixed,
+                                  const cudaGraphConditionalHandle* cond, cudaStream_t st) {
+    Extra& e = extras()[c];
+    const bool fp64 = prec == MOFEM_FP64;
+    const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
+    const long long bs = (long long)per(c);
+    void *U, *R, *Z, *Qn, *Qp, *LQ;
+    if (fp64) {
+        U = w64(c, W64_U); R = w64(c, W64_R); Z = w64(c, W64_Z);
+        Qn = w64(c, s % 2 ? W64_QB : W64_QA); Qp = w64(c, s % 2 ? W64_QA : W64_QB); LQ = w64(c, W64_LQ);
+    } else {
+        U = w32(c, W32_U); R = w32(c, W32_R); Z = w32(c, W32_Z);
+        Qn = w32(c, s % 2 ? W32_QB : W32_QA); Qp = w32(c, s % 2 ? W32_QA : W32_QB); LQ = w32(c, W32_LQ);
+    }
+    double* rz_cur = e.rz_slots[s % 2];
+    double* rz_next = e.rz_slots[(s + 1) % 2];
+    // 1) Q = Z + beta Q_prev ; LQ = L(Q) ; <Q, LQ>
+    ApplyArgs a = apply_args_square(c, fp64);
+    a.X = Qp; a.x_bs = bs; a.x_ld = c->ld;
+    a.Z = Z; a.Xnew = Qn;
+    a.Y = LQ; a.y_bs = bs; a.y_ld = c->ld;
+    a.partial = c->part.qlq;
+    a.sc = c->d_sc;
+    a.rz_cur = rz_cur; a.rz_prev = rz_next; a.rzo = c->part.rzo;
+    a.n_rz = c->part.n_rz; a.n_rzo = c->part.n_upd;
+    a.flex = fp64 ? 0 : 1;
+    MOFEM_TRY(launch_apply(c->K, c->NT, fp64, APPLY_QUPDATE, a, c->batch, st));
+    // 2) alpha ; U += alpha Q ; R -= alpha LQ
+    MOFEM_TRY(launch_pcg_update(c, fp64, U, R, Qn, LQ, Z, fp64 ? nullptr : c->tc[which].Rop,
+                                (!fp64 && which == 1) ? 1 : 0, rz_cur, fp64 ? 0 : 1, st));
+    // 3) convergence
+    MOFEM_TRY(launch_pcg_control(c, max_iter, fixed, cond, st));
+    // 4) Z = P^{-1}(R), <R, Z>
+    if (fp64) {
+        MOFEM_TRY(precond64(c, (const double*)R, bs, c->ld, (double*)Z, bs, c->ld, st));
+        MOFEM_TRY(launch_dot_partials(R, Z, true, bs, bs, c->batch, rz_next, c->part.n_rz, st));
+    } else {
+        if (which == 0) {   // TF32 reads R directly: refresh the operand copy (FP32 -> FP32)
+            MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[0].Rop, 0, bs, c->ld, c->q, c->q, c->batch, st));
+        }
+        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, rz_next, c->d_sc, st));
+    }
+    return MOFEM_OK;
+}
+
+// Build (once per precision) the graph: WHILE(cond) { iteration(0); iteration(1) }.
+static mofem_status build_loop_graph(mofem_ctx* c, mofem_precision prec, int max_iter, bool fixed) {
+    Extra& e = extras()[c];
+    const int pi = (int)prec;
+    if (c->loop_graph[pi] && c->it_graph_max_iter[pi] == (fixed ? -max_iter : max_iter)) return MOFEM_OK;
+    if (c->loop_graph[pi]) {
+        cudaGraphExecDestroy(c->loop_graph[pi]);
+        c->loop_graph[pi] = nullptr;
+    }
+    cudaGraph_t g;
+    MOFEM_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    MOFEM_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    MOFEM_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    MOFEM_CUDA_TRY(cudaStreamBeginCaptureToGraph(e.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    mofem_status s0 = pcg_iteration(c, prec, 0, max_iter, fixed, &h, e.cap);
+    mofem_status s1 = s0 == MOFEM_OK ? pcg_iteration(c, prec, 1, max_iter, fixed, &h, e.cap) : s0;
+    cudaGraph_t out = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e.cap, &out);
+    if (s1 != MOFEM_OK) {
+        cudaGraphDestroy(g);
+        return s1;
+    }
+    MOFEM_CUDA_TRY(ce);
+    cudaGraphExec_t ex;
+    MOFEM_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    c->loop_graph[pi] = ex;
+    c->it_graph_max_iter[pi] = fixed ? -max_iter : max_iter;
+    return MOFEM_OK;
+}
+
+// Host-driven alternative (MOFEM_FLAG_HOST_LOOP): one graph of two iterations
+// launched until every instance is inactive.
+static mofem_status build_step_graph(mofem_ctx* c, mofem_precision prec, int max_iter, bool fixed) {
+    Extra& e = extras()[c];
+    const int pi = (int)prec;
+    if (c->it_graph[pi] && c->it_graph_max_iter[pi] == (fixed ? -max_iter : max_iter)) return MOFEM_OK;
+    if (c->it_graph[pi]) {
+        cudaGraphExecDestroy(c->it_graph[pi]);
+        c->it_graph[pi] = nullptr;
+    }
+    MOFEM_CUDA_TRY(cudaStreamBeginCapture(e.cap, cudaStreamCaptureModeRelaxed));
+    mofem_status s0 = pcg_iteration(c, prec, 0, max_iter, fixed, nullptr, e.cap);
+    mofem_status s1 = s0 == MOFEM_OK ? pcg_iteration(c, prec, 1, max_iter, fixed, nullptr, e.cap) : s0;
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e.cap, &g);
+    if (s1 != MOFEM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s1;
+    }
+    MOFEM_CUDA_TRY(ce);
+    cudaGraphExec_t ex;
+    MOFEM_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    c->it_graph[pi] = ex;
+    c->it_graph_max_iter[pi] = fixed ? -max_iter : max_iter;
+    return MOFEM_OK;
+}
+
+static mofem_status read_scalars(mofem_ctx* c, std::vector<PcgScalars>& sc, cudaStream_t st) {
+    sc.resize(c->batch);
+    MOFEM_CUDA_TRY(cudaMemcpyAsync(sc.data(), c->d_sc, sizeof(PcgScalars) * c->batch, cudaMemcpyDeviceToHost, st));
+    MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    return MOFEM_OK;
+}
+
+// Fixed-order host sum of per-instance partials (deterministic).
+static mofem_status sum_partials(const double* d, int nper, int batch, std::vector<double>& out, cudaStream_t st) {
+    std::vector<double> h((size_t)nper * batch);
+    MOFEM_CUDA_TRY(cudaMemcpyAsync(h.data(), d, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    out.assign(batch, 0.0);
+    for (int i = 0; i < batch; ++i)
+        for (int j = 0; j < nper; ++j) out[i] += h[(size_t)i * nper + j];
+    return MOFEM_OK;
+}
+
+// Run one inner solve: R (working precision) holds the start residual, U = 0 or a
+// guess already in the U buffer.  Stops at ||R|| <= rtol * sqrt(ref2) (ref2 = ||R0||^2 when null).
+static mofem_status run_inner(mofem_ctx* c, mofem_precision prec, int max_iter, bool fixed, const double* ref2_dev,
+                              double rtol, cudaStream_t st) {
+    Extra& e = extras()[c];
+    const bool fp64 = prec == MOFEM_FP64;
+    const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
+    const long long bs = (long long)per(c);
+    void* R = fp64 ? (void*)w64(c, W64_R) : (void*)w32(c, W32_R);
+    void* Z = fp64 ? (void*)w64(c, W64_Z) : (void*)w32(c, W32_Z);
+    void* Qp = fp64 ? (void*)w64(c, W64_QB) : (void*)w32(c, W32_QB);
+    const size_t esz = fp64 ? 8 : 4;
+    MOFEM_CUDA_TRY(cudaMemsetAsync(Qp, 0, bs * c->batch * esz, st));
+    // ||R0||^2 partials (reuse the update's rr slots) -> init
+    MOFEM_TRY(launch_dot_partials(R, R, fp64, bs, bs, c->batch, c->part.rr, c->part.n_upd, st));
+    MOFEM_TRY(launch_pcg_init(c, c->part.rr, c->part.n_upd, ref2_dev, rtol, st));
+    // Z0 = P^{-1}(R0) and <R0, Z0> into rz slot 0
+    if (fp64) {
+        MOFEM_TRY(precond64(c, (const double*)R, bs, c->ld, (double*)Z, bs, c->ld, st));
+        MOFEM_TRY(launch_dot_partials(R, Z, true, bs, bs, c->batch, e.rz_slots[0], c->part.n_rz, st));
+    } else {
+        MOFEM_TRY(tc_prepare(c, which, st));
+        MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[which].Rop, which == 1 ? 2 : 0, bs, c->ld, c->q, c->q,
+                                 c->batch, st));
+        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st));
+    }
+    const int pi = (int)prec;
+    if (c->opts.flags & MOFEM_FLAG_HOST_LOOP) {
+        MOFEM_TRY(build_step_graph(c, prec, max_iter, fixed));
+        std::vector<PcgScalars> sc;
+        for (int guard = 0; guard < max_iter + 2; guard += 2) {
+            MOFEM_CUDA_TRY(cudaGraphLaunch(c->it_graph[pi], st));
+            MOFEM_TRY(read_scalars(c, sc, st));
+            bool any = false;
+            for (auto& s : sc) any = any || s.active;
+            if (!any) break;
+        }
+    } else {
+        MOFEM_TRY(build_loop_graph(c, prec, max_iter, fixed));
+        MOFEM_CUDA_TRY(cudaGraphLaunch(c->loop_graph[pi], st));
+    }
+    return MOFEM_OK;
+}
+
+static mofem_status finish_info(mofem_ctx* c, mofem_solve_info* info, mofem_status st_code, int iters, int outer,
+                                double rel, float ms) {
+    if (info) {
+        info->status = st_code;
+        info->iterations = iters;
+        info->outer_steps = outer;
+        info->batch = c->batch;
+        info->rel_residual = rel;
+        info->ms_total = ms;
+    }
+    return st_code;
+}
+
+// Core solve on Bm64 (already formed).  U: q x q per instance, ld u_ld, FP64,
+// in/out.  Stop: ||B - L(U)|| <= rtol * ref, ref = ||B|| (ref_is_r0 = 0) or the
+// initial residual norm (ref_is_r0 = 1, IMEX rule).
+static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld, double rtol, int max_iter,
+                               mofem_precision prec, int ref_is_r0, mofem_solve_info* info, cudaStream_t st) {
+    Extra& e = extras()[c];
+    const int B = c->batch, q = c->q, ld = c->ld;
+    const long long bs = (long long)per(c);
+    const bool fixed = (c->opts.flags & MOFEM_FLAG_FIXED_ITERS) != 0;
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+    MOFEM_CUDA_TRY(cudaEventRecord(c->ev0, st));
+    // reference norms
+    std::vector<double> bb, rr;
+    MOFEM_TRY(launch_dot_partials(c->Bm64, c->Bm64, true, bs, bs, B, e.bb_part, c->part.n_rz, st));
+    MOFEM_TRY(sum_partials(e.bb_part, c->part.n_rz, B, bb, st));
+    MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
+    MOFEM_TRY(sum_partials(e.res_part, c->part.n_apply, B, rr, st));
+    std::vector<double> ref2(B);
+    for (int i = 0; i < B; ++i) ref2[i] = ref_is_r0 ? rr[i] : bb[i];
+    int total_it = 0, outer = 0;
+    mofem_status code = MOFEM_OK;
+    std::vector<PcgScalars> sc;
+    auto rel_max = [&](const std::vector<double>& r) {
+        double m = 0.0;
+        for (int i = 0; i < B; ++i) {
+            double v = ref2[i] > 0 ? std::sqrt(r[i] / ref2[i]) : (r[i] > 0 ? INFINITY : 0.0);
+            if (!(v <= m)) m = v;   // NaN propagates
+        }
+        return m;
+    };
+    double rel = rel_max(rr);
+    if (prec == MOFEM_FP64) {
+        MOFEM_TRY(ensure_w64(c, st));
+        // U64 <- U (internal layout), R <- R64
+        MOFEM_TRY(launch_convert(U, 1, u_bs, u_ld, w64(c, W64_U), 1, bs, ld, q, q, B, st));
+        MOFEM_CUDA_TRY(cudaMemcpyAsync(w64(c, W64_R), c->R64, sizeof(double) * bs * B, cudaMemcpyDeviceToDevice, st));
+        // the stop test is relative to sqrt(ref2): pass ref2 to the init kernel
+        MOFEM_CUDA_TRY(cudaMemcpyAsync(e.ref2, ref2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+        if (rel > rtol) {
+            MOFEM_TRY(run_inner(c, prec, max_iter, fixed, e.ref2, rtol, st));
+            MOFEM_TRY(read_scalars(c, sc, st));
+            for (auto& s : sc) total_it = std::max(total_it, s.iters);
+        }
+        MOFEM_TRY(launch_convert(w64(c, W64_U), 1, bs, ld, U, 1, u_bs, u_ld, q, q, B, st));
+        MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
+        MOFEM_TRY(sum_partials(e.res_part, c->part.n_apply, B, rr, st));
+        rel = rel_max(rr);
+        outer = 1;
+    } else {
+        MOFEM_TRY(ensure_w32(c, st));
+        const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
+        MOFEM_TRY(tc_prepare(c, which, st));
+        const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 20;
+        const double eta0 = c->opts.inner_rtol > 0 ? c->opts.inner_rtol : 1e-4;
+        while (!(rel <= rtol) && outer < max_outer && std::isfinite(rel)) {
+            // inner tolerance: no further than needed for this step
+            double eta = std::max(eta0, 0.3 * rtol / rel);
+            if (eta >= 1.0) eta = 0.5;
+            // R32 <- R64 ; converged instances get R = 0 (inactive)
+            MOFEM_TRY(launch_convert(c->R64, 1, bs, ld, w32(c, W32_R), 0, bs, ld, q, q, B, st));
+            for (int i = 0; i < B; ++i) {
+                double ri = ref2[i] > 0 ? std::sqrt(rr[i] / ref2[i]) : 0.0;
+                if (ri <= rtol) MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_R) + bs * i, 0, sizeof(float) * bs, st));
+            }
+            MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_U), 0, sizeof(float) * bs * B, st));
+            MOFEM_TRY(run_inner(c, prec, max_iter, fixed, nullptr, eta, st));
+            MOFEM_TRY(launch_axpy_into64(U, u_bs, u_ld, w32(c, W32_U), bs, ld, q, B, st));
+            MOFEM_TRY(read_scalars(c, sc, st));
+            int it = 0;
+            for (auto& s : sc) it = std::max(it, s.iters);
+            total_it += it;
+            ++outer;
+            MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
+            MOFEM_TRY(sum_partials(e.res_part, c->part.n_apply, B, rr, st));
+            rel = rel_max(rr);
+            if (fixed) break;
+        }
+    }
+    MOFEM_CUDA_TRY(cudaEventRecord(c->ev1, st));
+    MOFEM_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    int dev_status = 0;
+    MOFEM_CUDA_TRY(cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    MOFEM_TRY(read_scalars(c, sc, st));
+    int sc_status = 0;
+    for (auto& s : sc) sc_status |= s.status;
+    dev_status |= sc_status;
+    if (dev_status & DEV_ERR_TIMEOUT) code = MOFEM_ERR_TIMEOUT;
+    else if ((dev_status & DEV_ERR_NONFINITE) || !std::isfinite(rel)) code = MOFEM_ERR_NONFINITE;
+    else if (dev_status & DEV_ERR_BREAKDOWN && !(rel <= rtol)) code = MOFEM_ERR_BREAKDOWN;
+    else if (!(rel <= rtol) && !fixed) code = MOFEM_ERR_NOT_CONVERGED;
+    return finish_info(c, info, code, total_it, outer, rel, ms);
+}
+
+mofem_status solver_init(mofem_ctx* c, cudaStream_t st) { return ensure_common(c, st); }
+
+mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rtol, int max_iter, mofem_precision prec,
+                            mofem_solve_info* info, cudaStream_t st) {
+    MOFEM_TRY(ensure_common(c, st));
+    MOFEM_TRY(op_rhs(c, F, c->Bm64, (long long)per(c), c->ld, st));
+    return solve_core(c, U, (long long)c->q * c->q, c->q, rtol, max_iter, prec, 0, info, st);
+}
+
+mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
+                        mofem_precision prec, mofem_solve_info* info, cudaStream_t st) {
+    MOFEM_TRY(ensure_common(c, st));
+    const double gam = c->gamma[0];
+    double* Fbar = nullptr;
+    MOFEM_CUDA_TRY(cudaMallocAsync((void**)&Fbar, sizeof(double) * (size_t)c->n * c->n * c->batch, st));
+    mofem_status s = launch_imex_rhs(Un, Fn, Fbar, c->n, c->q, c->off, gam, tau, c->batch, st);
+    if (s == MOFEM_OK) s = op_rhs(c, Fbar, c->Bm64, (long long)per(c), c->ld, st);
+    cudaFreeAsync(Fbar, st);
+    MOFEM_TRY(s);
+    (void)d_u;
+    const long long qq = (long long)c->q * c->q;
+    if (Unp1 != Un)
+        MOFEM_CUDA_TRY(cudaMemcpyAsync(Unp1, Un, sizeof(double) * qq * c->batch, cudaMemcpyDeviceToDevice, st));
+    return solve_core(c, Unp1, qq, c->q, tau, 100000, prec, 1, info, st);
+}

@@ -1,0 +1,210 @@
+"""Thin Python binding of libmofem (ctypes): argument marshalling only.
+
+Every computation happens in libmofem's CUDA kernels behind the C ABI of
+``include/mofem.h``; this module converts torch tensors to raw device
+pointers and the current torch stream to a ``cudaStream_t``.  There is no CPU
+fallback: if ``libmofem.so`` is missing, importing the binding raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmofem.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_EIG, ERR_NONFINITE, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT, \
+    ERR_OOM, ERR_UNSUPPORTED = range(10)
+DIRICHLET, NEUMANN = 0, 1
+FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
+PENCIL_AVERAGED, PENCIL_DOMINANT = 0, 1
+FLAG_HOST_LOOP, FLAG_FIXED_ITERS = 1, 2
+
+PRECISIONS = {"fp64": FP64, "tf32": MIXED_TF32, "bf16": MIXED_BF16}
+
+_GFN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("g", _GFN), ("dg", _GFN), ("ctx", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("quad_points", ctypes.c_int), ("pencil", ctypes.c_int), ("max_outer", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("flags", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_steps", ctypes.c_int),
+                ("batch", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+
+class MofemError(RuntimeError):
+    def __init__(self, fn, code, lib):
+        name = lib.mofem_status_string(code).decode()
+        detail = lib.mofem_last_error().decode()
+        super().__init__(f"{fn} -> {name}" + (f": {detail}" if detail else ""))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmofem.so not built ({LIB_PATH}); run paper_2109_01173_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    c_int, c_double, vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "mofem_setup": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), vp, P(vp)],
+        "mofem_setup_batched": [c_int, P(Profile), P(Profile), c_int, c_int, P(c_double), c_int, P(Opts), vp, P(vp)],
+        "mofem_get_dims": [vp, P(c_int), P(c_int), P(c_int), P(c_int)],
+        "mofem_apply": [vp, vp, vp, c_int, c_int, vp],
+        "mofem_rhs": [vp, vp, vp, c_int, vp],
+        "mofem_precond": [vp, vp, vp, c_int, c_int, vp],
+        "mofem_pcg_solve": [vp, vp, vp, c_double, c_int, c_int, P(SolveInfo), vp],
+        "mofem_imex_step": [vp, c_double, c_double, vp, vp, vp, c_int, P(SolveInfo), vp],
+        "mofem_destroy": [vp],
+        "mofem_host_tables": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), P(c_int), P(c_int),
+                              vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = c_int
+    lib.mofem_status_string.argtypes = [c_int]
+    lib.mofem_status_string.restype = ctypes.c_char_p
+    lib.mofem_last_error.argtypes = []
+    lib.mofem_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+LIB = _load()
+
+EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply", "mofem_rhs", "mofem_precond",
+            "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
+            "mofem_host_tables"]
+
+
+def _check(fn, code):
+    if code != OK:
+        raise MofemError(fn, code, LIB)
+
+
+def make_profile(p):
+    """C profile from any object with vectorised ``g(x)`` and ``dg(x)`` methods.
+
+    Returns (struct, keepalive); keep ``keepalive`` referenced while the C side may call back.
+    """
+    g = _GFN(lambda x, ctx: float(p.g(x)))
+    dg = _GFN(lambda x, ctx: float(p.dg(x)))
+    prof = Profile(g, dg, None)
+    return prof, (g, dg)
+
+
+def make_opts(quad_points=0, pencil=PENCIL_AVERAGED, max_outer=0, inner_rtol=0.0, flags=0):
+    return Opts(quad_points, pencil, max_outer, inner_rtol, flags)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def host_tables(g1, g2, k, n, gamma, bc=DIRICHLET, opts=None):
+    """Setup tables computed on the host by the library (no GPU needed)."""
+    p1, k1 = make_profile(g1)
+    p2, k2 = make_profile(g2)
+    d = 1 if k == 0 else k
+    P = 2 * d + 1
+    q = n - 2 if bc == DIRICHLET else n
+    S = np.zeros((8, P, q))
+    T = np.zeros((8, P, q))
+    Sr = np.zeros((P, q))
+    Tr = np.zeros((P, q))
+    nt = ctypes.c_int()
+    qq = ctypes.c_int()
+    o = opts or make_opts()
+    code = LIB.mofem_host_tables(ctypes.byref(p1), ctypes.byref(p2), k, n, gamma, bc, ctypes.byref(o),
+                                 ctypes.byref(nt), ctypes.byref(qq), S.ctypes.data, T.ctypes.data,
+                                 Sr.ctypes.data, Tr.ctypes.data)
+    _check("mofem_host_tables", code)
+    return dict(n_terms=nt.value, q=qq.value, S=S[:nt.value], T=T[:nt.value], Srh=Sr, Trh=Tr, K=d)
+
+
+class Handle:
+    """One (possibly batched) MO-FEM problem living on the current CUDA device."""
+
+    def __init__(self, g1, g2, k, n, gamma, bc=DIRICHLET, opts=None):
+        g1 = g1 if isinstance(g1, (list, tuple)) else [g1]
+        g2 = g2 if isinstance(g2, (list, tuple)) else [g2]
+        gam = np.atleast_1d(np.asarray(gamma, dtype=np.float64))
+        B = max(len(g1), len(g2), gam.size)
+        if len(g1) == 1:
+            g1 = list(g1) * B
+        if len(g2) == 1:
+            g2 = list(g2) * B
+        if gam.size == 1:
+            gam = np.repeat(gam, B)
+        keep = []
+        arr1 = (Profile * B)()
+        arr2 = (Profile * B)()
+        for i in range(B):
+            arr1[i], k1 = make_profile(g1[i])
+            arr2[i], k2 = make_profile(g2[i])
+            keep += [k1, k2]
+        self._opts = opts or make_opts()
+        h = ctypes.c_void_p()
+        gam_c = (ctypes.c_double * B)(*gam.tolist())
+        code = LIB.mofem_setup_batched(B, arr1, arr2, k, n, gam_c, bc, ctypes.byref(self._opts), _stream(),
+                                       ctypes.byref(h))
+        _check("mofem_setup_batched", code)
+        self.h = h
+        self.batch, self.n, self.k, self.bc = B, n, k, bc
+        b, nn, q, nt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check("mofem_get_dims", LIB.mofem_get_dims(h, ctypes.byref(b), ctypes.byref(nn), ctypes.byref(q),
+                                                    ctypes.byref(nt)))
+        self.q, self.n_terms = q.value, nt.value
+
+    def apply(self, X, Y, precision="fp64", ld=None):
+        _check("mofem_apply", LIB.mofem_apply(self.h, _ptr(X), _ptr(Y), ld or X.shape[-1],
+                                              PRECISIONS[precision], _stream()))
+        return Y
+
+    def rhs(self, F, B, ld=None):
+        _check("mofem_rhs", LIB.mofem_rhs(self.h, _ptr(F), _ptr(B), ld or B.shape[-1], _stream()))
+        return B
+
+    def precond(self, R, Z, precision="fp64", ld=None):
+        _check("mofem_precond", LIB.mofem_precond(self.h, _ptr(R), _ptr(Z), ld or R.shape[-1],
+                                                  PRECISIONS[precision], _stream()))
+        return Z
+
+    def pcg_solve(self, F, U, rtol=1e-10, max_iter=500, precision="bf16", check=True):
+        info = SolveInfo()
+        code = LIB.mofem_pcg_solve(self.h, _ptr(F), _ptr(U), rtol, max_iter, PRECISIONS[precision],
+                                   ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_pcg_solve", code)
+        return info, code
+
+    def imex_step(self, d_u, tau, Un, Fn, Unp1, precision="bf16", check=True):
+        info = SolveInfo()
+        code = LIB.mofem_imex_step(self.h, d_u, tau, _ptr(Un), _ptr(Fn), _ptr(Unp1), PRECISIONS[precision],
+                                   ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_imex_step", code)
+        return info, code
+
+    def close(self):
+        if self.h:
+            LIB.mofem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
