@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark: MO-PCG solves/s and ms/iter, P2 with 2049 x 2049 nodes (q = 2047).
+
+Workload (per rank): B independent elliptic problems -Lap u + u = f on the
+x-normal domain {0 <= x <= 1, 0 <= y <= 1 + 0.25 sin(2 pi x)}, zero Dirichlet
+data, P2 elements with 2049 nodes per direction, f a seeded sum of 32 Fourier
+modes (seed = rank * B + i).  One step = one batched solve (right-hand side,
+FP64 true residuals, inner mixed-precision MO-PCG, refinement) of the B
+instances from U = 0 to ||B - L(U)||_F <= 1e-10 ||B||_F.  Setup (1D tables
+and the FP64 eigendecompositions) is done once before timing and reported
+separately.  Instances are independent: N ranks solve N * B problems with no
+collective on the data path (weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--precision bf16|tf32|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MO-PCG solves/s and ms/iter, P2 N=2049 (mixed vs FP64 GPU form, rel.err<=1e-8)"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mofem", choices=["mofem", "reference"])
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp64"])
+    ap.add_argument("--n", type=int, default=2049)
+    ap.add_argument("--k", type=int, default=2)
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=3, help="oracle MO-PCG iterations per reference sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def make_inputs(B, n, k, rank):
+    from paper_2109_01173_gb300.inputs import metric_instance
+    return [metric_instance(n=n, k=k, seed=rank * B + i) for i in range(B)]
+
+
+# ----------------------------------------------------------------------------------
+def oracle_sample(inst, iters):
+    """Time `iters` MO-PCG iterations of the FP64 oracle on one instance (setup excluded)."""
+    from oracle.operator import Problem, apply_terms, rhs
+    from oracle import pcg
+    t0 = time.perf_counter()
+    P = Problem(inst["g1"], inst["g2"], inst["k"], inst["n"], inst["gamma"])
+    terms = [(S, T) for S, T in P.terms() if abs(S).sum() > 0]
+    Pc = pcg.ReducedSylvester(*P.pencils())
+    B = rhs(P, inst["F"])
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    _, info = pcg.mo_pcg(lambda X: apply_terms(terms, X), Pc, B, rtol=1e-30, max_iter=iters)
+    t_it = (time.perf_counter() - t1) / max(info["iterations"], 1)
+    return t_setup, t_it
+
+
+def cpu_cores():
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(v):
+            return int(os.environ[v])
+    return os.cpu_count()
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    inst = make_inputs(1, a.n, a.k, 0)[0]
+    # iterations the method needs at this size (FP64 MO-PCG, same preconditioner)
+    iters_needed = 45
+    samples = []
+    t_setup = None
+    for s in range(a.warmup + a.steps):
+        ts, ti = oracle_sample(inst, a.ref_iters)
+        t_setup = ts
+        if s >= a.warmup:
+            samples.append(ti)
+    t_iter = statistics.median(samples)
+    value = 1.0 / (t_iter * iters_needed)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t_iter * a.ref_iters * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"P{a.k} elliptic, {a.n}x{a.n} nodes, q={a.n - 2}, curved domain 1+0.25sin(2pi x), "
+                               f"32-mode Fourier f", "global_batch": 1, "l2": "inputs larger than L2 (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"{a.ref_iters} oracle MO-PCG iterations per step (numpy/scipy FP64, reduced "
+                                   f"preconditioner, setup {t_setup:.1f}s excluded); solves/s = 1/(s_per_iter x "
+                                   f"{iters_needed} iterations)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "ms_per_iter": t_iter * 1e3,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------
+def run_mofem(a):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_2109_01173_gb300.mofem as mf
+    B, n, k = a.batch, a.n, a.k
+    insts = make_inputs(B, n, k, rank)
+    t0 = time.perf_counter()
+    h = mf.Handle([i["g1"] for i in insts], [i["g2"] for i in insts], k, n, [i["gamma"] for i in insts])
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    q = h.q
+    F = torch.tensor(np.stack([i["F"] for i in insts]), dtype=torch.float64, device="cuda")
+    U = torch.zeros((B, q, q), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(Ub, Fb, prec=a.precision, max_iter=500):
+        Ub.zero_()
+        info, code = h.pcg_solve(Fb, Ub, rtol=a.rtol, max_iter=max_iter, precision=prec, check=False)
+        if code != 0:
+            raise RuntimeError(f"pcg_solve status {code} (rel_residual {info.rel_residual:.3e}): "
+                               f"{mf.LIB.mofem_last_error().decode()}")
+        return info
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(a.warmup):
+        step(U, F)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, launches, rels = [], 0, []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(a.steps):
+        info = step(U, F)
+        iters.append(info.iterations)
+        launches += info.kernel_launches
+        rels.append(info.rel_residual)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed = float(t.item())
+    value = B * world * a.steps / elapsed
+    ms_step = elapsed / a.steps * 1e3
+    ms_iter = elapsed * 1e3 / max(sum(iters), 1)
+
+    # ---- end to end through the C ABI with host buffers ----------------------------
+    F_host = F.cpu().pin_memory()
+    U_host = torch.empty((B, q, q), dtype=torch.float64).pin_memory()
+    F_dev = torch.empty_like(F)
+    U_dev = torch.empty_like(U)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(a.steps):
+        F_dev.copy_(F_host, non_blocking=True)
+        step(U_dev, F_dev)
+        U_host.copy_(U_dev, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_elapsed = e0.elapsed_time(e1) / 1e3
+    t = torch.tensor([e2e_elapsed], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = B * world * a.steps / float(t.item())
+    err_e2e = float((U_host.cuda() - U).abs().max().item())
+
+    # ---- hot-kernel timing (CUDA events on the launching stream) ---------------------
+    peaks, peak_src = measured_peaks()
+    reps = 20
+
+    def time_kernel(kid, prec):
+        h.bench_kernel(kid, prec, 3)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        h.bench_kernel(kid, prec, reps)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / reps / 1e3
+
+    prec_k = a.precision if a.precision != "fp64" else "bf16"
+    t_gemm = [time_kernel(i, prec_k) for i in (1, 2, 3, 4)]
+    t_apply = time_kernel(0, prec_k)
+    t_upd = time_kernel(5, prec_k)
+    flops_gemm = 2.0 * B * q ** 3
+    gemm_tflops = [flops_gemm / t / 1e12 for t in t_gemm]
+    tg = statistics.mean(t_gemm)
+    peak_t = peaks["bf16_tflops"] if prec_k == "bf16" else peaks["bf16_tflops"] / 2.0
+    apply_bytes = 4.0 * B * q * q * 4      # read Q_prev, Z; write Q_new, L(Q)   (FP32)
+    upd_bytes = 30.0 * B * q * q          # read U,R,Q,LQ,Z_old; write U,R (FP32) and R (BF16)
+
+    # ---- FP64 form (same instances, same stopping rule) ------------------------------
+    fp64 = None
+    if not a.no_fp64_form and a.precision != "fp64":
+        U64 = torch.zeros_like(U)
+        torch.cuda.synchronize()
+        f0 = time.perf_counter()
+        info64 = step(U64, F, prec="fp64", max_iter=500)
+        f_el = time.perf_counter() - f0
+        diff = float(((U64 - U).norm() / U64.norm()).item())
+        fp64 = {"solves_per_s": B / f_el, "ms_per_step": f_el * 1e3, "iterations": info64.iterations,
+                "ms_per_iter": f_el * 1e3 / max(info64.iterations, 1), "rel_residual": info64.rel_residual,
+                "mixed_speedup": value / world / (B / f_el), "rel_diff_mixed_vs_fp64": diff}
+
+    # ---- CPU baseline: the oracle on a bounded sample ----------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        ts, ti = oracle_sample(insts[0], a.ref_iters)
+        fp64_iters = fp64["iterations"] if fp64 else 45
+        cpu = {"value": 1.0 / (ti * fp64_iters), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{a.ref_iters} FP64 oracle MO-PCG iterations on instance 0 (numpy/scipy, reduced "
+                         f"preconditioner; setup {ts:.1f}s excluded), {ti * 1e3:.0f} ms/iter; solves/s = "
+                         f"1/(s_per_iter x {fp64_iters} iterations of the FP64 GPU form)"}
+
+    h.close()
+    if rank != 0:
+        return 0
+    working_set_mb = B * (q * q * (6 * 4 + 8 * 2 + 3 * 8)) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16-gemm/f32-vec/f64-refine", "tf32": "tf32-gemm/f32-vec/f64-refine",
+                  "fp64": "f64"}[a.precision],
+        "data": "synthetic",
+        "config": {"workload": f"P{k} elliptic -Lap u + u = f, {n}x{n} nodes (q={q}), Dirichlet, domain "
+                               f"0<=y<=1+0.25sin(2pi x), 32-mode Fourier f, rtol {a.rtol:g}",
+                   "global_batch": B * world, "batch_per_gpu": B, "precision": a.precision,
+                   "l2": f"inputs larger than L2 (working set ~{working_set_mb:.0f} MB per GPU)",
+                   "parallelism": f"instances sharded over {world} GPU(s), no collective"},
+        "ms_per_iter": ms_iter, "iterations_per_solve": statistics.mean(iters),
+        "rel_residual_max": max(rels), "setup_s": setup_s,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": {"bound": "tensor", "kernel": "k_gemm<bf16> (preconditioner GEMM, mean of G1..G4)",
+                     "achieved": flops_gemm / tg / 1e12, "peak": peak_t, "unit": "TFLOP/s",
+                     "frac": flops_gemm / tg / 1e12 / peak_t, "traffic": None,
+                     "peak_source": f"{peak_src} bf16_tflops (burst)" + (" / 2 for TF32" if prec_k == "tf32" else ""),
+                     "per_gemm_us": [round(t * 1e6, 2) for t in t_gemm],
+                     "per_gemm_tflops": [round(x, 1) for x in gemm_tflops]},
+        "roofline_apply": {"bound": "hbm", "kernel": "k_apply<float,K=2,NT=5,QUPDATE>",
+                           "achieved": apply_bytes / t_apply / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": apply_bytes / t_apply / 1e9 / peaks["hbm_gbs"], "us": t_apply * 1e6},
+        "roofline_update": {"bound": "hbm", "kernel": "k_update<float,bf16>",
+                            "achieved": upd_bytes / t_upd / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": upd_bytes / t_upd / 1e9 / peaks["hbm_gbs"], "us": t_upd * 1e6},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * n * n * 8,
+                "d2h_bytes_per_step": B * q * q * 8, "max_abs_diff_vs_device_run": err_e2e},
+        "fp64_form": fp64,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_mofem(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -92,6 +92,7 @@ typedef struct {
     int batch;
     double rel_residual;   /* max over instances of ||B - L(U)||_F / ||B||_F, FP64, recomputed at exit */
     double ms_total;       /* device time of the solve (CUDA events) */
+    long long kernel_launches; /* libmofem kernels launched by the solve (graph nodes included) */
 } mofem_solve_info;
 
 typedef struct mofem_ctx* mofem_handle;
@@ -162,6 +163,17 @@ mofem_status mofem_pcg_solve(mofem_handle h, const double* F, double* U, double 
 mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const double* U_n,
                              const double* F_n, double* U_np1, mofem_precision prec,
                              mofem_solve_info* info, cudaStream_t stream);
+
+/* Benchmark hook (no counterpart in the paper): launch one hot kernel `reps`
+ * times on the handle's internal buffers, asynchronously on `stream`, so that
+ * a caller can time it with events on that stream.  kernel:
+ *   0 = FP32 operator apply with the fused search-direction update (PCG form),
+ *   1..4 = preconditioner GEMM G1..G4 (prec MIXED_TF32 or MIXED_BF16),
+ *   5 = FP32 PCG update (alpha, U, R, BF16 copy of R, partial sums),
+ *   6 = FP64 operator apply (true residual form).
+ * The buffers' contents are whatever the last solve left (timing only). */
+mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps,
+                                cudaStream_t stream);
 
 /* Release every buffer the handle owns. */
 mofem_status mofem_destroy(mofem_handle h);

@@ -37,3 +37,22 @@ mofem_status launch_apply_f64(int K, int nt, int mode, const ApplyArgs& a, int b
         default: return MOFEM_ERR_UNSUPPORTED;
     }
 }
+
+template <int K>
+static mofem_status pcg_nt_f64(int nt, const CUtensorMap& mZ, const CUtensorMap& mQ, const ApplyPcgArgs& a, int batch,
+                               cudaStream_t st) {
+    if (nt == 5) return launch_pcg_t<double, K, 5, true>(mZ, mQ, a, batch, st);
+    if (nt == 8) return launch_pcg_t<double, K, 8, true>(mZ, mQ, a, batch, st);
+    return MOFEM_ERR_UNSUPPORTED;
+}
+
+mofem_status launch_apply_pcg_f64(int K, int nt, const CUtensorMap& mZ, const CUtensorMap& mQ, const ApplyPcgArgs& a,
+                                  int batch, cudaStream_t st) {
+    switch (K) {
+        case 1: return pcg_nt_f64<1>(nt, mZ, mQ, a, batch, st);
+        case 2: return pcg_nt_f64<2>(nt, mZ, mQ, a, batch, st);
+        case 3: return pcg_nt_f64<3>(nt, mZ, mQ, a, batch, st);
+        case 4: return pcg_nt_f64<4>(nt, mZ, mQ, a, batch, st);
+        default: return MOFEM_ERR_UNSUPPORTED;
+    }
+}

@@ -1,18 +1,25 @@
-// BLAS-1 and control kernels of the device-resident MO-PCG (Sec. 5, Eq.
+// BLAS-1 kernels of the device-resident MO-PCG (Sec. 5, Eq.
 // laplace_xnormal_pcg_iteration with the standard PCG recurrences):
-//   alpha = <R, Z> / <Q, L(Q)>,  U += alpha Q,  R -= alpha L(Q)          (k_update)
-//   stop / breakdown / non-finite tests on FP64 sums                     (k_control)
+//   U += alpha Q,  R -= alpha L(Q), ||R||^2, <R_new, Z_old>        (k_update)
+//   <R, Z> and beta after the FP64 preconditioner                  (k_dot)
+//   start of an inner solve                                        (k_init)
 // plus the small helpers of setup and refinement (conversions, transposes,
-// Hadamard divide of the FP64 preconditioner, FP64 correction, norms).
+// Hadamard divide of the FP64 preconditioner, FP64 correction, IMEX RHS).
 //
-// Every Frobenius inner product is accumulated in FP64: each CTA writes one
-// partial and consumers sum the partials in a fixed order, so results are
-// bitwise reproducible run to run.  Internal q x q matrices are stored with a
-// padded leading dimension ld (multiple of 64) whose padding columns hold zeros,
-// so the elementwise kernels stream them as flat arrays of 16-byte vectors.
+// Scalars without host round trips: each reducing kernel writes one FP64
+// partial per CTA; the last CTA of each instance (atomic ticket after a
+// __threadfence) sums that instance's partials in a fixed order and updates
+// the instance's PcgScalars (alpha, convergence flags, beta), so results are
+// bitwise reproducible and no separate control kernel is needed.  The last CTA
+// of the whole update launch sets the CUDA-graph WHILE condition.
+//
+// Internal q x q matrices use a padded leading dimension ld (multiple of 64)
+// whose padding columns stay zero, so the elementwise kernels stream them as
+// flat arrays of 16-byte vectors.
 #include "internal.h"
 
 #include <cuda_bf16.h>
+#include <type_traits>
 
 namespace {
 
@@ -24,9 +31,10 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Fixed-order sum of n partials by one warp, read through L2 (written by other SMs).
 __device__ __forceinline__ double warp_sum_partials(const double* p, int n) {
     double s = 0.0;
-    for (int i = threadIdx.x & 31; i < n; i += 32) s += p[i];
+    for (int i = threadIdx.x & 31; i < n; i += 32) s += __ldcg(p + i);
     return warp_sum(s);
 }
 
@@ -48,12 +56,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 struct UpdArgs {
     void* U; void* R; const void* Q; const void* LQ; const void* Zold; void* Rop;
     long long bs;        // batch stride (elements) = q * ld
-    long long nvec;      // vectors per instance
-    const double* qlq; int n_qlq;
-    const double* rz; int n_rz;
+    long long nvec;      // 16-byte vectors per instance
     double* rr_part; double* rzo_part; int n_upd;
-    const PcgScalars* sc;
-    int flex;
+    PcgScalars* sc;
+    unsigned* counter;   // [batch] per-instance CTA tickets
+    unsigned* gcounter;  // tickets of the whole launch (graph conditional)
+    int use_sc, flex, max_iter, fixed;
+    cudaGraphConditionalHandle cond;
+    int has_cond;
 };
 
 template <typename T> struct Vec;
@@ -71,98 +81,129 @@ __device__ __forceinline__ double dot_v(const float4& a, const float4& b) {
 }
 __device__ __forceinline__ double dot_v(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
 
+__device__ __forceinline__ uint2 pack_bf16x4(const float4& r) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(r.x, r.y);
+    __nv_bfloat162 hi = __floats2bfloat162_rn(r.z, r.w);
+    uint2 pk;
+    pk.x = *reinterpret_cast<unsigned*>(&lo);
+    pk.y = *reinterpret_cast<unsigned*>(&hi);
+    return pk;
+}
+
+// One vector step of the update, accumulating ||R||^2 and <R_new, Z_old>.
+template <typename T, int ROP, typename V>
+__device__ __forceinline__ void upd_one(V& u, V& r, const V& qv, const V& lq, const V& zo, T alpha, int flex,
+                                        double& rr, double& rzo, uint2* rb) {
+    axpy_v(u, qv, alpha);
+    axpy_v(r, lq, -alpha);
+    rr += dot_v(r, r);
+    if (flex) rzo += dot_v(r, zo);
+    if constexpr (ROP == 1) *rb = pack_bf16x4(r);
+}
+
 // ROP: 0 = no operand copy, 1 = BF16 copy of R for the tensor-core GEMM.
+// alpha is read from the scalar state (set by the apply kernel's last CTA).
 template <typename T, int ROP>
 __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
     using V = typename Vec<T>::type;
+    static_assert(ROP == 0 || Vec<T>::W == 4, "BF16 operand copy is produced by the FP32 update only");
     __shared__ double sh[UPD_THREADS / 32];
-    __shared__ double alpha_s;
+    __shared__ int last_s, glast_s;
     const int inst = blockIdx.y;
-    if (g.sc && !g.sc[inst].active) return;
-    if (threadIdx.x < 32) {
-        double qlq = warp_sum_partials(g.qlq + (size_t)inst * g.n_qlq, g.n_qlq);
-        double rz = warp_sum_partials(g.rz + (size_t)inst * g.n_rz, g.n_rz);
-        double al = rz / qlq;
-        if (!(qlq > 0.0) || !isfinite(al)) al = 0.0;   // flagged by k_control
-        if (threadIdx.x == 0) alpha_s = al;
-    }
-    __syncthreads();
-    const T alpha = (T)alpha_s;
-    V* U = reinterpret_cast<V*>(reinterpret_cast<T*>(g.U) + (size_t)inst * g.bs);
-    V* R = reinterpret_cast<V*>(reinterpret_cast<T*>(g.R) + (size_t)inst * g.bs);
-    const V* Q = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Q) + (size_t)inst * g.bs);
-    const V* LQ = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.LQ) + (size_t)inst * g.bs);
-    const V* Zo = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Zold) + (size_t)inst * g.bs);
-    double rr = 0.0, rzo = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.nvec;
-         i += (long long)gridDim.x * blockDim.x) {
-        V u = U[i], r = R[i];
-        const V qv = Q[i], lq = LQ[i];
-        axpy_v(u, qv, alpha);
-        axpy_v(r, lq, -alpha);
-        U[i] = u;
-        R[i] = r;
-        rr += dot_v(r, r);
-        if (g.flex) rzo += dot_v(r, Zo[i]);
-        if constexpr (ROP == 1) {
-            static_assert(Vec<T>::W == 4, "BF16 operand copy is produced by the FP32 update only");
-            __nv_bfloat162 lo = __floats2bfloat162_rn(r.x, r.y);
-            __nv_bfloat162 hi = __floats2bfloat162_rn(r.z, r.w);
-            uint2 pk;
-            pk.x = *reinterpret_cast<unsigned*>(&lo);
-            pk.y = *reinterpret_cast<unsigned*>(&hi);
-            reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(g.Rop) + (size_t)inst * g.bs)[i] = pk;
-        }
-    }
-    double s1 = block_sum<UPD_THREADS>(rr, sh);
-    double s2 = block_sum<UPD_THREADS>(rzo, sh);
-    if (threadIdx.x == 0) {
-        g.rr_part[(size_t)inst * g.n_upd + blockIdx.x] = s1;
-        if (g.rzo_part) g.rzo_part[(size_t)inst * g.n_upd + blockIdx.x] = s2;
-    }
-}
-
-struct CtlArgs {
-    PcgScalars* sc;
-    const double* rr; int n_rr;
-    const double* qlq; int n_qlq;
-    int batch, max_iter, fixed;
-    cudaGraphConditionalHandle cond;
-    int has_cond;
-};
-
-__global__ void __launch_bounds__(256) k_control(CtlArgs g) {
-    __shared__ int any;
-    if (threadIdx.x == 0) any = 0;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int inst = warp; inst < g.batch; inst += nw) {
-        PcgScalars* s = g.sc + inst;
-        if (!s->active) continue;
-        double rr = warp_sum_partials(g.rr + (size_t)inst * g.n_rr, g.n_rr);
-        double qlq = warp_sum_partials(g.qlq + (size_t)inst * g.n_qlq, g.n_qlq);
-        if (lane == 0) {
-            int it = s->iters + 1;
-            s->iters = it;
-            s->rr = rr;
-            int act = 1;
-            if (!isfinite(rr) || !isfinite(qlq)) {
-                s->status |= DEV_ERR_NONFINITE;
-                act = 0;
-            } else if (!(qlq > 0.0)) {
-                s->status |= DEV_ERR_BREAKDOWN;
-                act = 0;
-            } else if (!g.fixed && rr <= s->tol2) {
-                act = 0;
-            } else if (it >= g.max_iter) {
-                act = 0;
+    PcgScalars* sc = g.sc + inst;
+    const bool active = !g.use_sc || sc->active;
+    if (active) {
+        const T alpha = g.use_sc ? (T)sc->alpha : (T)0.5;
+        V* U = reinterpret_cast<V*>(reinterpret_cast<T*>(g.U) + (size_t)inst * g.bs);
+        V* R = reinterpret_cast<V*>(reinterpret_cast<T*>(g.R) + (size_t)inst * g.bs);
+        const V* Q = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Q) + (size_t)inst * g.bs);
+        const V* LQ = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.LQ) + (size_t)inst * g.bs);
+        const V* Zo = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Zold) + (size_t)inst * g.bs);
+        uint2* Rb = nullptr;
+        if constexpr (ROP == 1)
+            Rb = reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(g.Rop) + (size_t)inst * g.bs);
+        double rr = 0.0, rzo = 0.0;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        constexpr int UNR = 4;   // independent 16-byte loads in flight per thread and array
+        long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        for (; i0 + (UNR - 1) * stride < g.nvec; i0 += UNR * stride) {
+            V u[UNR], r[UNR], qv[UNR], lq[UNR], zo[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const long long i = i0 + k * stride;
+                u[k] = U[i];
+                r[k] = R[i];
+                qv[k] = Q[i];
+                lq[k] = LQ[i];
+                if (g.flex) zo[k] = Zo[i];
+                else zo[k] = qv[k];
             }
-            s->active = act;
-            if (act) atomicOr(&any, 1);
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const long long i = i0 + k * stride;
+                upd_one<T, ROP>(u[k], r[k], qv[k], lq[k], zo[k], alpha, g.flex, rr, rzo, Rb ? Rb + i : nullptr);
+                U[i] = u[k];
+                R[i] = r[k];
+            }
+        }
+        for (; i0 < g.nvec; i0 += stride) {
+            V u = U[i0], r = R[i0];
+            const V zo = g.flex ? Zo[i0] : Q[i0];
+            upd_one<T, ROP>(u, r, Q[i0], LQ[i0], zo, alpha, g.flex, rr, rzo, Rb ? Rb + i0 : nullptr);
+            U[i0] = u;
+            R[i0] = r;
+        }
+        const double s1 = block_sum<UPD_THREADS>(rr, sh);
+        const double s2 = block_sum<UPD_THREADS>(rzo, sh);
+        if (threadIdx.x == 0) {
+            g.rr_part[(size_t)inst * g.n_upd + blockIdx.x] = s1;
+            g.rzo_part[(size_t)inst * g.n_upd + blockIdx.x] = s2;
+            __threadfence();
+            const unsigned t = atomicAdd(g.counter + inst, 1u);
+            last_s = (t == gridDim.x - 1) ? 1 : 0;
+        }
+        __syncthreads();
+        if (last_s && threadIdx.x < 32) {
+            __threadfence();
+            const double rrs = warp_sum_partials(g.rr_part + (size_t)inst * g.n_upd, g.n_upd);
+            const double rzs = warp_sum_partials(g.rzo_part + (size_t)inst * g.n_upd, g.n_upd);
+            if (threadIdx.x == 0) {
+                g.counter[inst] = 0;
+                if (g.use_sc) {
+                    const int it = sc->iters + 1;
+                    sc->iters = it;
+                    sc->rr = rrs;
+                    sc->rzo = rzs;
+                    int act = 1;
+                    if (!isfinite(rrs)) {
+                        sc->status |= DEV_ERR_NONFINITE;
+                        act = 0;
+                    } else if (!g.fixed && rrs <= sc->tol2) {
+                        act = 0;
+                    } else if (it >= g.max_iter) {
+                        act = 0;
+                    }
+                    sc->active = act;
+                }
+            }
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && g.has_cond) cudaGraphSetConditional(g.cond, any ? 1u : 0u);
+    // graph conditional: the last CTA of the launch sets "some instance active"
+    if (g.has_cond) {
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned t = atomicAdd(g.gcounter, 1u);
+            glast_s = (t == gridDim.x * gridDim.y - 1) ? 1 : 0;
+        }
+        __syncthreads();
+        if (glast_s && threadIdx.x == 0) {
+            __threadfence();
+            int any = 0;
+            for (unsigned i = 0; i < gridDim.y; ++i) any |= __ldcg(&g.sc[i].active);
+            *g.gcounter = 0;
+            cudaGraphSetConditional(g.cond, any ? 1u : 0u);
+        }
+    }
 }
 
 // Start of an inner solve: rr0 = ||R0||^2, stop threshold tol2 = rtol^2 * ref2
@@ -186,6 +227,10 @@ __global__ void k_init(InitArgs g) {
             s->rr = rr;
             s->tol2 = g.rtol * g.rtol * ref;
             s->iters = 0;
+            s->alpha = 0.0;
+            s->beta = 0.0;
+            s->rz = 1.0;
+            s->rzo = 0.0;
             s->status = isfinite(rr) ? 0 : DEV_ERR_NONFINITE;
             s->active = (rr > s->tol2 && isfinite(rr)) ? 1 : 0;
         }
@@ -208,22 +253,48 @@ __global__ void k_imex_rhs(const double* Un, const double* Fn, double* Fbar, int
     }
 }
 
-// Dot-product partials <A, B> over a flat [batch][nvec] range.
+// Dot-product partials <A, B> over a flat [batch][n] range.  With `sc`, the
+// last CTA of each instance sums them in a fixed order and performs the
+// preconditioner finalisation of the PCG: rz_new = <R, Z>,
+// beta = (rz_new - flex <R_new, Z_old>) / rz_old.
 template <typename T>
 __global__ void __launch_bounds__(UPD_THREADS) k_dot(const T* A, const T* B, long long bs, long long n,
-                                                    double* part, int nblk) {
+                                                    double* part, int nblk, PcgScalars* sc, unsigned* counter,
+                                                    int flex) {
     __shared__ double sh[UPD_THREADS / 32];
+    __shared__ int last_s;
     const int inst = blockIdx.y;
+    if (sc && !sc[inst].active) return;
     A += (size_t)inst * bs;
     B += (size_t)inst * bs;
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         acc += (double)A[i] * (double)B[i];
     double s = block_sum<UPD_THREADS>(acc, sh);
-    if (threadIdx.x == 0) part[(size_t)inst * nblk + blockIdx.x] = s;
+    if (threadIdx.x == 0) {
+        part[(size_t)inst * nblk + blockIdx.x] = s;
+        if (sc) {
+            __threadfence();
+            const unsigned t = atomicAdd(counter + inst, 1u);
+            last_s = (t == (unsigned)nblk - 1) ? 1 : 0;
+        }
+    }
+    if (!sc) return;
+    __syncthreads();
+    if (last_s && threadIdx.x < 32) {
+        __threadfence();
+        const double rz = warp_sum_partials(part + (size_t)inst * nblk, nblk);
+        if (threadIdx.x == 0) {
+            counter[inst] = 0;
+            PcgScalars* p = sc + inst;
+            double beta = (rz - (flex ? p->rzo : 0.0)) / p->rz;
+            if (!isfinite(beta)) beta = 0.0;
+            p->beta = beta;
+            p->rz = rz;
+        }
+    }
 }
 
-// kinds: 0 float, 1 double, 2 bf16
 template <typename S, typename D>
 __global__ void k_convert(const S* src, long long s_bs, int s_ld, D* dst, long long d_bs, int d_ld, int rows, int cols) {
     const int inst = blockIdx.z;
@@ -270,55 +341,30 @@ __global__ void k_axpy_into64(double* U, long long u_bs, int u_ld, const float* 
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q; c += gridDim.x * blockDim.x) u[c] += (double)dv[c];
 }
 
-// Sum of squares per instance, fixed order: one CTA per instance.
-__global__ void __launch_bounds__(256) k_sumsq64(const double* A, long long bs, int ld, int rows, int cols, double* out) {
-    __shared__ double sh[8];
-    const int inst = blockIdx.x;
-    const double* a = A + (size_t)inst * bs;
-    double acc = 0.0;
-    for (int r = 0; r < rows; ++r)
-        for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-            double v = a[(size_t)r * ld + c];
-            acc += v * v;
-        }
-    double s = block_sum<256>(acc, sh);
-    if (threadIdx.x == 0) out[inst] = s;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
 mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* R, const void* Q, const void* LQ,
-                               const void* Zold, void* Rop, int rop_kind, const double* rz_partials, int flex,
-                               cudaStream_t st) {
+                               const void* Zold, void* Rop, int rop_kind, int flex, int max_iter, bool fixed,
+                               const cudaGraphConditionalHandle* cond, cudaStream_t st, bool use_scalars) {
     UpdArgs g;
     g.U = U; g.R = R; g.Q = Q; g.LQ = LQ; g.Zold = Zold; g.Rop = Rop;
     g.bs = (long long)c->q * c->ld;
     g.nvec = g.bs / (fp64 ? 2 : 4);
-    g.qlq = c->part.qlq; g.n_qlq = c->part.n_apply;
-    g.rz = rz_partials; g.n_rz = c->part.n_rz;
     g.rr_part = c->part.rr; g.rzo_part = c->part.rzo; g.n_upd = c->part.n_upd;
     g.sc = c->d_sc;
+    g.counter = c->d_ctr + 1 * c->batch;
+    g.gcounter = c->d_ctr + 4 * c->batch;
+    g.use_sc = use_scalars ? 1 : 0;
     g.flex = flex;
+    g.max_iter = max_iter;
+    g.fixed = fixed ? 1 : 0;
+    g.has_cond = (cond && use_scalars) ? 1 : 0;
+    g.cond = cond ? *cond : 0;
     dim3 grid(c->part.n_upd, c->batch);
     if (fp64) k_update<double, 0><<<grid, UPD_THREADS, 0, st>>>(g);
     else if (rop_kind == 1) k_update<float, 1><<<grid, UPD_THREADS, 0, st>>>(g);
     else k_update<float, 0><<<grid, UPD_THREADS, 0, st>>>(g);
-    MOFEM_CUDA_TRY(cudaGetLastError());
-    return MOFEM_OK;
-}
-
-mofem_status launch_pcg_control(const mofem_ctx* c, int max_iter, bool fixed, const cudaGraphConditionalHandle* cond,
-                                cudaStream_t st) {
-    CtlArgs g;
-    g.sc = c->d_sc;
-    g.rr = c->part.rr; g.n_rr = c->part.n_upd;
-    g.qlq = c->part.qlq; g.n_qlq = c->part.n_apply;
-    g.batch = c->batch; g.max_iter = max_iter; g.fixed = fixed ? 1 : 0;
-    g.has_cond = cond ? 1 : 0;
-    if (cond) g.cond = *cond;
-    else g.cond = 0;
-    k_control<<<1, 256, 0, st>>>(g);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }
@@ -345,10 +391,14 @@ mofem_status launch_imex_rhs(const double* Un, const double* Fn, double* Fbar, i
 }
 
 mofem_status launch_dot_partials(const void* A, const void* B, bool fp64, long long bs, long long n, int batch,
-                                 double* part, int nblk, cudaStream_t st) {
+                                 double* part, int nblk, cudaStream_t st, PcgScalars* sc, unsigned* counter, int flex) {
     dim3 grid(nblk, batch);
-    if (fp64) k_dot<double><<<grid, UPD_THREADS, 0, st>>>((const double*)A, (const double*)B, bs, n, part, nblk);
-    else k_dot<float><<<grid, UPD_THREADS, 0, st>>>((const float*)A, (const float*)B, bs, n, part, nblk);
+    if (fp64)
+        k_dot<double><<<grid, UPD_THREADS, 0, st>>>((const double*)A, (const double*)B, bs, n, part, nblk, sc, counter,
+                                                    flex);
+    else
+        k_dot<float><<<grid, UPD_THREADS, 0, st>>>((const float*)A, (const float*)B, bs, n, part, nblk, sc, counter,
+                                                   flex);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }
@@ -399,13 +449,6 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
                                 int q, int batch, cudaStream_t st) {
     dim3 grid((q + 255) / 256, q, batch);
     k_axpy_into64<<<grid, 256, 0, st>>>(U64, u_bs, u_ld, dU, d_bs, d_ld, q);
-    MOFEM_CUDA_TRY(cudaGetLastError());
-    return MOFEM_OK;
-}
-
-mofem_status launch_sumsq64(const double* A, long long bs, int ld, int rows, int cols, int batch, double* out,
-                            cudaStream_t st) {
-    k_sumsq64<<<batch, 256, 0, st>>>(A, bs, ld, rows, cols, out);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

@@ -125,6 +125,12 @@ mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const doubl
     return solve_imex(h, d_u, tau, U_n, F_n, U_np1, prec, info, stream);
 }
 
+mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps, cudaStream_t stream) {
+    if (!h || kernel < 0 || kernel > 6 || reps < 0 || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
+    if (kernel >= 1 && kernel <= 4 && prec == MOFEM_FP64) return MOFEM_ERR_INVALID_ARG;
+    return bench_kernel(h, kernel, prec, reps, stream);
+}
+
 mofem_status mofem_destroy(mofem_handle h) {
     if (!h) return MOFEM_ERR_INVALID_ARG;
     cudaDeviceSynchronize();

@@ -5,12 +5,13 @@
 //     Z = Q1 ((Q1^T R Q2) ./ (lambda_a + mu_b)) Q2^T
 //
 // computed as four GEMMs, each of the form D = A B^T with both operands
-// "K-major" (row-major, contraction index contiguous) and a transposed store
-// out[n][m] = D[m][n] (coalesced straight out of the 32x32b TMEM layout):
-//   G1: D[a][j] = sum_b R[a][b]   Q2T[j][b]          -> X1T[j][a]   (X1 = R Q2)
-//   G2: D[i][j] = sum_a Q1T[i][a] X1T[j][a]          -> WT[j][i] = D / (lam_i + mu_j)
-//   G3: D[j][a] = sum_i WT[j][i]  Q1[a][i]           -> Y[a][j]     (Y = Q1 W)
-//   G4: D[b][a] = sum_j Q2[b][j]  Y[a][j]            -> Z[a][b]     (Z = Y Q2^T), + <R, Z> partials
+// "K-major" (row-major, contraction index contiguous), the output D stored in
+// its natural row-major layout, which is exactly the K-major operand the next
+// GEMM needs:
+//   G1: D[j][a] = sum_b Q2T[j][b] R[a][b]     -> X1T[j][a]   (X1 = R Q2)
+//   G2: D[j][i] = sum_a X1T[j][a] Q1T[i][a]   -> WT[j][i] = D / (lam_i + mu_j)
+//   G3: D[a][j] = sum_i Q1[a][i] WT[j][i]     -> Y[a][j]     (Y = Q1 W)
+//   G4: D[a][b] = sum_j Y[a][j] Q2[b][j]      -> Z[a][b]     (Z = Y Q2^T), + <R, Z> partials
 //
 // Kernel: one 128 x 256 output tile per CTA (M = 128 TMEM lanes, N = 256 FP32
 // TMEM columns), 128 threads.  Warp 0 lane 0 issues TMA loads of 128-byte-wide
@@ -44,7 +45,9 @@ struct GemmArgs {
     const float* lam; long long lam_bs; const float* mu;
     const float* R; long long r_bs; int r_ld;
     double* rz_part;
-    const PcgScalars* sc;
+    PcgScalars* sc;       // skip inactive instances; with rz_part, last-CTA beta finalisation
+    unsigned* counter;    // [batch] CTA tickets (zeroed, self-resetting)
+    int flex;
     int* status;
 };
 
@@ -216,31 +219,64 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     double acc = 0.0;
     if (ok) {
+        // thread = TMEM lane = output row m; it holds 32 consecutive columns per
+        // tcgen05.ld and writes them as 16-byte vectors (row-major output).
         const int m = m0 + warp * 32 + lane;
         const bool m_ok = m < g.M;
-        float lam_m = 0.f;
-        if (g.epi == EPI_DIV && m_ok) lam_m = g.lam[(size_t)inst * g.lam_bs + m];
-        const size_t obase = (size_t)inst * g.out_bs;
+        float mu_m = 0.f;
+        if (g.epi == EPI_DIV && m_ok) mu_m = g.mu[m];
+        const size_t obase = (size_t)inst * g.out_bs + (size_t)m * g.out_ld;
+        const bool vec_ok = (g.out_ld % 8) == 0;
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
             const int nb = n0 + c * 32;
-            if (!m_ok) continue;
+            if (!m_ok || nb >= g.N) continue;
+            if (g.epi == EPI_DIV) {
+                const float* lam = g.lam + (size_t)inst * g.lam_bs + nb;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int n = nb + j;
-                if (n >= g.N) break;
-                float x = v[j];
-                const size_t o = obase + (size_t)n * g.out_ld + m;
-                if (g.epi == EPI_DIV) x = x / (lam_m + g.mu[n]);
-                if (g.epi == EPI_Z) {
-                    reinterpret_cast<float*>(g.out)[o] = x;
-                    if (g.R) acc += (double)x * (double)g.R[(size_t)inst * g.r_bs + (size_t)n * g.r_ld + m];
-                } else if (g.out_bf16) {
-                    reinterpret_cast<__nv_bfloat16*>(g.out)[o] = __float2bfloat16_rn(x);
+                for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], lam[j] + mu_m);
+            }
+            const bool full = vec_ok && nb + 32 <= g.N;
+            if (g.out_bf16) {
+                __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(g.out) + obase + nb;
+                if (full) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 8) {
+                        uint4 pk;
+                        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[j], v[j + 1]);
+                        __nv_bfloat162 p1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
+                        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
+                        __nv_bfloat162 p3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
+                        pk.x = *reinterpret_cast<uint32_t*>(&p0);
+                        pk.y = *reinterpret_cast<uint32_t*>(&p1);
+                        pk.z = *reinterpret_cast<uint32_t*>(&p2);
+                        pk.w = *reinterpret_cast<uint32_t*>(&p3);
+                        *reinterpret_cast<uint4*>(o + j) = pk;
+                    }
                 } else {
-                    reinterpret_cast<float*>(g.out)[o] = x;
+                    for (int j = 0; j < 32 && nb + j < g.N; ++j) o[j] = __float2bfloat16_rn(v[j]);
+                }
+            } else {
+                float* o = reinterpret_cast<float*>(g.out) + obase + nb;
+                const float* r = (g.epi == EPI_Z && g.R) ? g.R + (size_t)inst * g.r_bs + (size_t)m * g.r_ld + nb
+                                                         : nullptr;
+                if (full && (!r || (g.r_ld % 4) == 0)) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        if (r) {
+                            const float4 rv = *reinterpret_cast<const float4*>(r + j);
+                            acc += (double)v[j] * rv.x + (double)v[j + 1] * rv.y + (double)v[j + 2] * rv.z +
+                                   (double)v[j + 3] * rv.w;
+                        }
+                    }
+                } else {
+                    for (int j = 0; j < 32 && nb + j < g.N; ++j) {
+                        o[j] = v[j];
+                        if (r) acc += (double)v[j] * (double)r[j];
+                    }
                 }
             }
         }
@@ -254,11 +290,38 @@ __global__ void __launch_bounds__(128, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (g.epi == EPI_Z && g.rz_part && threadIdx.x == 0)
-        g.rz_part[(size_t)inst * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] =
-            red[0] + red[1] + red[2] + red[3];
     if (warp == 2)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    if (g.epi == EPI_Z && g.rz_part) {
+        // <R, Z> partial; the last CTA of the instance sets rz and beta (fixed-order sum)
+        __shared__ int last_s;
+        const int nblk = gridDim.x * gridDim.y;
+        if (threadIdx.x == 0) {
+            g.rz_part[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+            last_s = 0;
+            if (g.sc && g.counter) {
+                __threadfence();
+                const unsigned t = atomicAdd(g.counter + inst, 1u);
+                last_s = (t == (unsigned)nblk - 1) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        if (last_s && warp == 0) {
+            __threadfence();
+            double rz = 0.0;
+            for (int i = lane; i < nblk; i += 32) rz += __ldcg(g.rz_part + (size_t)inst * nblk + i);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
+            if (lane == 0) {
+                g.counter[inst] = 0;
+                PcgScalars* p = g.sc + inst;
+                double beta = (rz - (g.flex ? p->rzo : 0.0)) / p->rz;
+                if (!isfinite(beta)) beta = 0.0;
+                p->beta = beta;
+                p->rz = rz;
+            }
+        }
+    }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -302,6 +365,35 @@ mofem_status make_map(CUtensorMap* m, const void* base, int esize, int cols, int
     }
     return MOFEM_OK;
 }
+
+}  // namespace
+
+// 3D tensor map over [batch][rows][cols] for plain (unswizzled) row tiles of
+// box_cols x box_rows elements (the operator-apply staging).
+mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
+                          int box_cols, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) {
+        mofem_set_last_error("cuTensorMapEncodeTiled entry point unavailable", __FILE__, __LINE__);
+        return MOFEM_ERR_CUDA;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * esize, (cuuint64_t)rows * ld * esize};
+    cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                     const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled (rows) failed (%d)", (int)r);
+        mofem_set_last_error(buf, __FILE__, __LINE__);
+        return MOFEM_ERR_CUDA;
+    }
+    return MOFEM_OK;
+}
+
+namespace {
 
 template <int KIND>
 mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch, cudaStream_t st) {
@@ -359,22 +451,41 @@ mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
     MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(tmp);
     // A maps (box rows BM) and B maps (box rows BN) of the four GEMMs
-    MOFEM_TRY(make_map(&p.mA[0], p.Rop, es, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[0], p.Q2T, es, q, q, 1, ld, BN));
-    MOFEM_TRY(make_map(&p.mA[1], p.Q1T, es, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[1], p.X1T, es, q, q, B, ld, BN));
-    MOFEM_TRY(make_map(&p.mA[2], p.WT, es, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[2], p.Q1, es, q, q, B, ld, BN));
-    MOFEM_TRY(make_map(&p.mA[3], p.Q2, es, q, q, 1, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[3], p.Y, es, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[0], p.Q2T, es, q, q, 1, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[0], p.Rop, es, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[1], p.X1T, es, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[1], p.Q1T, es, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[2], p.Q1, es, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[2], p.WT, es, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[3], p.Y, es, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&p.mB[3], p.Q2, es, q, q, 1, ld, BN));
     p.ready = true;
     return MOFEM_OK;
+}
+
+// One of the four GEMMs (index 0..3) on the plan's internal buffers (timing).
+mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaStream_t st) {
+    const TcPlan& p = c->tc[which];
+    const int q = c->q, ld = c->ld;
+    const int bk = which == 1 ? 64 : 32;
+    GemmArgs g{};
+    g.M = q; g.N = q; g.nk = (q + bk - 1) / bk;
+    g.status = c->d_status;
+    g.lam = c->lam32; g.lam_bs = ld; g.mu = c->mu32;
+    g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = which == 1;
+    void* outs[4] = {p.X1T, p.WT, p.Y, Z};
+    const int epis[4] = {EPI_STORE, EPI_DIV, EPI_STORE, EPI_Z};
+    g.out = outs[idx]; g.epi = epis[idx];
+    g.a_shared = idx == 0; g.b_shared = idx == 3;
+    if (idx == 3) g.out_bf16 = 0;
+    return which == 1 ? launch_gemm<1>(p.mA[idx], p.mB[idx], g, c->batch, st)
+                      : launch_gemm<0>(p.mA[idx], p.mB[idx], g, c->batch, st);
 }
 
 // Z = P^{-1}(R) with R already in p.Rop (rounded operand).  R32 (FP32, same
 // layout as Z) feeds the fused <R, Z> partials when rz_partial != nullptr.
 mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z, int z_ld,
-                        long long z_bs, double* rz_partial, const PcgScalars* sc, cudaStream_t st) {
+                        long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st) {
     const TcPlan& p = c->tc[which];
     const int q = c->q, ld = c->ld;
     const int bk = which == 1 ? 64 : 32;
@@ -395,17 +506,19 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
                           : launch_gemm<0>(p.mA[i], p.mB[i], g, c->batch, st);
     };
     // G1: X1T = (R Q2)^T
-    g.out = p.X1T; g.epi = EPI_STORE; g.a_shared = 0; g.b_shared = 1;
+    g.out = p.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
     MOFEM_TRY(run(0));
-    // G2: WT = ((Q1^T X1) ./ (lam + mu))^T
+    // G2: WT[j][i] = (Q1^T X1)[i][j] / (lam_i + mu_j)
     g.out = p.WT; g.epi = EPI_DIV; g.a_shared = 0; g.b_shared = 0;
     MOFEM_TRY(run(1));
     // G3: Y = Q1 W
     g.out = p.Y; g.epi = EPI_STORE; g.a_shared = 0; g.b_shared = 0;
     MOFEM_TRY(run(2));
     // G4: Z = Y Q2^T (+ <R, Z> partials)
-    g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 1; g.b_shared = 0;
+    g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 0; g.b_shared = 1;
     g.R = R32; g.r_bs = r_bs; g.r_ld = r_ld; g.rz_part = rz_partial;
+    g.counter = c->d_ctr + 2 * c->batch;
+    g.flex = 1;
     MOFEM_TRY(run(3));
     return MOFEM_OK;
 }

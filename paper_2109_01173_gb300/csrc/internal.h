@@ -22,7 +22,9 @@ enum : int {
 // Per-instance scalar state of the device-resident PCG (FP64).
 struct PcgScalars {
     double rz;          // <R, Z> of the current iterate
-    double rz_prev;     // <R, Z> of the previous iterate (flexible beta denominator)
+    double rzo;         // <R_new, Z_old> (flexible beta numerator correction)
+    double alpha;       // step of the current iteration
+    double beta;        // direction coefficient for the next iteration
     double rr0;         // ||R_0||^2 of this (inner) solve
     double rr;          // ||R||^2 after the last update
     double tol2;        // stop when rr <= tol2
@@ -84,6 +86,7 @@ struct mofem_ctx {
     Partials part{};
     PcgScalars* d_sc = nullptr;  // [batch]
     int* d_status = nullptr;     // device error bits
+    unsigned* d_ctr = nullptr;   // [5][batch] CTA tickets for last-CTA finalisation (zeroed, self-resetting)
     double* d_red = nullptr;     // small scratch for reductions [batch * 8]
 
     cublasHandle_t cublas = nullptr;
@@ -93,6 +96,7 @@ struct mofem_ctx {
     cudaGraphExec_t it_graph[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t loop_graph[3] = {nullptr, nullptr, nullptr};
     int it_graph_max_iter[3] = {0, 0, 0};
+    bool host_stepped[3] = {false, false, false};   // conditional graph unavailable for this precision
 };
 
 // ---- error helpers -------------------------------------------------------
@@ -139,6 +143,22 @@ struct ApplyArgs {
 mofem_status launch_apply(int K, int nt, bool fp64, int mode, const ApplyArgs& a, int batch, cudaStream_t st);
 int apply_rows_per_cta(int K);
 
+// PCG form of the apply on internal buffers (TMA staging): Q = Z + beta Q_prev
+// (written to Qnew), L(Q) -> LQ, partial <Q, L(Q)>, last CTA sets alpha.
+struct ApplyPcgArgs {
+    const void* S; long long s_bs; const void* T;
+    int q, ld; long long bs;
+    void* Qnew; void* LQ;
+    double* partial; unsigned* counter;
+    PcgScalars* sc; int use_sc;
+    int* status;
+};
+mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, const CUtensorMap& mQ,
+                              const ApplyPcgArgs& a, int batch, cudaStream_t st);
+int apply_pcg_rows_per_cta(int K);
+mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
+                          int box_cols, int box_rows);
+
 // ---- BLAS-1 / control kernels (blas1.cu) ----------------------------------
 mofem_status launch_convert(const void* src, int src_kind, long long s_bs, int s_ld,
                             void* dst, int dst_kind, long long d_bs, int d_ld,
@@ -157,8 +177,10 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
 // plan.Rop; writes Z (FP32) and, if rz_partial, the <R, Z> partials (R32 = R in FP32).
 mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st);
 mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z,
-                        int z_ld, long long z_bs, double* rz_partial, const PcgScalars* sc, cudaStream_t st);
+                        int z_ld, long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st);
 int tc_rz_ctas(const mofem_ctx* c);
+mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaStream_t st);
+mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int reps, cudaStream_t st);
 
 // ---- solver (solver.cu) ------------------------------------------------------
 mofem_status solver_init(mofem_ctx* c, cudaStream_t st);
@@ -168,7 +190,7 @@ mofem_status op_rhs(mofem_ctx* c, const double* F, double* Bout, long long b_bs,
 mofem_status precond64(mofem_ctx* c, const double* R, long long r_bs, int r_ld, double* Z, long long z_bs,
                        int z_ld, cudaStream_t st);
 mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs, int r_ld, float* Z,
-                        long long z_bs, int z_ld, double* rz_partial, const PcgScalars* sc, cudaStream_t st);
+                        long long z_bs, int z_ld, double* rz_partial, PcgScalars* sc, cudaStream_t st);
 mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rtol, int max_iter,
                             mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
 mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,

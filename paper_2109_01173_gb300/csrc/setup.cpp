@@ -344,7 +344,23 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
     Band& Mt = H.Mt;
     Band& Kt = H.Kt;
 
-    // --- upload tables ----------------------------------------------------------
+    // --- upload tables (difference form: row sum in the diagonal slot) -------------
+    auto rowsum_one = [&](double* base) {
+        for (int r = 0; r < q; ++r) {
+            double sum = 0.0;
+            for (int j = 0; j < c->P; ++j) sum += base[(size_t)j * q + r];
+            base[(size_t)c->K * q + r] = sum;
+        }
+    };
+    // T tables: every t-pass runs in difference form.  S tables: only the terms
+    // whose s-factor is stiffness- or convection-like (the apply kernel's mask:
+    // terms 0,3,4 of the five-term operator, 0,4,5,6,7 of the eight-term one).
+    const unsigned smask = c->NT == 5 ? 0x19u : 0xF1u;
+    for (int i = 0; i < B; ++i)
+        for (int t = 0; t < c->NT; ++t)
+            if ((smask >> t) & 1u) rowsum_one(Sh.data() + ((size_t)i * c->NT + t) * c->P * q);
+    for (int t = 0; t < c->NT; ++t) rowsum_one(Th.data() + (size_t)t * c->P * q);
+    rowsum_one(Trh.data());
     std::vector<float> tmp;
     auto up64 = [&](double** d, const std::vector<double>& h) -> mofem_status {
         MOFEM_TRY(dev_alloc(d, h.size()));

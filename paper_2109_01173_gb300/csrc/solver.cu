@@ -28,14 +28,13 @@
 #include <algorithm>
 
 mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* R, const void* Q, const void* LQ,
-                               const void* Zold, void* Rop, int rop_kind, const double* rz_partials, int flex,
-                               cudaStream_t st);
-mofem_status launch_pcg_control(const mofem_ctx* c, int max_iter, bool fixed, const cudaGraphConditionalHandle* cond,
-                                cudaStream_t st);
+                               const void* Zold, void* Rop, int rop_kind, int flex, int max_iter, bool fixed,
+                               const cudaGraphConditionalHandle* cond, cudaStream_t st, bool use_scalars = true);
 mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
                              cudaStream_t st);
 mofem_status launch_dot_partials(const void* A, const void* B, bool fp64, long long bs, long long n, int batch,
-                                 double* part, int nblk, cudaStream_t st);
+                                 double* part, int nblk, cudaStream_t st, PcgScalars* sc = nullptr,
+                                 unsigned* counter = nullptr, int flex = 0);
 mofem_status launch_imex_rhs(const double* Un, const double* Fn, double* Fbar, int n, int q, int off, double gam,
                              double tau, int batch, cudaStream_t st);
 
@@ -55,6 +54,9 @@ struct Extra {   // per-handle scratch not in the public struct
     double* rz_slots[2] = {nullptr, nullptr};
     void* cublas_ws = nullptr;
     cudaStream_t cap = nullptr;
+    int n_res = 0;                 // CTAs of the generic apply (residual partials) per instance
+    bool maps32 = false, maps64 = false;
+    CUtensorMap mZ32, mQA32, mQB32, mZ64, mQA64, mQB64;   // apply staging maps (PCG form)
 };
 
 }  // namespace
@@ -70,17 +72,20 @@ static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
     Extra& e = extras()[c];
     if (c->d_part) return MOFEM_OK;
     const int B = c->batch;
-    const int TA = apply_rows_per_cta(c->K);
+    const int TA = apply_pcg_rows_per_cta(c->K);
     c->part.n_apply = ((c->q + 127) / 128) * ((c->q + TA - 1) / TA);
+    const int TG = apply_rows_per_cta(c->K);
+    e.n_res = ((c->q + 127) / 128) * ((c->q + TG - 1) / TG);
     long long nvec = (long long)per(c) / 4;
-    c->part.n_upd = (int)std::max(1LL, std::min(128LL, (nvec + 255) / 256));
+    c->part.n_upd = (int)std::max(1LL, std::min(296LL, (nvec + 1023) / 1024));
     c->part.n_rz = tc_rz_ctas(c);
-    const size_t n_total = (size_t)B * (c->part.n_apply * 2 + c->part.n_upd * 2 + c->part.n_rz * 3) + B;
+    const size_t n_total =
+        (size_t)B * (c->part.n_apply + e.n_res + c->part.n_upd * 2 + c->part.n_rz * 3) + B;
     MOFEM_CUDA_TRY(cudaMalloc(&c->d_part, n_total * sizeof(double)));
     MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_part, 0, n_total * sizeof(double), st));
     double* p = c->d_part;
     c->part.qlq = p; p += (size_t)B * c->part.n_apply;
-    e.res_part = p; p += (size_t)B * c->part.n_apply;
+    e.res_part = p; p += (size_t)B * e.n_res;
     c->part.rr = p; p += (size_t)B * c->part.n_upd;
     c->part.rzo = p; p += (size_t)B * c->part.n_upd;
     e.rz_slots[0] = p; p += (size_t)B * c->part.n_rz;
@@ -88,6 +93,8 @@ static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
     e.bb_part = p; p += (size_t)B * c->part.n_rz;
     e.ref2 = p;
     c->part.rz = e.rz_slots[0];
+    MOFEM_CUDA_TRY(cudaMalloc(&c->d_ctr, sizeof(unsigned) * (4 * B + 1)));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned) * (4 * B + 1), st));
     MOFEM_CUDA_TRY(cudaMalloc(&c->d_sc, sizeof(PcgScalars) * B));
     MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_sc, 0, sizeof(PcgScalars) * B, st));
     MOFEM_CUDA_TRY(cudaMalloc(&c->d_status, sizeof(int)));
@@ -122,6 +129,26 @@ static mofem_status ensure_w64(mofem_ctx* c, cudaStream_t st) {
         MOFEM_CUDA_TRY(cudaMalloc(&e.cublas_ws, ws));
         if (cublasSetWorkspace(c->cublas, e.cublas_ws, ws) != CUBLAS_STATUS_SUCCESS) return MOFEM_ERR_CUDA;
         cublasSetMathMode(c->cublas, CUBLAS_DEFAULT_MATH);
+    }
+    return MOFEM_OK;
+}
+
+// TMA maps of the staged apply tiles over the PCG buffers Z, Q_a, Q_b.
+static mofem_status ensure_apply_maps(mofem_ctx* c, bool fp64) {
+    Extra& e = extras()[c];
+    const int HR = apply_pcg_rows_per_cta(c->K) + 2 * c->K;
+    const int WCT = 128 + 8;
+    if (fp64 && !e.maps64) {
+        MOFEM_TRY(make_row_map(&e.mZ64, w64(c, W64_Z), 8, c->q, c->q, c->batch, c->ld, WCT, HR));
+        MOFEM_TRY(make_row_map(&e.mQA64, w64(c, W64_QA), 8, c->q, c->q, c->batch, c->ld, WCT, HR));
+        MOFEM_TRY(make_row_map(&e.mQB64, w64(c, W64_QB), 8, c->q, c->q, c->batch, c->ld, WCT, HR));
+        e.maps64 = true;
+    }
+    if (!fp64 && !e.maps32) {
+        MOFEM_TRY(make_row_map(&e.mZ32, w32(c, W32_Z), 4, c->q, c->q, c->batch, c->ld, WCT, HR));
+        MOFEM_TRY(make_row_map(&e.mQA32, w32(c, W32_QA), 4, c->q, c->q, c->batch, c->ld, WCT, HR));
+        MOFEM_TRY(make_row_map(&e.mQB32, w32(c, W32_QB), 4, c->q, c->q, c->batch, c->ld, WCT, HR));
+        e.maps32 = true;
     }
     return MOFEM_OK;
 }
@@ -212,7 +239,7 @@ mofem_status precond64(mofem_ctx* c, const double* R, long long r_bs, int r_ld, 
 
 // Tensor-core preconditioner on a user (or internal) FP32 matrix R.
 mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs, int r_ld, float* Z, long long z_bs,
-                        int z_ld, double* rz_partial, const PcgScalars* sc, cudaStream_t st) {
+                        int z_ld, double* rz_partial, PcgScalars* sc, cudaStream_t st) {
     MOFEM_TRY(tc_prepare(c, which, st));
     TcPlan& p = c->tc[which];
     MOFEM_TRY(launch_convert(R, 0, r_bs, r_ld, p.Rop, which == 1 ? 2 : 0, (long long)per(c), c->ld, c->q, c->q,
@@ -228,40 +255,39 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
     const long long bs = (long long)per(c);
     void *U, *R, *Z, *Qn, *Qp, *LQ;
+    const CUtensorMap *mZ, *mQp;
     if (fp64) {
         U = w64(c, W64_U); R = w64(c, W64_R); Z = w64(c, W64_Z);
         Qn = w64(c, s % 2 ? W64_QB : W64_QA); Qp = w64(c, s % 2 ? W64_QA : W64_QB); LQ = w64(c, W64_LQ);
+        mZ = &e.mZ64; mQp = s % 2 ? &e.mQA64 : &e.mQB64;
     } else {
         U = w32(c, W32_U); R = w32(c, W32_R); Z = w32(c, W32_Z);
         Qn = w32(c, s % 2 ? W32_QB : W32_QA); Qp = w32(c, s % 2 ? W32_QA : W32_QB); LQ = w32(c, W32_LQ);
+        mZ = &e.mZ32; mQp = s % 2 ? &e.mQA32 : &e.mQB32;
     }
-    double* rz_cur = e.rz_slots[s % 2];
-    double* rz_next = e.rz_slots[(s + 1) % 2];
-    // 1) Q = Z + beta Q_prev ; LQ = L(Q) ; <Q, LQ>
-    ApplyArgs a = apply_args_square(c, fp64);
-    a.X = Qp; a.x_bs = bs; a.x_ld = c->ld;
-    a.Z = Z; a.Xnew = Qn;
-    a.Y = LQ; a.y_bs = bs; a.y_ld = c->ld;
-    a.partial = c->part.qlq;
-    a.sc = c->d_sc;
-    a.rz_cur = rz_cur; a.rz_prev = rz_next; a.rzo = c->part.rzo;
-    a.n_rz = c->part.n_rz; a.n_rzo = c->part.n_upd;
-    a.flex = fp64 ? 0 : 1;
-    MOFEM_TRY(launch_apply(c->K, c->NT, fp64, APPLY_QUPDATE, a, c->batch, st));
-    // 2) alpha ; U += alpha Q ; R -= alpha LQ
+    // 1) Q = Z + beta Q_prev ; LQ = L(Q) ; alpha = <R,Z>/<Q,LQ> (last CTA)
+    ApplyPcgArgs a{};
+    a.S = fp64 ? (const void*)c->S64 : (const void*)c->S32;
+    a.s_bs = (long long)c->NT * c->P * c->q;
+    a.T = fp64 ? (const void*)c->T64 : (const void*)c->T32;
+    a.q = c->q; a.ld = c->ld; a.bs = bs;
+    a.Qnew = Qn; a.LQ = LQ;
+    a.partial = c->part.qlq; a.counter = c->d_ctr;
+    a.sc = c->d_sc; a.use_sc = 1;
+    a.status = c->d_status;
+    MOFEM_TRY(launch_apply_pcg(c->K, c->NT, fp64, *mZ, *mQp, a, c->batch, st));
+    // 2) U += alpha Q ; R -= alpha LQ ; convergence (last CTA) ; graph condition
     MOFEM_TRY(launch_pcg_update(c, fp64, U, R, Qn, LQ, Z, fp64 ? nullptr : c->tc[which].Rop,
-                                (!fp64 && which == 1) ? 1 : 0, rz_cur, fp64 ? 0 : 1, st));
-    // 3) convergence
-    MOFEM_TRY(launch_pcg_control(c, max_iter, fixed, cond, st));
-    // 4) Z = P^{-1}(R), <R, Z>
+                                (!fp64 && which == 1) ? 1 : 0, fp64 ? 0 : 1, max_iter, fixed, cond, st, true));
+    // 3) Z = P^{-1}(R) ; rz and beta (last CTA)
     if (fp64) {
         MOFEM_TRY(precond64(c, (const double*)R, bs, c->ld, (double*)Z, bs, c->ld, st));
-        MOFEM_TRY(launch_dot_partials(R, Z, true, bs, bs, c->batch, rz_next, c->part.n_rz, st));
+        MOFEM_TRY(launch_dot_partials(R, Z, true, bs, bs, c->batch, e.rz_slots[0], c->part.n_rz, st, c->d_sc,
+                                      c->d_ctr + 2 * c->batch, 0));
     } else {
-        if (which == 0) {   // TF32 reads R directly: refresh the operand copy (FP32 -> FP32)
+        if (which == 0)   // TF32 GEMMs read their own FP32 operand copy of R
             MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[0].Rop, 0, bs, c->ld, c->q, c->q, c->batch, st));
-        }
-        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, rz_next, c->d_sc, st));
+        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st));
     }
     return MOFEM_OK;
 }
@@ -363,14 +389,16 @@ static mofem_status run_inner(mofem_ctx* c, mofem_precision prec, int max_iter, 
     void* Z = fp64 ? (void*)w64(c, W64_Z) : (void*)w32(c, W32_Z);
     void* Qp = fp64 ? (void*)w64(c, W64_QB) : (void*)w32(c, W32_QB);
     const size_t esz = fp64 ? 8 : 4;
+    MOFEM_TRY(ensure_apply_maps(c, fp64));
     MOFEM_CUDA_TRY(cudaMemsetAsync(Qp, 0, bs * c->batch * esz, st));
-    // ||R0||^2 partials (reuse the update's rr slots) -> init
+    // ||R0||^2 -> init (active flags, tolerance, counters)
     MOFEM_TRY(launch_dot_partials(R, R, fp64, bs, bs, c->batch, c->part.rr, c->part.n_upd, st));
     MOFEM_TRY(launch_pcg_init(c, c->part.rr, c->part.n_upd, ref2_dev, rtol, st));
-    // Z0 = P^{-1}(R0) and <R0, Z0> into rz slot 0
+    // Z0 = P^{-1}(R0) and rz = <R0, Z0> (last-CTA finalisation)
     if (fp64) {
         MOFEM_TRY(precond64(c, (const double*)R, bs, c->ld, (double*)Z, bs, c->ld, st));
-        MOFEM_TRY(launch_dot_partials(R, Z, true, bs, bs, c->batch, e.rz_slots[0], c->part.n_rz, st));
+        MOFEM_TRY(launch_dot_partials(R, Z, true, bs, bs, c->batch, e.rz_slots[0], c->part.n_rz, st, c->d_sc,
+                                      c->d_ctr + 2 * c->batch, 0));
     } else {
         MOFEM_TRY(tc_prepare(c, which, st));
         MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[which].Rop, which == 1 ? 2 : 0, bs, c->ld, c->q, c->q,
@@ -378,26 +406,35 @@ static mofem_status run_inner(mofem_ctx* c, mofem_precision prec, int max_iter, 
         MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st));
     }
     const int pi = (int)prec;
-    if (c->opts.flags & MOFEM_FLAG_HOST_LOOP) {
-        MOFEM_TRY(build_step_graph(c, prec, max_iter, fixed));
-        std::vector<PcgScalars> sc;
-        for (int guard = 0; guard < max_iter + 2; guard += 2) {
-            MOFEM_CUDA_TRY(cudaGraphLaunch(c->it_graph[pi], st));
-            MOFEM_TRY(read_scalars(c, sc, st));
-            bool any = false;
-            for (auto& s : sc) any = any || s.active;
-            if (!any) break;
+    bool stepped = (c->opts.flags & MOFEM_FLAG_HOST_LOOP) || c->host_stepped[pi];
+    if (!stepped) {
+        mofem_status gs = build_loop_graph(c, prec, max_iter, fixed);
+        if (gs == MOFEM_OK) {
+            MOFEM_CUDA_TRY(cudaGraphLaunch(c->loop_graph[pi], st));
+            return MOFEM_OK;
         }
-    } else {
-        MOFEM_TRY(build_loop_graph(c, prec, max_iter, fixed));
-        MOFEM_CUDA_TRY(cudaGraphLaunch(c->loop_graph[pi], st));
+        // A device-side loop cannot be built for this precision (cuBLAS kernels in
+        // the body of a conditional node are rejected at some sizes): step the
+        // two-iteration graph from the host instead, for this and later solves.
+        cudaGetLastError();
+        c->host_stepped[pi] = true;
+    }
+    MOFEM_TRY(build_step_graph(c, prec, max_iter, fixed));
+    std::vector<PcgScalars> sc;
+    for (int guard = 0; guard < max_iter + 2; guard += 2) {
+        MOFEM_CUDA_TRY(cudaGraphLaunch(c->it_graph[pi], st));
+        MOFEM_TRY(read_scalars(c, sc, st));
+        bool any = false;
+        for (auto& s : sc) any = any || s.active;
+        if (!any) break;
     }
     return MOFEM_OK;
 }
 
 static mofem_status finish_info(mofem_ctx* c, mofem_solve_info* info, mofem_status st_code, int iters, int outer,
-                                double rel, float ms) {
+                                double rel, float ms, long long launches) {
     if (info) {
+        info->kernel_launches = launches;
         info->status = st_code;
         info->iterations = iters;
         info->outer_steps = outer;
@@ -424,38 +461,55 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
     MOFEM_TRY(launch_dot_partials(c->Bm64, c->Bm64, true, bs, bs, B, e.bb_part, c->part.n_rz, st));
     MOFEM_TRY(sum_partials(e.bb_part, c->part.n_rz, B, bb, st));
     MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
-    MOFEM_TRY(sum_partials(e.res_part, c->part.n_apply, B, rr, st));
+    MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
     std::vector<double> ref2(B);
     for (int i = 0; i < B; ++i) ref2[i] = ref_is_r0 ? rr[i] : bb[i];
     int total_it = 0, outer = 0;
+    long long launches = 3;   // dot(B,B), residual, (rhs counted by the caller)
+    // kernels per inner solve: init sequence + WHILE bodies of two iterations
+    // (libmofem kernels only; the FP64 form's DGEMMs are cuBLAS kernels and not counted)
+    auto inner_launches = [&](int it, bool fp64) -> long long {
+        const long long per_it = fp64 ? 2 + 2 : (prec == MOFEM_MIXED_TF32 ? 2 + 1 + 4 : 2 + 4);
+        const long long bodies = std::max(1, (it + 1) / 2);
+        const long long init = fp64 ? 2 + 2 : 2 + 1 + 4;
+        return init + bodies * 2 * per_it;
+    };
     mofem_status code = MOFEM_OK;
     std::vector<PcgScalars> sc;
     auto rel_max = [&](const std::vector<double>& r) {
         double m = 0.0;
         for (int i = 0; i < B; ++i) {
-            double v = ref2[i] > 0 ? std::sqrt(r[i] / ref2[i]) : (r[i] > 0 ? INFINITY : 0.0);
+            double v;
+            if (!std::isfinite(ref2[i]) || !std::isfinite(r[i])) v = NAN;
+            else v = ref2[i] > 0 ? std::sqrt(r[i] / ref2[i]) : (r[i] > 0 ? INFINITY : 0.0);
             if (!(v <= m)) m = v;   // NaN propagates
         }
         return m;
     };
     double rel = rel_max(rr);
     if (prec == MOFEM_FP64) {
+        // FP64 MO-PCG from U with stop ||R|| <= rtol ||B|| on the recursively
+        // updated residual; if the recomputed true residual misses the target,
+        // restart from the current U with the true residual (residual replacement).
         MOFEM_TRY(ensure_w64(c, st));
-        // U64 <- U (internal layout), R <- R64
+        const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 20;
         MOFEM_TRY(launch_convert(U, 1, u_bs, u_ld, w64(c, W64_U), 1, bs, ld, q, q, B, st));
-        MOFEM_CUDA_TRY(cudaMemcpyAsync(w64(c, W64_R), c->R64, sizeof(double) * bs * B, cudaMemcpyDeviceToDevice, st));
-        // the stop test is relative to sqrt(ref2): pass ref2 to the init kernel
         MOFEM_CUDA_TRY(cudaMemcpyAsync(e.ref2, ref2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
-        if (rel > rtol) {
+        while (!(rel <= rtol) && outer < max_outer && std::isfinite(rel)) {
+            MOFEM_CUDA_TRY(cudaMemcpyAsync(w64(c, W64_R), c->R64, sizeof(double) * bs * B, cudaMemcpyDeviceToDevice, st));
             MOFEM_TRY(run_inner(c, prec, max_iter, fixed, e.ref2, rtol, st));
             MOFEM_TRY(read_scalars(c, sc, st));
-            for (auto& s : sc) total_it = std::max(total_it, s.iters);
+            int it = 0;
+            for (auto& s : sc) it = std::max(it, s.iters);
+            total_it += it;
+            ++outer;
+            launches += inner_launches(it, true) + 2;
+            MOFEM_TRY(launch_convert(w64(c, W64_U), 1, bs, ld, U, 1, u_bs, u_ld, q, q, B, st));
+            MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
+            MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
+            rel = rel_max(rr);
+            if (fixed) break;
         }
-        MOFEM_TRY(launch_convert(w64(c, W64_U), 1, bs, ld, U, 1, u_bs, u_ld, q, q, B, st));
-        MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
-        MOFEM_TRY(sum_partials(e.res_part, c->part.n_apply, B, rr, st));
-        rel = rel_max(rr);
-        outer = 1;
     } else {
         MOFEM_TRY(ensure_w32(c, st));
         const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
@@ -480,8 +534,9 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
             ++outer;
+            launches += inner_launches(it, false) + 3;   // + convert R, axpy, residual
             MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
-            MOFEM_TRY(sum_partials(e.res_part, c->part.n_apply, B, rr, st));
+            MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
             rel = rel_max(rr);
             if (fixed) break;
         }
@@ -500,7 +555,7 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
     else if ((dev_status & DEV_ERR_NONFINITE) || !std::isfinite(rel)) code = MOFEM_ERR_NONFINITE;
     else if (dev_status & DEV_ERR_BREAKDOWN && !(rel <= rtol)) code = MOFEM_ERR_BREAKDOWN;
     else if (!(rel <= rtol) && !fixed) code = MOFEM_ERR_NOT_CONVERGED;
-    return finish_info(c, info, code, total_it, outer, rel, ms);
+    return finish_info(c, info, code, total_it, outer, rel, ms, launches + 1);
 }
 
 mofem_status solver_init(mofem_ctx* c, cudaStream_t st) { return ensure_common(c, st); }
@@ -527,4 +582,43 @@ mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, 
     if (Unp1 != Un)
         MOFEM_CUDA_TRY(cudaMemcpyAsync(Unp1, Un, sizeof(double) * qq * c->batch, cudaMemcpyDeviceToDevice, st));
     return solve_core(c, Unp1, qq, c->q, tau, 100000, prec, 1, info, st);
+}
+
+// Benchmark hook: repeated launches of one hot kernel on internal buffers.
+mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int reps, cudaStream_t st) {
+    MOFEM_TRY(ensure_common(c, st));
+    const long long bs = (long long)per(c);
+    const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
+    if (kernel == 6) {
+        for (int r = 0; r < reps; ++r)
+            MOFEM_TRY(op_residual64(c, c->Bm64, bs, c->ld, c->R64, extras()[c].res_part, st));
+        return MOFEM_OK;
+    }
+    MOFEM_TRY(ensure_w32(c, st));
+    if (kernel >= 1 && kernel <= 4) {
+        MOFEM_TRY(tc_prepare(c, which, st));
+        for (int r = 0; r < reps; ++r) MOFEM_TRY(tc_gemm_one(c, which, kernel - 1, w32(c, W32_Z), st));
+        return MOFEM_OK;
+    }
+    if (kernel == 0) {
+        MOFEM_TRY(ensure_apply_maps(c, false));
+        Extra& e = extras()[c];
+        ApplyPcgArgs a{};
+        a.S = c->S32; a.s_bs = (long long)c->NT * c->P * c->q; a.T = c->T32;
+        a.q = c->q; a.ld = c->ld; a.bs = bs;
+        a.Qnew = w32(c, W32_QA); a.LQ = w32(c, W32_LQ);
+        a.partial = c->part.qlq; a.counter = c->d_ctr + 3 * c->batch;
+        a.sc = c->d_sc; a.use_sc = 0;
+        a.status = c->d_status;
+        for (int r = 0; r < reps; ++r) MOFEM_TRY(launch_apply_pcg(c->K, c->NT, false, e.mZ32, e.mQB32, a, c->batch, st));
+        return MOFEM_OK;
+    }
+    if (kernel == 5) {
+        MOFEM_TRY(tc_prepare(c, 1, st));
+        for (int r = 0; r < reps; ++r)
+            MOFEM_TRY(launch_pcg_update(c, false, w32(c, W32_U), w32(c, W32_R), w32(c, W32_QA), w32(c, W32_LQ),
+                                        w32(c, W32_Z), c->tc[1].Rop, 1, 1, 1 << 30, true, nullptr, st, false));
+        return MOFEM_OK;
+    }
+    return MOFEM_ERR_INVALID_ARG;
 }

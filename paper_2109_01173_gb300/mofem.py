@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_steps", ctypes.c_int),
-                ("batch", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("batch", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong)]
 
 
 class MofemError(RuntimeError):
@@ -63,6 +64,7 @@ def _load():
         "mofem_pcg_solve": [vp, vp, vp, c_double, c_int, c_int, P(SolveInfo), vp],
         "mofem_imex_step": [vp, c_double, c_double, vp, vp, vp, c_int, P(SolveInfo), vp],
         "mofem_destroy": [vp],
+        "mofem_bench_kernel": [vp, c_int, c_int, c_int, vp],
         "mofem_host_tables": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), P(c_int), P(c_int),
                               vp, vp, vp, vp],
     }
@@ -81,7 +83,7 @@ LIB = _load()
 
 EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply", "mofem_rhs", "mofem_precond",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
-            "mofem_host_tables"]
+            "mofem_host_tables", "mofem_bench_kernel"]
 
 
 def _check(fn, code):
@@ -197,6 +199,10 @@ class Handle:
         if check:
             _check("mofem_imex_step", code)
         return info, code
+
+    def bench_kernel(self, kernel, precision="bf16", reps=1):
+        """Launch one hot kernel `reps` times on internal buffers (timing hook)."""
+        _check("mofem_bench_kernel", LIB.mofem_bench_kernel(self.h, kernel, PRECISIONS[precision], reps, _stream()))
 
     def close(self):
         if self.h:

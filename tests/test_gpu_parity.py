@@ -1,0 +1,272 @@
+"""GPU parity of libmofem (through the C ABI) against the FP64 CPU oracle.
+
+Covers every hot-path step: operator apply (FP64 and FP32), right-hand side,
+reduced-approach preconditioner (FP64 DGEMM form and tcgen05 TF32/BF16 form),
+MO-PCG solves (FP64 form and mixed form with refinement), batching, the IMEX
+step, error reporting, determinism, and the full-size P2 2049 x 2049 workload
+of bench.py (sampled outputs and size-independent properties).
+
+Tolerances (written per test) follow from the arithmetic:
+* FP64 apply / rhs: a sum of at most 8 * 81 products -> 1e-13 of max |Y|.
+* FP32 apply: forward error of the two-stage sums in difference form
+  (row sum x_r + sum A_rj (x_j - x_r)), elementwise
+  |err| <= 2 (P + NT P + 2) u32 (|S| |X| |T|^T)  with u32 = 2^-24.
+* tensor-core preconditioner vs FP64: operands rounded to BF16 (u = 2^-9) or
+  truncated to TF32 (2^-10) in four chained GEMMs: Frobenius 2.5e-2 / 1.5e-2.
+* solves: relative error <= 1e-8 against the oracle's 1e-13-residual solution
+  and FP64 true residual <= rtol = 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle.operator import Problem, apply_terms, rhs, apply_entry
+from oracle import pcg
+from paper_2109_01173_gb300.inputs import Profile, ZERO, SIN_TOP, fourier_f, metric_instance
+
+pytestmark = pytest.mark.gpu
+
+TWO = (Profile(c2=0.1), Profile(c0=1.0, ca=0.2, cf=1.0))
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    torch.cuda.set_device(0)
+    import paper_2109_01173_gb300.mofem as m
+    return m
+
+
+def torch_():
+    import torch
+    return torch
+
+
+def live(P):
+    return [(S, T) for S, T in P.terms() if abs(S).sum() > 0]
+
+
+def dom(name):
+    return (ZERO, SIN_TOP) if name == "one" else TWO
+
+
+# (k, n, domain, bc): several 128-column tiles and ~65-row tiles with ragged tails
+APPLY_CASES = [(2, 301, "one", 0), (1, 200, "two", 1), (4, 161, "two", 0), (0, 150, "one", 0),
+               (3, 151, "one", 1), (2, 263, "two", 1), (1, 5, "one", 0), (2, 5, "two", 0)]
+
+
+@pytest.mark.parametrize("k,n,dname,bc", APPLY_CASES)
+def test_apply_parity(mf, k, n, dname, bc):
+    torch = torch_()
+    g1, g2 = dom(dname)
+    P = Problem(g1, g2, k, n, 0.7, bc="dirichlet" if bc == 0 else "neumann")
+    h = mf.Handle(g1, g2, k, n, 0.7, bc=bc)
+    q = h.q
+    X = np.random.default_rng(k * 1000 + n).standard_normal((q, q))
+    Yo = apply_terms(live(P), X)
+    # FP64 (padded leading dimension exercises ld != q)
+    ld = q + 3
+    Xt = torch.zeros((q, ld), dtype=torch.float64, device="cuda")
+    Xt[:, :q] = torch.tensor(X, device="cuda")
+    Yt = torch.full((q, ld), 7.0, dtype=torch.float64, device="cuda")
+    h.apply(Xt, Yt, "fp64", ld=ld)
+    Y = Yt[:, :q].cpu().numpy()
+    assert np.abs(Y - Yo).max() <= 1e-13 * np.abs(Yo).max()
+    assert torch.all(Yt[:, q:] == 7.0)                       # padding untouched
+    # FP32: elementwise forward-error bound of the two-stage sums
+    X32 = X.astype(np.float32)
+    Yo32 = apply_terms(live(P), X32.astype(np.float64))
+    absb = apply_terms([(abs(S), abs(T)) for S, T in live(P)], np.abs(X32.astype(np.float64)))
+    Pw = 2 * max(k, 1) + 1
+    bound = 2 * (Pw + h.n_terms * Pw + 2) * U32 * absb
+    Xf = torch.tensor(X32, device="cuda")
+    Yf = torch.zeros_like(Xf)
+    h.apply(Xf, Yf, "bf16")
+    err = np.abs(Yf.cpu().numpy().astype(np.float64) - Yo32)
+    assert np.all(err <= bound + 1e-30)
+    h.close()
+
+
+@pytest.mark.parametrize("k,n,dname,bc", APPLY_CASES[:5])
+def test_rhs_parity(mf, k, n, dname, bc):
+    torch = torch_()
+    g1, g2 = dom(dname)
+    P = Problem(g1, g2, k, n, 0.7, bc="dirichlet" if bc == 0 else "neumann")
+    h = mf.Handle(g1, g2, k, n, 0.7, bc=bc)
+    F = np.random.default_rng(n).standard_normal((n, n))
+    Bt = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    h.rhs(torch.tensor(F, device="cuda"), Bt)
+    Bo = rhs(P, F)
+    assert np.abs(Bt.cpu().numpy() - Bo).max() <= 1e-13 * np.abs(Bo).max()
+    h.close()
+
+
+@pytest.mark.parametrize("k,n,dname,bc", [(2, 301, "one", 0), (1, 200, "two", 1), (4, 161, "two", 0),
+                                          (0, 150, "one", 0), (2, 5, "one", 0)])
+def test_precond_parity(mf, k, n, dname, bc):
+    torch = torch_()
+    g1, g2 = dom(dname)
+    P = Problem(g1, g2, k, n, 0.7, bc="dirichlet" if bc == 0 else "neumann")
+    h = mf.Handle(g1, g2, k, n, 0.7, bc=bc)
+    E1, E2, F1, F2 = P.pencils()
+    Zo = pcg.ReducedSylvester(E1, E2, F1, F2)(np.random.default_rng(1).standard_normal((h.q, h.q)))
+    R = np.random.default_rng(1).standard_normal((h.q, h.q))
+    Zt = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    h.precond(torch.tensor(R, device="cuda"), Zt, "fp64")
+    Z = Zt.cpu().numpy()
+    assert np.linalg.norm(Z - Zo) <= 1e-9 * np.linalg.norm(Zo)
+    back = E1 @ Z @ F1.T + E2 @ Z @ F2.T
+    assert np.linalg.norm(back - R) <= 1e-9 * np.linalg.norm(R)
+    for prec, tol in (("bf16", 2.5e-2), ("tf32", 1.5e-2)):
+        Zf = torch.zeros((h.q, h.q), dtype=torch.float32, device="cuda")
+        h.precond(torch.tensor(R, dtype=torch.float32, device="cuda"), Zf, prec)
+        Zm = Zf.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(Zm - Zo) <= tol * np.linalg.norm(Zo), prec
+    h.close()
+
+
+SOLVE_CASES = [(2, 129, "one", 0, 1.0), (1, 97, "two", 1, 2.0), (4, 81, "two", 0, 0.0), (0, 101, "one", 0, 1.0),
+               (3, 64, "one", 1, 0.5)]
+
+
+@pytest.mark.parametrize("k,n,dname,bc,gamma", SOLVE_CASES)
+@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32"])
+def test_solve_parity(mf, k, n, dname, bc, gamma, prec):
+    torch = torch_()
+    g1, g2 = dom(dname)
+    P = Problem(g1, g2, k, n, gamma, bc="dirichlet" if bc == 0 else "neumann")
+    F = fourier_f(g1, g2, n, seed=n + k)
+    Uo, _ = pcg.solve(P, F, rtol=1e-13)
+    h = mf.Handle(g1, g2, k, n, gamma, bc=bc)
+    U = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(torch.tensor(F, device="cuda"), U, rtol=1e-10, max_iter=400, precision=prec)
+    assert code == 0 and info.rel_residual <= 1e-10
+    Ug = U.cpu().numpy()
+    assert np.linalg.norm(Ug - Uo) <= 1e-8 * np.linalg.norm(Uo)
+    # the oracle's own FP64 residual of the GPU solution
+    B = rhs(P, F)
+    assert np.linalg.norm(B - apply_terms(live(P), Ug)) <= 1.5e-10 * np.linalg.norm(B)
+    h.close()
+
+
+def test_batched_solve(mf):
+    torch = torch_()
+    n, k = 97, 2
+    g2s = [Profile(c0=1.0, sa=0.1, sf=1), Profile(c0=1.0, sa=0.25, sf=2), Profile(c0=1.0, sa=0.3, sf=3)]
+    gam = [0.0, 3.5, 9.0]
+    Fs = [fourier_f(ZERO, g, n, seed=i) for i, g in enumerate(g2s)]
+    h = mf.Handle([ZERO] * 3, g2s, k, n, gam)
+    U = torch.zeros((3, h.q, h.q), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(torch.tensor(np.stack(Fs), device="cuda"), U, rtol=1e-10, max_iter=400,
+                             precision="bf16")
+    assert code == 0
+    for i in range(3):
+        Uo, _ = pcg.solve(Problem(ZERO, g2s[i], k, n, gam[i]), Fs[i], rtol=1e-13)
+        assert np.linalg.norm(U[i].cpu().numpy() - Uo) <= 1e-8 * np.linalg.norm(Uo), i
+    h.close()
+
+
+def test_deterministic(mf):
+    torch = torch_()
+    inst = metric_instance(n=129, k=2, seed=3)
+    h = mf.Handle(inst["g1"], inst["g2"], 2, 129, 1.0)
+    F = torch.tensor(inst["F"], device="cuda")
+    out = []
+    for _ in range(2):
+        U = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+        h.pcg_solve(F, U, rtol=1e-10, max_iter=300, precision="bf16")
+        out.append(U.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+    h.close()
+
+
+def test_error_reporting(mf):
+    torch = torch_()
+    inst = metric_instance(n=65, k=1, seed=0)
+    h = mf.Handle(inst["g1"], inst["g2"], 1, 65, 1.0, opts=mf.make_opts(max_outer=1))
+    F = torch.tensor(inst["F"], device="cuda")
+    U = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(F, U, rtol=1e-10, max_iter=1, precision="bf16", check=False)
+    assert code == mf.ERR_NOT_CONVERGED and info.iterations == 1
+    Fn = F.clone()
+    Fn[10, 10] = float("nan")
+    U.zero_()
+    info, code = h.pcg_solve(Fn, U, rtol=1e-10, max_iter=50, precision="fp64", check=False)
+    assert code == mf.ERR_NONFINITE
+    h.close()
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_imex_step(mf, bc):
+    """One IMEX Euler step (Sec. 6): (M + d tau A) U1 = M (U0 + tau f), stop ||R_s|| <= tau ||R_0||."""
+    torch = torch_()
+    n, k, du, tau = 65, 2, 0.05, 1e-3
+    g1, g2 = Profile(c2=0.1), Profile(c0=1.0, ca=0.2, cf=1.0)
+    gam = 1.0 / (du * tau)
+    P = Problem(g1, g2, k, n, gam, bc="dirichlet" if bc == 0 else "neumann")
+    q = P.q
+    rng = np.random.default_rng(0)
+    U0 = rng.uniform(0, 1, (q, q))
+    Fn = rng.standard_normal((n, n))
+    h = mf.Handle(g1, g2, k, n, gam, bc=bc)
+    Ut = torch.zeros((q, q), dtype=torch.float64, device="cuda")
+    info, code = h.imex_step(du, tau, torch.tensor(U0, device="cuda"), torch.tensor(Fn, device="cuda"), Ut,
+                             precision="bf16")
+    assert code == 0
+    off = 1 if bc == 0 else 0
+    Fbar = gam * tau * Fn
+    Fbar[off:off + q, off:off + q] += gam * U0
+    B = rhs(P, Fbar)
+    L = lambda X: apply_terms(live(P), X)
+    r0 = np.linalg.norm(B - L(U0))
+    r1 = np.linalg.norm(B - L(Ut.cpu().numpy()))
+    assert r1 <= tau * r0
+    h.close()
+
+
+# ---- full-size workload of bench.py: P2, 2049 x 2049 nodes -----------------------------
+@pytest.fixture(scope="module")
+def full(mf):
+    torch = torch_()
+    inst = metric_instance(n=2049, k=2, seed=0)
+    P = Problem(inst["g1"], inst["g2"], 2, 2049, 1.0)
+    h = mf.Handle(inst["g1"], inst["g2"], 2, 2049, 1.0)
+    yield inst, P, h
+    h.close()
+
+
+def test_full_size_sampled_apply(mf, full):
+    torch = torch_()
+    inst, P, h = full
+    q = h.q
+    X = np.random.default_rng(11).standard_normal((q, q))
+    Xt = torch.tensor(X, device="cuda")
+    Yt = torch.zeros_like(Xt)
+    h.apply(Xt, Yt, "fp64")
+    Y = Yt.cpu().numpy()
+    terms = live(P)
+    rng = np.random.default_rng(12)
+    pts = [(0, 0), (q - 1, q - 1), (0, q - 1), (q - 1, 0), (127, 128), (64, 2046)]
+    pts += [tuple(p) for p in rng.integers(0, q, size=(40, 2))]
+    scale = np.abs(Y).max()
+    for a, b in pts:
+        assert abs(Y[a, b] - apply_entry(terms, X, a, b)) <= 1e-13 * scale, (a, b)
+
+
+def test_full_size_solve(mf, full):
+    torch = torch_()
+    inst, P, h = full
+    F = torch.tensor(inst["F"], device="cuda")
+    U = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(F, U, rtol=1e-10, max_iter=500, precision="bf16")
+    assert code == 0
+    Ug = U.cpu().numpy()
+    B = rhs(P, inst["F"])
+    res = np.linalg.norm(B - apply_terms(live(P), Ug)) / np.linalg.norm(B)
+    assert res <= 1.5e-10
+    U64 = torch.zeros_like(U)
+    info64, code64 = h.pcg_solve(F, U64, rtol=1e-10, max_iter=500, precision="fp64")
+    assert code64 == 0
+    assert float(((U64 - U).norm() / U64.norm()).item()) <= 1e-8
