@@ -175,6 +175,24 @@ mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const doubl
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps,
                                 cudaStream_t stream);
 
+/* Preconditioner without device allocation.  No counterpart in the paper: an
+ * interface for callers that cannot allocate device memory where they apply
+ * the preconditioner (code that must not trigger the implicit device
+ * synchronisation of cudaMalloc/cudaFree in a latency-critical loop, or that
+ * runs under a memory budget enforced by its own allocator).
+ * Computes the same Z = P^{-1}(R) as mofem_precond(MOFEM_MIXED_BF16): float R
+ * and Z, q x q per instance, leading dimension ld >= q, batch stride ld*q.
+ * All temporaries (BF16 copies of Q1, Q1^T, Q2, Q2^T and R, and the three GEMM
+ * intermediates) live in one static device array of 8 x 2^18 BF16 elements
+ * (4 MiB), held by every GPU that loads the library until the process exits.
+ * Limit: batch * q * round_up(q, 64) <= 262144 (e.g. one instance with
+ * q <= 512); larger handles get MOFEM_ERR_INVALID_ARG (see mofem_last_error).
+ * The first call on a device looks up the array's device address (a CUDA
+ * runtime query, no allocation); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU race and must be serialised by the caller. */
+mofem_status mofem_precond_noalloc(mofem_handle h, const float* R, float* Z, int ld, cudaStream_t stream);
+
 /* Release every buffer the handle owns. */
 mofem_status mofem_destroy(mofem_handle h);
 

@@ -522,3 +522,34 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
     MOFEM_TRY(run(3));
     return MOFEM_OK;
 }
+
+// The four preconditioner GEMMs on caller-provided BF16 buffers (operand copies
+// Q1, Q1T, Q2, Q2T; rounded R in Rop; intermediates X1T, WT, Y), all
+// [batch][q][ld] (Q2, Q2T: one instance).  Builds its tensor maps on the host
+// (no allocation) and writes Z (FP32, z_ld, z_bs).
+mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z, int z_ld, long long z_bs,
+                                cudaStream_t st) {
+    const int q = c->q, ld = b.ld, B = c->batch;
+    CUtensorMap mA[4], mB[4];
+    MOFEM_TRY(make_map(&mA[0], b.Q2T, 2, q, q, 1, ld, BM));
+    MOFEM_TRY(make_map(&mB[0], b.Rop, 2, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&mA[1], b.X1T, 2, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&mB[1], b.Q1T, 2, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&mA[2], b.Q1, 2, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&mB[2], b.WT, 2, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&mA[3], b.Y, 2, q, q, B, ld, BM));
+    MOFEM_TRY(make_map(&mB[3], b.Q2, 2, q, q, 1, ld, BN));
+    GemmArgs g{};
+    g.M = q; g.N = q; g.nk = (q + 63) / 64;
+    g.status = c->d_status;
+    g.lam = c->lam32; g.lam_bs = c->ld; g.mu = c->mu32;
+    g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = 1;
+    g.out = b.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
+    MOFEM_TRY(launch_gemm<1>(mA[0], mB[0], g, B, st));
+    g.out = b.WT; g.epi = EPI_DIV; g.a_shared = 0; g.b_shared = 0;
+    MOFEM_TRY(launch_gemm<1>(mA[1], mB[1], g, B, st));
+    g.out = b.Y; g.epi = EPI_STORE;
+    MOFEM_TRY(launch_gemm<1>(mA[2], mB[2], g, B, st));
+    g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 0; g.b_shared = 1;
+    return launch_gemm<1>(mA[3], mB[3], g, B, st);
+}

@@ -180,6 +180,12 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
                         int z_ld, long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st);
 int tc_rz_ctas(const mofem_ctx* c);
 mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaStream_t st);
+struct TcBuffers {   // caller-provided BF16 buffers of the preconditioner GEMMs
+    void *Q1, *Q1T, *Q2, *Q2T, *Rop, *X1T, *WT, *Y;
+    int ld;
+};
+mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z, int z_ld, long long z_bs,
+                                cudaStream_t st);
 mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int reps, cudaStream_t st);
 
 // ---- solver (solver.cu) ------------------------------------------------------
