@@ -287,7 +287,7 @@ def run_mofem(a):
     tg = statistics.mean(t_gemm)
     peak_t = peaks["bf16_tflops"] if prec_k == "bf16" else peaks["bf16_tflops"] / 2.0
     apply_bytes = 4.0 * B * q * q * 4      # read Q_prev, Z; write Q_new, L(Q)   (FP32)
-    upd_bytes = 30.0 * B * q * q          # read U,R,Q,LQ,Z_old; write U,R (FP32) and R (BF16)
+    upd_bytes = 38.0 * B * q * q          # read dU hi/lo, R, Q, LQ, Z_old; write dU hi/lo, R (FP32), R (BF16)
 
     # ---- FP64 form (same instances, same stopping rule) ------------------------------
     fp64 = None

@@ -92,18 +92,43 @@ __device__ __forceinline__ double compute_tile(const T* Xs, int ws, int c0, cons
         if constexpr (TSMEM) return Ts[(i * P + l) * TB + tid];
         else return tc[i][l];
     };
+    // Term 0, (K_s[h] + gamma M_s[h]) (x) M_t, is the one whose t-factor is a mass
+    // and whose s-factor is a stiffness: an FP32 rounding of the t-pass value would
+    // be amplified by the s-stiffness by ~(mesh size)^-2 on smooth fields.  With
+    // D = diag(rowsum M_t) and N = D^{-1}(M_t - D) (zero row sums), the t-pass is
+    // split exactly as X M_t^T = D (X + X N^T): the s-pass is applied separately to
+    // the exact staged column X and to the small W' = X N^T, and the sum is scaled
+    // by D_b once.  Other terms first apply their stiffness/derivative factor.
+    constexpr bool SPLIT0 = NT > 1 && sizeof(T) == 4;   // FP64 keeps enough digits in the t-mass product
     T ring[NT][P];
+    T xr0[SPLIT0 ? P : 1];
+    T n0[SPLIT0 ? P : 1];   // N coefficients of term 0 (row b of D^{-1} M_t off the diagonal)
+    T d0 = (T)1;
+    if constexpr (SPLIT0) {
+        d0 = tcoef(0, K);
+        const T dinv = d0 != (T)0 ? (T)1 / d0 : (T)0;
+#pragma unroll
+        for (int l = 0; l < P; ++l) n0[l] = (l == K) ? (T)0 : tcoef(0, l) * dinv;
+    }
     auto tpass = [&](int lr, int slot) {
         T xv[P];
         const T* row = Xs + lr * ws + c0 + tid - K;
 #pragma unroll
         for (int l = 0; l < P; ++l) xv[l] = row[l];
         const T xc = xv[K];
+        if constexpr (SPLIT0) xr0[slot] = xc;
 #pragma unroll
         for (int l = 0; l < P; ++l)
             if (l != K) xv[l] -= xc;
+        if constexpr (SPLIT0) {
+            T w = (T)0;
 #pragma unroll
-        for (int i = 0; i < NT; ++i) {
+            for (int l = 0; l < P; ++l)
+                if (l != K) w = fma(n0[l], xv[l], w);
+            ring[0][slot] = w;
+        }
+#pragma unroll
+        for (int i = SPLIT0 ? 1 : 0; i < NT; ++i) {
             T w = tcoef(i, K) * xc;
 #pragma unroll
             for (int l = 0; l < P; ++l)
@@ -113,7 +138,7 @@ __device__ __forceinline__ double compute_tile(const T* Xs, int ws, int c0, cons
     };
 #pragma unroll
     for (int lr = 0; lr < 2 * K; ++lr) tpass(lr, lr);
-    double acc = 0.0;
+    T accT = (T)0;   // per-thread partial of <X, Y> or <Y, Y> (working precision; few terms)
     for (int m = 0; m < MR; ++m) {
 #pragma unroll
         for (int u = 0; u < P; ++u) {
@@ -121,8 +146,19 @@ __device__ __forceinline__ double compute_tile(const T* Xs, int ws, int c0, cons
             tpass(al + 2 * K, (u + P - 1) % P);
             const T* srow = Ss + al * SR;
             T y = (T)0;
+            if constexpr (SPLIT0) {
+                const T xc = xr0[(u + K) % P], wc = ring[0][(u + K) % P];
+                T ya = srow[K] * xc, yb = srow[K] * wc;
 #pragma unroll
-            for (int i = 0; i < NT; ++i) {
+                for (int j = 0; j < P; ++j)
+                    if (j != K) {
+                        ya = fma(srow[j], xr0[(u + j) % P] - xc, ya);
+                        yb = fma(srow[j], ring[0][(u + j) % P] - wc, yb);
+                    }
+                y = d0 * (ya + yb);
+            }
+#pragma unroll
+            for (int i = SPLIT0 ? 1 : 0; i < NT; ++i) {
                 const T wc = ring[i][(u + K) % P];
                 y = fma(srow[i * P + K], wc, y);
                 if ((DM >> i) & 1u) {
@@ -140,15 +176,15 @@ __device__ __forceinline__ double compute_tile(const T* Xs, int ws, int c0, cons
                 const size_t o = (size_t)ar * y_ld + b;
                 if (MODE == APPLY_RESIDUAL) {
                     y = Bm[o] - y;
-                    acc += (double)y * (double)y;
+                    accT = fma(y, y, accT);
                 } else if (want_xy) {
-                    acc += (double)Xs[(al + K) * ws + c0 + tid] * (double)y;
+                    accT = fma(Xs[(al + K) * ws + c0 + tid], y, accT);
                 }
                 Y[o] = y;
             }
         }
     }
-    return acc;
+    return (double)accT;
 }
 
 template <typename T, int K, int NT, bool TSMEM, int TA>

@@ -54,7 +54,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 struct UpdArgs {
-    void* U; void* R; const void* Q; const void* LQ; const void* Zold; void* Rop;
+    void* U;             // iterate: T (FP64 form) or the hi part of the double-float correction (mixed)
+    void* Ulo;           // lo part (mixed form)
+    void* R; const void* Q; const void* LQ; const void* Zold; void* Rop;
     long long bs;        // batch stride (elements) = q * ld
     long long nvec;      // 16-byte vectors per instance
     double* rr_part; double* rzo_part; int n_upd;
@@ -76,10 +78,6 @@ __device__ __forceinline__ void axpy_v(float4& u, const float4& q, float a) {
 __device__ __forceinline__ void axpy_v(double2& u, const double2& q, double a) {
     u.x = fma(a, q.x, u.x); u.y = fma(a, q.y, u.y);
 }
-__device__ __forceinline__ double dot_v(const float4& a, const float4& b) {
-    return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
-}
-__device__ __forceinline__ double dot_v(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
 
 __device__ __forceinline__ uint2 pack_bf16x4(const float4& r) {
     __nv_bfloat162 lo = __floats2bfloat162_rn(r.x, r.y);
@@ -90,20 +88,63 @@ __device__ __forceinline__ uint2 pack_bf16x4(const float4& r) {
     return pk;
 }
 
-// One vector step of the update, accumulating ||R||^2 and <R_new, Z_old>.
-template <typename T, int ROP, typename V>
-__device__ __forceinline__ void upd_one(V& u, V& r, const V& qv, const V& lq, const V& zo, T alpha, int flex,
-                                        double& rr, double& rzo, uint2* rb) {
-    axpy_v(u, qv, alpha);
-    axpy_v(r, lq, -alpha);
-    rr += dot_v(r, r);
-    if (flex) rzo += dot_v(r, zo);
-    if constexpr (ROP == 1) *rb = pack_bf16x4(r);
+// Iterate storage.  FP64 form: U in FP64.  Mixed form: the inner correction is
+// accumulated as a double-float pair (hi, lo) of FP32 arrays with error-free
+// transformations (exact product alpha*q via FMA, TwoSum, renormalisation), so
+// its precision (~2^-48) never limits the refinement, while all arithmetic stays
+// on the FP32 pipes (FP64 throughput on this GPU is a small fraction of FP32).
+struct DF { float4 h, l; };
+
+__device__ __forceinline__ void df_add_prod(float& h, float& l, float a, float q) {
+    const float p = a * q;
+    const float e = fmaf(a, q, -p);          // a*q = p + e exactly
+    const float s = h + p;
+    const float v = s - h;
+    float t = (h - (s - v)) + (p - v);       // TwoSum(h, p) error
+    t += l + e;
+    h = s + t;                               // renormalise
+    l = t - (h - s);
 }
+
+template <typename T, bool MIXED>
+struct UVec;
+template <typename T>
+struct UVec<T, false> {   // plain iterate in T
+    using V = typename Vec<T>::type;
+    struct Val { V a; };
+    V* p;
+    __device__ __forceinline__ Val load(long long i) const { return Val{p[i]}; }
+    __device__ __forceinline__ void axpy_store(long long i, Val u, const V& q, T a) {
+        axpy_v(u.a, q, a);
+        p[i] = u.a;
+    }
+};
+template <>
+struct UVec<float, true> {   // double-float correction
+    struct Val { float4 h, l; };
+    float4* ph;
+    float4* pl;
+    __device__ __forceinline__ Val load(long long i) const { return Val{ph[i], pl[i]}; }
+    __device__ __forceinline__ void axpy_store(long long i, Val u, const float4& q, float a) {
+        df_add_prod(u.h.x, u.l.x, a, q.x);
+        df_add_prod(u.h.y, u.l.y, a, q.y);
+        df_add_prod(u.h.z, u.l.z, a, q.z);
+        df_add_prod(u.h.w, u.l.w, a, q.w);
+        ph[i] = u.h;
+        pl[i] = u.l;
+    }
+};
+
+__device__ __forceinline__ float dot32(const float4& a, const float4& b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+__device__ __forceinline__ double dot32(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
 
 // ROP: 0 = no operand copy, 1 = BF16 copy of R for the tensor-core GEMM.
 // alpha is read from the scalar state (set by the apply kernel's last CTA).
-template <typename T, int ROP>
+// Dot products: working precision within a thread (a few dozen terms), FP64
+// across threads and CTAs (fixed order).
+template <typename T, bool MIXED, int ROP>
 __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
     using V = typename Vec<T>::type;
     static_assert(ROP == 0 || Vec<T>::W == 4, "BF16 operand copy is produced by the FP32 update only");
@@ -114,7 +155,13 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
     const bool active = !g.use_sc || sc->active;
     if (active) {
         const T alpha = g.use_sc ? (T)sc->alpha : (T)0.5;
-        V* U = reinterpret_cast<V*>(reinterpret_cast<T*>(g.U) + (size_t)inst * g.bs);
+        UVec<T, MIXED> U;
+        if constexpr (MIXED) {
+            U.ph = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.U) + (size_t)inst * g.bs);
+            U.pl = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.Ulo) + (size_t)inst * g.bs);
+        } else {
+            U.p = reinterpret_cast<V*>(reinterpret_cast<T*>(g.U) + (size_t)inst * g.bs);
+        }
         V* R = reinterpret_cast<V*>(reinterpret_cast<T*>(g.R) + (size_t)inst * g.bs);
         const V* Q = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Q) + (size_t)inst * g.bs);
         const V* LQ = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.LQ) + (size_t)inst * g.bs);
@@ -122,37 +169,36 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
         uint2* Rb = nullptr;
         if constexpr (ROP == 1)
             Rb = reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(g.Rop) + (size_t)inst * g.bs);
-        double rr = 0.0, rzo = 0.0;
+        T rrt = (T)0, rzt = (T)0;
         const long long stride = (long long)gridDim.x * blockDim.x;
         constexpr int UNR = 4;   // independent 16-byte loads in flight per thread and array
         long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        using UV = typename UVec<T, MIXED>::Val;
+        auto body = [&](long long i, UV u, V r, const V& qv, const V& lq, const V& zo) {
+            U.axpy_store(i, u, qv, alpha);
+            axpy_v(r, lq, -alpha);
+            R[i] = r;
+            rrt += dot32(r, r);
+            if (g.flex) rzt += dot32(r, zo);
+            if constexpr (ROP == 1) Rb[i] = pack_bf16x4(r);
+        };
         for (; i0 + (UNR - 1) * stride < g.nvec; i0 += UNR * stride) {
-            V u[UNR], r[UNR], qv[UNR], lq[UNR], zo[UNR];
+            UV u[UNR];
+            V r[UNR], qv[UNR], lq[UNR], zo[UNR];
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {
                 const long long i = i0 + k * stride;
-                u[k] = U[i];
+                u[k] = U.load(i);
                 r[k] = R[i];
                 qv[k] = Q[i];
                 lq[k] = LQ[i];
-                if (g.flex) zo[k] = Zo[i];
-                else zo[k] = qv[k];
+                zo[k] = g.flex ? Zo[i] : qv[k];
             }
 #pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const long long i = i0 + k * stride;
-                upd_one<T, ROP>(u[k], r[k], qv[k], lq[k], zo[k], alpha, g.flex, rr, rzo, Rb ? Rb + i : nullptr);
-                U[i] = u[k];
-                R[i] = r[k];
-            }
+            for (int k = 0; k < UNR; ++k) body(i0 + k * stride, u[k], r[k], qv[k], lq[k], zo[k]);
         }
-        for (; i0 < g.nvec; i0 += stride) {
-            V u = U[i0], r = R[i0];
-            const V zo = g.flex ? Zo[i0] : Q[i0];
-            upd_one<T, ROP>(u, r, Q[i0], LQ[i0], zo, alpha, g.flex, rr, rzo, Rb ? Rb + i0 : nullptr);
-            U[i0] = u;
-            R[i0] = r;
-        }
+        for (; i0 < g.nvec; i0 += stride) body(i0, U.load(i0), R[i0], Q[i0], LQ[i0], g.flex ? Zo[i0] : Q[i0]);
+        const double rr = (double)rrt, rzo = (double)rzt;
         const double s1 = block_sum<UPD_THREADS>(rr, sh);
         const double s2 = block_sum<UPD_THREADS>(rzo, sh);
         if (threadIdx.x == 0) {
@@ -334,6 +380,19 @@ __global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const d
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) row[j] /= (li + mu[j]);
 }
 
+// U64 += hi + lo (end of an inner solve of the mixed form), then hi = lo = 0.
+__global__ void k_fold_df(double* U, long long bs, float* hi, float* lo, long long n) {
+    const int inst = blockIdx.y;
+    U += (size_t)inst * bs;
+    hi += (size_t)inst * bs;
+    lo += (size_t)inst * bs;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        U[i] += (double)hi[i] + (double)lo[i];
+        hi[i] = 0.f;
+        lo[i] = 0.f;
+    }
+}
+
 __global__ void k_axpy_into64(double* U, long long u_bs, int u_ld, const float* d, long long d_bs, int d_ld, int q) {
     const int inst = blockIdx.z, r = blockIdx.y;
     double* u = U + (size_t)inst * u_bs + (size_t)r * u_ld;
@@ -344,11 +403,11 @@ __global__ void k_axpy_into64(double* U, long long u_bs, int u_ld, const float* 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* R, const void* Q, const void* LQ,
-                               const void* Zold, void* Rop, int rop_kind, int flex, int max_iter, bool fixed,
-                               const cudaGraphConditionalHandle* cond, cudaStream_t st, bool use_scalars) {
+mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo, void* R, const void* Q,
+                               const void* LQ, const void* Zold, void* Rop, int rop_kind, int flex, int max_iter,
+                               bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st, bool use_scalars) {
     UpdArgs g;
-    g.U = U; g.R = R; g.Q = Q; g.LQ = LQ; g.Zold = Zold; g.Rop = Rop;
+    g.U = U; g.Ulo = Ulo; g.R = R; g.Q = Q; g.LQ = LQ; g.Zold = Zold; g.Rop = Rop;
     g.bs = (long long)c->q * c->ld;
     g.nvec = g.bs / (fp64 ? 2 : 4);
     g.rr_part = c->part.rr; g.rzo_part = c->part.rzo; g.n_upd = c->part.n_upd;
@@ -362,9 +421,9 @@ mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* R, 
     g.has_cond = (cond && use_scalars) ? 1 : 0;
     g.cond = cond ? *cond : 0;
     dim3 grid(c->part.n_upd, c->batch);
-    if (fp64) k_update<double, 0><<<grid, UPD_THREADS, 0, st>>>(g);
-    else if (rop_kind == 1) k_update<float, 1><<<grid, UPD_THREADS, 0, st>>>(g);
-    else k_update<float, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+    if (fp64) k_update<double, false, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+    else if (rop_kind == 1) k_update<float, true, 1><<<grid, UPD_THREADS, 0, st>>>(g);
+    else k_update<float, true, 0><<<grid, UPD_THREADS, 0, st>>>(g);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }
@@ -449,6 +508,13 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
                                 int q, int batch, cudaStream_t st) {
     dim3 grid((q + 255) / 256, q, batch);
     k_axpy_into64<<<grid, 256, 0, st>>>(U64, u_bs, u_ld, dU, d_bs, d_ld, q);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, cudaStream_t st) {
+    dim3 grid(592, batch);
+    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

@@ -13,14 +13,15 @@
 //   G3: D[a][j] = sum_i Q1[a][i] WT[j][i]     -> Y[a][j]     (Y = Q1 W)
 //   G4: D[a][b] = sum_j Y[a][j] Q2[b][j]      -> Z[a][b]     (Z = Y Q2^T), + <R, Z> partials
 //
-// Kernel: one 128 x 256 output tile per CTA (M = 128 TMEM lanes, N = 256 FP32
-// TMEM columns), 128 threads.  Warp 0 lane 0 issues TMA loads of 128-byte-wide
-// K slices (SWIZZLE_128B) into a 4-stage shared-memory ring; warp 1 lane 0
-// issues tcgen05.mma (kind::f16 with BF16 operands or kind::tf32) and releases
-// stages with tcgen05.commit; warp 2 owns the TMEM allocation; all four warps
-// run the epilogue (tcgen05.ld 32x32b.x32).  Every mbarrier wait is bounded
-// (2 s of %globaltimer); on expiry the CTA records DEV_ERR_TIMEOUT, skips the
-// epilogue, frees its TMEM and exits.  No cluster multicast is used.
+// Kernel (k_gemm_p): 128 x 256 output tiles (M = 128 TMEM lanes, N = 256 FP32
+// TMEM columns), a persistent grid of one CTA per SM walking all tiles of all
+// instances.  TMA loads 128-byte-wide K slices (SWIZZLE_128B) into a 4-stage
+// shared-memory ring; one thread issues tcgen05.mma (kind::f16 with BF16
+// operands, or kind::tf32) and releases stages with tcgen05.commit; two TMEM
+// accumulators let the epilogue (tcgen05.ld 32x32b.x32) of one tile overlap the
+// mainloop of the next.  Every mbarrier wait is bounded (2 s of %globaltimer);
+// on expiry the CTA records DEV_ERR_TIMEOUT, stops all roles, frees its TMEM and
+// exits.  No cluster multicast is used.
 #include "internal.h"
 
 #include <cuda_bf16.h>
@@ -39,7 +40,7 @@ enum { EPI_STORE = 0, EPI_DIV = 1, EPI_Z = 2 };
 
 struct GemmArgs {
     void* out; long long out_bs; int out_ld; int out_bf16;
-    int M, N, nk;
+    int M, N, nk, batch;
     int a_shared, b_shared;
     int epi;
     const float* lam; long long lam_bs; const float* mu;
@@ -145,182 +146,258 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised variant (the one launched): one CTA per SM walks
+// the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of all instances.
+//   warps 0-3 : epilogue (TMEM lanes 0-127 = output rows), overlapping the next
+//               tile's mainloop thanks to two TMEM accumulators (2 x 256 columns)
+//   warp 4    : TMA producer (4-stage ring, 128-byte swizzled K slices)
+//   warp 5    : TMEM allocation and tcgen05.mma issue (one elected lane)
+// Barriers: full/empty per stage, tfull/tempty per accumulator.  Every wait is
+// bounded; a timeout raises a CTA-wide abort flag that ends all roles.
+constexpr int P_THREADS = 192;
+constexpr uint32_t TMEM_COLS_P = 512;
+
+struct PBars {
+    uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
+    uint32_t tmem_slot;
+    int abort;
+    double red[2][4];
+};
+
+__device__ __forceinline__ bool pwait(uint32_t a, uint32_t parity, volatile int* abort) {
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(a, parity)) {
+        if (*abort) return false;
+        if (gtimer() - t0 > WAIT_LIMIT_NS) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+// Epilogue of one 32-column chunk held by this thread (row m): divide, store
+// (16-byte vectors when aligned), and the <R, Z> accumulation of G4.
+__device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, int nb, float (&v)[32], float mu_m,
+                                          double& acc) {
+    const size_t obase = (size_t)inst * g.out_bs + (size_t)m * g.out_ld;
+    const bool vec_ok = (g.out_ld % 8) == 0;
+    if (g.epi == EPI_DIV) {
+        const float* lam = g.lam + (size_t)inst * g.lam_bs + nb;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], lam[j] + mu_m);
+    }
+    const bool full = vec_ok && nb + 32 <= g.N;
+    if (g.out_bf16) {
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(g.out) + obase + nb;
+        if (full) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                uint4 pk;
+                __nv_bfloat162 p0 = __floats2bfloat162_rn(v[j], v[j + 1]);
+                __nv_bfloat162 p1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
+                __nv_bfloat162 p2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
+                __nv_bfloat162 p3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
+                pk.x = *reinterpret_cast<uint32_t*>(&p0);
+                pk.y = *reinterpret_cast<uint32_t*>(&p1);
+                pk.z = *reinterpret_cast<uint32_t*>(&p2);
+                pk.w = *reinterpret_cast<uint32_t*>(&p3);
+                *reinterpret_cast<uint4*>(o + j) = pk;
+            }
+        } else {
+            for (int j = 0; j < 32 && nb + j < g.N; ++j) o[j] = __float2bfloat16_rn(v[j]);
+        }
+    } else {
+        float* o = reinterpret_cast<float*>(g.out) + obase + nb;
+        const float* r = (g.epi == EPI_Z && g.R) ? g.R + (size_t)inst * g.r_bs + (size_t)m * g.r_ld + nb : nullptr;
+        float a32 = 0.f;   // FP32 within the 32-column chunk, FP64 across chunks
+        if (full && (!r || (g.r_ld % 4) == 0)) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                if (r) {
+                    const float4 rv = *reinterpret_cast<const float4*>(r + j);
+                    a32 = fmaf(v[j], rv.x, a32);
+                    a32 = fmaf(v[j + 1], rv.y, a32);
+                    a32 = fmaf(v[j + 2], rv.z, a32);
+                    a32 = fmaf(v[j + 3], rv.w, a32);
+                }
+            }
+        } else {
+            for (int j = 0; j < 32 && nb + j < g.N; ++j) {
+                o[j] = v[j];
+                if (r) a32 = fmaf(v[j], r[j], a32);
+            }
+        }
+        acc += (double)a32;
+    }
+}
+
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
-    k_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
-    const int inst = blockIdx.z;
-    if (g.sc && !g.sc[inst].active) return;
+__global__ void __launch_bounds__(P_THREADS, 1)
+    k_gemm_p(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-    __shared__ double red[4];
+    PBars* pb = reinterpret_cast<PBars*>(smem + STAGES * STAGE_BYTES);
+    volatile int* abort_flag = &pb->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+    const int ntn = (g.N + BN - 1) / BN, ntm = (g.M + BM - 1) / BM;
+    const int per_inst = ntn * ntm;
+    const int total = per_inst * g.batch;
+    constexpr int BK = 128 / (KIND == 1 ? 2 : 4);
+    auto bar_addr = [&](uint64_t* b) { return smem_u32(b); };
+    auto active = [&](int inst) { return !g.sc || g.sc[inst].active; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(bar_addr(&pb->full[s]), 1);
+            mbar_init(bar_addr(&pb->empty[s]), 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_addr(&pb->tfull[b]), 1);
+            mbar_init(bar_addr(&pb->tempty[b]), 4);
+        }
+        pb->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB)) : "memory");
     }
-    if (warp == 2) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&pb->tmem_slot)),
+                     "r"(TMEM_COLS_P)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    bool ok = true;
+    const uint32_t tmem = pb->tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        const int za = g.a_shared ? 0 : inst, zb = g.b_shared ? 0 : inst;
-        for (int kb = 0; kb < g.nk; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
-                ok = false;
-                break;
-            }
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-            tma_load_3d(sa, &mA, full0 + 8 * s, kb * (128 / (KIND == 1 ? 2 : 4)), m0, za);
-            tma_load_3d(sa + A_BYTES, &mB, full0 + 8 * s, kb * (128 / (KIND == 1 ? 2 : 4)), n0, zb);
-        }
-    } else if (warp == 1 && lane == 0) {
-        for (int kb = 0; kb < g.nk; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(full0 + 8 * s, ph)) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)   // 4 x 32-byte K steps per 128-byte slice
-                mma<KIND>(tmem, make_desc(sa + 32 * kk), make_desc(sa + A_BYTES + 32 * kk), (kb | kk) != 0);
-            mma_commit(empty0 + 8 * s);
-        }
-        mma_commit(done);
-    }
-
-    // ---- epilogue: all 128 threads, thread = TMEM lane = output row m ----
-    ok = mbar_wait(done, 0) && ok;
-    __syncwarp();
-    ok = __syncthreads_and(ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    double acc = 0.0;
-    if (ok) {
-        // thread = TMEM lane = output row m; it holds 32 consecutive columns per
-        // tcgen05.ld and writes them as 16-byte vectors (row-major output).
-        const int m = m0 + warp * 32 + lane;
-        const bool m_ok = m < g.M;
-        float mu_m = 0.f;
-        if (g.epi == EPI_DIV && m_ok) mu_m = g.mu[m];
-        const size_t obase = (size_t)inst * g.out_bs + (size_t)m * g.out_ld;
-        const bool vec_ok = (g.out_ld % 8) == 0;
-#pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-            const int nb = n0 + c * 32;
-            if (!m_ok || nb >= g.N) continue;
-            if (g.epi == EPI_DIV) {
-                const float* lam = g.lam + (size_t)inst * g.lam_bs + nb;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], lam[j] + mu_m);
-            }
-            const bool full = vec_ok && nb + 32 <= g.N;
-            if (g.out_bf16) {
-                __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(g.out) + obase + nb;
-                if (full) {
-#pragma unroll
-                    for (int j = 0; j < 32; j += 8) {
-                        uint4 pk;
-                        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[j], v[j + 1]);
-                        __nv_bfloat162 p1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
-                        __nv_bfloat162 p2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
-                        __nv_bfloat162 p3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
-                        pk.x = *reinterpret_cast<uint32_t*>(&p0);
-                        pk.y = *reinterpret_cast<uint32_t*>(&p1);
-                        pk.z = *reinterpret_cast<uint32_t*>(&p2);
-                        pk.w = *reinterpret_cast<uint32_t*>(&p3);
-                        *reinterpret_cast<uint4*>(o + j) = pk;
-                    }
-                } else {
-                    for (int j = 0; j < 32 && nb + j < g.N; ++j) o[j] = __float2bfloat16_rn(v[j]);
+    if (warp == 4) {
+        if (lane == 0) {   // ---- TMA producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB)) : "memory");
+            int it = 0;
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+                const int inst = t / per_inst, r = t - inst * per_inst;
+                if (!active(inst)) continue;
+                const int m0 = (r / ntn) * BM, n0 = (r % ntn) * BN;
+                const int za = g.a_shared ? 0 : inst, zb = g.b_shared ? 0 : inst;
+                for (int kb = 0; kb < g.nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (it >= STAGES && !pwait(bar_addr(&pb->empty[s]), ph ^ 1u, abort_flag)) break;
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                    mbar_expect_tx(bar_addr(&pb->full[s]), STAGE_BYTES);
+                    tma_load_3d(sa, &mA, bar_addr(&pb->full[s]), kb * BK, m0, za);
+                    tma_load_3d(sa + A_BYTES, &mB, bar_addr(&pb->full[s]), kb * BK, n0, zb);
                 }
-            } else {
-                float* o = reinterpret_cast<float*>(g.out) + obase + nb;
-                const float* r = (g.epi == EPI_Z && g.R) ? g.R + (size_t)inst * g.r_bs + (size_t)m * g.r_ld + nb
-                                                         : nullptr;
-                if (full && (!r || (g.r_ld % 4) == 0)) {
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {   // ---- MMA issuer
+            int it = 0, tl = 0;
+            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+                const int inst = t / per_inst;
+                if (!active(inst)) continue;
+                const int b = tl & 1;
+                const uint32_t use = (uint32_t)(tl >> 1);
+                if (tl >= 2 && !pwait(bar_addr(&pb->tempty[b]), (use - 1u) & 1u, abort_flag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(b * 256);
+                bool ok = true;
+                for (int kb = 0; kb < g.nk; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!pwait(bar_addr(&pb->full[s]), ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                        if (r) {
-                            const float4 rv = *reinterpret_cast<const float4*>(r + j);
-                            acc += (double)v[j] * rv.x + (double)v[j + 1] * rv.y + (double)v[j + 2] * rv.z +
-                                   (double)v[j + 3] * rv.w;
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma<KIND>(d, make_desc(sa + 32 * kk), make_desc(sa + A_BYTES + 32 * kk), (kb | kk) != 0);
+                    mma_commit(bar_addr(&pb->empty[s]));
+                }
+                mma_commit(bar_addr(&pb->tfull[b]));
+                ++tl;
+                if (!ok) break;
+            }
+        }
+    } else {   // ---- epilogue warps 0-3: thread = TMEM lane = output row within the tile
+        int tl = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            const int inst = t / per_inst, r = t - inst * per_inst;
+            if (!active(inst)) continue;
+            const int m0 = (r / ntn) * BM, n0 = (r % ntn) * BN;
+            const int b = tl & 1;
+            const uint32_t use = (uint32_t)(tl >> 1);
+            const bool ok = pwait(bar_addr(&pb->tfull[b]), use & 1u, abort_flag);
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, ok)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m = m0 + warp * 32 + lane;
+            const bool m_ok = m < g.M;
+            float mu_m = 0.f;
+            if (g.epi == EPI_DIV && m_ok) mu_m = g.mu[m];
+            double acc = 0.0;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256 + c * 32), v);
+                const int nb = n0 + c * 32;
+                if (m_ok && nb < g.N) epi_chunk(g, inst, m, nb, v, mu_m, acc);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_addr(&pb->tempty[b]));
+            if (g.epi == EPI_Z && g.rz_part) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) pb->red[tl & 1][warp] = acc;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (warp == 0) {
+                    int last = 0;
+                    if (lane == 0) {
+                        const double* rd = pb->red[tl & 1];
+                        g.rz_part[(size_t)inst * per_inst + r] = rd[0] + rd[1] + rd[2] + rd[3];
+                        if (g.sc && g.counter) {
+                            __threadfence();
+                            const unsigned tk = atomicAdd(g.counter + inst, 1u);
+                            last = (tk == (unsigned)per_inst - 1) ? 1 : 0;
                         }
                     }
-                } else {
-                    for (int j = 0; j < 32 && nb + j < g.N; ++j) {
-                        o[j] = v[j];
-                        if (r) acc += (double)v[j] * (double)r[j];
+                    last = __shfl_sync(0xffffffffu, last, 0);
+                    if (last) {   // fixed-order sum of this instance's partials: rz and beta
+                        __threadfence();
+                        double rz = 0.0;
+                        for (int i = lane; i < per_inst; i += 32) rz += __ldcg(g.rz_part + (size_t)inst * per_inst + i);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
+                        if (lane == 0) {
+                            g.counter[inst] = 0;
+                            PcgScalars* p = g.sc + inst;
+                            double beta = (rz - (g.flex ? p->rzo : 0.0)) / p->rz;
+                            if (!isfinite(beta)) beta = 0.0;
+                            p->beta = beta;
+                            p->rz = rz;
+                        }
                     }
                 }
             }
+            ++tl;
         }
-    } else if (threadIdx.x == 0 && g.status) {
-        atomicOr(g.status, DEV_ERR_TIMEOUT);
     }
-    if (g.epi == EPI_Z && g.rz_part) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) red[warp] = acc;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 2)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    if (g.epi == EPI_Z && g.rz_part) {
-        // <R, Z> partial; the last CTA of the instance sets rz and beta (fixed-order sum)
-        __shared__ int last_s;
-        const int nblk = gridDim.x * gridDim.y;
-        if (threadIdx.x == 0) {
-            g.rz_part[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = red[0] + red[1] + red[2] + red[3];
-            last_s = 0;
-            if (g.sc && g.counter) {
-                __threadfence();
-                const unsigned t = atomicAdd(g.counter + inst, 1u);
-                last_s = (t == (unsigned)nblk - 1) ? 1 : 0;
-            }
-        }
-        __syncthreads();
-        if (last_s && warp == 0) {
-            __threadfence();
-            double rz = 0.0;
-            for (int i = lane; i < nblk; i += 32) rz += __ldcg(g.rz_part + (size_t)inst * nblk + i);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
-            if (lane == 0) {
-                g.counter[inst] = 0;
-                PcgScalars* p = g.sc + inst;
-                double beta = (rz - (g.flex ? p->rzo : 0.0)) / p->rz;
-                if (!isfinite(beta)) beta = 0.0;
-                p->beta = beta;
-                p->rz = rz;
-            }
-        }
+    if (threadIdx.x == 0 && pb->abort && g.status) atomicOr(g.status, DEV_ERR_TIMEOUT);
+    if (warp == 5) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS_P) : "memory");
     }
 }
 
@@ -395,15 +472,30 @@ mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols,
 
 namespace {
 
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
 template <int KIND>
-mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch, cudaStream_t st) {
+mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g0, int batch, cudaStream_t st) {
     static bool attr = false;
+    const int smem = STAGES * STAGE_BYTES + 1024 + (int)sizeof(PBars) + 64;
     if (!attr) {
-        MOFEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        MOFEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_p<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr = true;
     }
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
-    k_gemm<KIND><<<grid, 128, SMEM_BYTES, st>>>(mA, mB, g);
+    GemmArgs g = g0;
+    g.batch = batch;
+    const int total = ((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * batch;
+    const int grid = total < num_sms() ? total : num_sms();
+    k_gemm_p<KIND><<<grid, P_THREADS, smem, st>>>(mA, mB, g);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

@@ -79,7 +79,8 @@ struct mofem_ctx {
     // FP64-form workspaces (lazily allocated)
     double* w64 = nullptr;     // 8 matrices [batch][q][ld]
     // mixed-form workspaces (lazily allocated)
-    float* w32 = nullptr;      // 7 matrices [batch][q][ld]: U, R, Z, Q0, Q1, LQ, tmp
+    float* w32 = nullptr;      // 6 matrices [batch][q][ld]: (spare), R, Z, Q_a, Q_b, L(Q)
+    double* U64m = nullptr;    // [batch][q][ld] FP64 iterate of the mixed form
     double* Bm64 = nullptr;    // [batch][q][ld] FP64 right-hand side
     double* R64 = nullptr;     // [batch][q][ld] FP64 true residual
     double* d_part = nullptr;  // partial sums

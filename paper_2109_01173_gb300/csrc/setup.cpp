@@ -471,7 +471,7 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
 }
 
 void mofem_free(mofem_ctx* c) {
-    void* ptrs[] = {c->S64, c->S32, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
+    void* ptrs[] = {c->U64m, c->S64, c->S32, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
                     c->lam32, c->mu32, c->w64, c->w32, c->Bm64, c->R64, c->d_part, c->d_sc, c->d_status,
                     c->d_red};
     for (void* p : ptrs) cudaFree(p);

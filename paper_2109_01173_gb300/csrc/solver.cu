@@ -23,13 +23,16 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include <algorithm>
 
-mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* R, const void* Q, const void* LQ,
-                               const void* Zold, void* Rop, int rop_kind, int flex, int max_iter, bool fixed,
-                               const cudaGraphConditionalHandle* cond, cudaStream_t st, bool use_scalars = true);
+mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo, void* R, const void* Q,
+                               const void* LQ, const void* Zold, void* Rop, int rop_kind, int flex, int max_iter,
+                               bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st,
+                               bool use_scalars = true);
+mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, cudaStream_t st);
 mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
                              cudaStream_t st);
 mofem_status launch_dot_partials(const void* A, const void* B, bool fp64, long long bs, long long n, int batch,
@@ -40,7 +43,7 @@ mofem_status launch_imex_rhs(const double* Un, const double* Fn, double* Fbar, i
 
 namespace {
 
-constexpr int W32_U = 0, W32_R = 1, W32_Z = 2, W32_QA = 3, W32_QB = 4, W32_LQ = 5, W32_N = 6;
+constexpr int W32_U = 0, W32_R = 1, W32_Z = 2, W32_QA = 3, W32_QB = 4, W32_LQ = 5, W32_ULO = 6, W32_N = 7;
 constexpr int W64_U = 0, W64_R = 1, W64_Z = 2, W64_QA = 3, W64_QB = 4, W64_LQ = 5, W64_T1 = 6, W64_T2 = 7, W64_N = 8;
 
 size_t per(const mofem_ctx* c) { return (size_t)c->q * c->ld; }
@@ -114,6 +117,8 @@ static mofem_status ensure_w32(mofem_ctx* c, cudaStream_t st) {
     size_t bytes = per(c) * c->batch * W32_N * sizeof(float);
     MOFEM_CUDA_TRY(cudaMalloc(&c->w32, bytes));
     MOFEM_CUDA_TRY(cudaMemsetAsync(c->w32, 0, bytes, st));
+    MOFEM_CUDA_TRY(cudaMalloc(&c->U64m, per(c) * c->batch * sizeof(double)));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(c->U64m, 0, per(c) * c->batch * sizeof(double), st));
     return MOFEM_OK;
 }
 
@@ -254,14 +259,14 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     const bool fp64 = prec == MOFEM_FP64;
     const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
     const long long bs = (long long)per(c);
-    void *U, *R, *Z, *Qn, *Qp, *LQ;
+    void *U, *Ulo = nullptr, *R, *Z, *Qn, *Qp, *LQ;
     const CUtensorMap *mZ, *mQp;
     if (fp64) {
         U = w64(c, W64_U); R = w64(c, W64_R); Z = w64(c, W64_Z);
         Qn = w64(c, s % 2 ? W64_QB : W64_QA); Qp = w64(c, s % 2 ? W64_QA : W64_QB); LQ = w64(c, W64_LQ);
         mZ = &e.mZ64; mQp = s % 2 ? &e.mQA64 : &e.mQB64;
     } else {
-        U = w32(c, W32_U); R = w32(c, W32_R); Z = w32(c, W32_Z);
+        U = w32(c, W32_U); Ulo = w32(c, W32_ULO); R = w32(c, W32_R); Z = w32(c, W32_Z);
         Qn = w32(c, s % 2 ? W32_QB : W32_QA); Qp = w32(c, s % 2 ? W32_QA : W32_QB); LQ = w32(c, W32_LQ);
         mZ = &e.mZ32; mQp = s % 2 ? &e.mQA32 : &e.mQB32;
     }
@@ -277,7 +282,7 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     a.status = c->d_status;
     MOFEM_TRY(launch_apply_pcg(c->K, c->NT, fp64, *mZ, *mQp, a, c->batch, st));
     // 2) U += alpha Q ; R -= alpha LQ ; convergence (last CTA) ; graph condition
-    MOFEM_TRY(launch_pcg_update(c, fp64, U, R, Qn, LQ, Z, fp64 ? nullptr : c->tc[which].Rop,
+    MOFEM_TRY(launch_pcg_update(c, fp64, U, Ulo, R, Qn, LQ, Z, fp64 ? nullptr : c->tc[which].Rop,
                                 (!fp64 && which == 1) ? 1 : 0, fp64 ? 0 : 1, max_iter, fixed, cond, st, true));
     // 3) Z = P^{-1}(R) ; rz and beta (last CTA)
     if (fp64) {
@@ -460,8 +465,22 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
     std::vector<double> bb, rr;
     MOFEM_TRY(launch_dot_partials(c->Bm64, c->Bm64, true, bs, bs, B, e.bb_part, c->part.n_rz, st));
     MOFEM_TRY(sum_partials(e.bb_part, c->part.n_rz, B, bb, st));
-    MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
-    MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
+    // initial residual; a zero initial guess needs no FP64 apply (R0 = B)
+    std::vector<double> uu;
+    MOFEM_TRY(launch_dot_partials(U, U, true, u_bs, (long long)q * q, B, e.bb_part + (size_t)B * c->part.n_rz / 2,
+                                  c->part.n_rz / 2 > 0 ? c->part.n_rz / 2 : 1, st));
+    MOFEM_TRY(sum_partials(e.bb_part + (size_t)B * c->part.n_rz / 2, c->part.n_rz / 2 > 0 ? c->part.n_rz / 2 : 1, B,
+                           uu, st));
+    bool zero_guess = true;
+    for (int i = 0; i < B; ++i) zero_guess = zero_guess && uu[i] == 0.0;
+    if (zero_guess) {
+        MOFEM_CUDA_TRY(cudaMemcpyAsync(c->R64, c->Bm64, sizeof(double) * bs * B, cudaMemcpyDeviceToDevice, st));
+        rr = bb;
+    } else {
+        MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
+        MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
+    }
+    const bool trace = getenv("MOFEM_TRACE") != nullptr;
     std::vector<double> ref2(B);
     for (int i = 0; i < B; ++i) ref2[i] = ref_is_r0 ? rr[i] : bb[i];
     int total_it = 0, outer = 0;
@@ -508,6 +527,7 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
             MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
             rel = rel_max(rr);
+            if (trace) fprintf(stderr, "[mofem] fp64 pass %d: iterations %d, rel residual %.3e\n", outer, it, rel);
             if (fixed) break;
         }
     } else {
@@ -516,6 +536,8 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
         MOFEM_TRY(tc_prepare(c, which, st));
         const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 20;
         const double eta0 = c->opts.inner_rtol > 0 ? c->opts.inner_rtol : 1e-4;
+        // the FP64 iterate lives in U64m (internal layout) during the solve
+        MOFEM_TRY(launch_convert(U, 1, u_bs, u_ld, c->U64m, 1, bs, ld, q, q, B, st));
         while (!(rel <= rtol) && outer < max_outer && std::isfinite(rel)) {
             // inner tolerance: no further than needed for this step
             double eta = std::max(eta0, 0.3 * rtol / rel);
@@ -526,20 +548,27 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
                 double ri = ref2[i] > 0 ? std::sqrt(rr[i] / ref2[i]) : 0.0;
                 if (ri <= rtol) MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_R) + bs * i, 0, sizeof(float) * bs, st));
             }
+            // inner FP32 MO-PCG on the correction (double-float accumulator, zero at
+            // start), folded into the FP64 iterate U64m at the end
             MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_U), 0, sizeof(float) * bs * B, st));
+            MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_ULO), 0, sizeof(float) * bs * B, st));
             MOFEM_TRY(run_inner(c, prec, max_iter, fixed, nullptr, eta, st));
-            MOFEM_TRY(launch_axpy_into64(U, u_bs, u_ld, w32(c, W32_U), bs, ld, q, B, st));
+            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, st));
             MOFEM_TRY(read_scalars(c, sc, st));
             int it = 0;
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
             ++outer;
-            launches += inner_launches(it, false) + 3;   // + convert R, axpy, residual
-            MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
+            launches += inner_launches(it, false) + 3;   // + convert R, fold, residual
+            MOFEM_TRY(op_residual64(c, c->U64m, bs, ld, c->R64, e.res_part, st));
             MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
             rel = rel_max(rr);
+            if (trace)
+                fprintf(stderr, "[mofem] outer %d: inner iterations %d (eta %.2e), rel residual %.3e\n", outer, it, eta,
+                        rel);
             if (fixed) break;
         }
+        MOFEM_TRY(launch_convert(c->U64m, 1, bs, ld, U, 1, u_bs, u_ld, q, q, B, st));
     }
     MOFEM_CUDA_TRY(cudaEventRecord(c->ev1, st));
     MOFEM_CUDA_TRY(cudaEventSynchronize(c->ev1));
@@ -616,7 +645,8 @@ mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int re
     if (kernel == 5) {
         MOFEM_TRY(tc_prepare(c, 1, st));
         for (int r = 0; r < reps; ++r)
-            MOFEM_TRY(launch_pcg_update(c, false, w32(c, W32_U), w32(c, W32_R), w32(c, W32_QA), w32(c, W32_LQ),
+            MOFEM_TRY(launch_pcg_update(c, false, w32(c, W32_U), w32(c, W32_ULO), w32(c, W32_R), w32(c, W32_QA),
+                                        w32(c, W32_LQ),
                                         w32(c, W32_Z), c->tc[1].Rop, 1, 1, 1 << 30, true, nullptr, st, false));
         return MOFEM_OK;
     }
