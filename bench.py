@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mofem", choices=["mofem", "reference"])
     ap.add_argument("--batch", type=int, default=4)
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp64"])
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "tf32", "fp64"])
     ap.add_argument("--n", type=int, default=2049)
     ap.add_argument("--k", type=int, default=2)
     ap.add_argument("--rtol", type=float, default=1e-10)
@@ -278,14 +278,14 @@ def run_mofem(a):
         torch.cuda.synchronize()
         return s0.elapsed_time(s1) / reps / 1e3
 
-    prec_k = a.precision if a.precision != "fp64" else "bf16"
+    prec_k = a.precision if a.precision != "fp64" else "fp16"
     t_gemm = [time_kernel(i, prec_k) for i in (1, 2, 3, 4)]
     t_apply = time_kernel(0, prec_k)
     t_upd = time_kernel(5, prec_k)
     flops_gemm = 2.0 * B * q ** 3
     gemm_tflops = [flops_gemm / t / 1e12 for t in t_gemm]
     tg = statistics.mean(t_gemm)
-    peak_t = peaks["bf16_tflops"] if prec_k == "bf16" else peaks["bf16_tflops"] / 2.0
+    peak_t = peaks["bf16_tflops"] if prec_k in ("bf16", "fp16") else peaks["bf16_tflops"] / 2.0
     apply_bytes = 4.0 * B * q * q * 4      # read Q_prev, Z; write Q_new, L(Q)   (FP32)
     upd_bytes = 38.0 * B * q * q          # read dU hi/lo, R, Q, LQ, Z_old; write dU hi/lo, R (FP32), R (BF16)
 
@@ -319,8 +319,8 @@ def run_mofem(a):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16": "bf16-gemm/f32-vec/f64-refine", "tf32": "tf32-gemm/f32-vec/f64-refine",
-                  "fp64": "f64"}[a.precision],
+        "dtype": {"fp16": "f16-gemm/f32-vec/f64-refine", "bf16": "bf16-gemm/f32-vec/f64-refine",
+                  "tf32": "tf32-gemm/f32-vec/f64-refine", "fp64": "f64"}[a.precision],
         "data": "synthetic",
         "config": {"workload": f"P{k} elliptic -Lap u + u = f, {n}x{n} nodes (q={q}), Dirichlet, domain "
                                f"0<=y<=1+0.25sin(2pi x), 32-mode Fourier f, rtol {a.rtol:g}",
@@ -331,10 +331,11 @@ def run_mofem(a):
         "rel_residual_max": max(rels), "setup_s": setup_s,
         "gpu_launches": launches,
         "clocks": clk,
-        "roofline": {"bound": "tensor", "kernel": "k_gemm<bf16> (preconditioner GEMM, mean of G1..G4)",
+        "roofline": {"bound": "tensor", "kernel": f"k_gemm_p<{prec_k}> (preconditioner GEMM, mean of G1..G4)",
                      "achieved": flops_gemm / tg / 1e12, "peak": peak_t, "unit": "TFLOP/s",
                      "frac": flops_gemm / tg / 1e12 / peak_t, "traffic": None,
-                     "peak_source": f"{peak_src} bf16_tflops (burst)" + (" / 2 for TF32" if prec_k == "tf32" else ""),
+                     "peak_source": f"{peak_src} bf16_tflops (burst; dense FP16 = BF16 rate)"
+                                    + (" / 2 for TF32" if prec_k == "tf32" else ""),
                      "per_gemm_us": [round(t * 1e6, 2) for t in t_gemm],
                      "per_gemm_tflops": [round(x, 1) for x in gemm_tflops]},
         "roofline_apply": {"bound": "hbm", "kernel": "k_apply<float,K=2,NT=5,QUPDATE>",

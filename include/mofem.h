@@ -57,10 +57,12 @@ typedef enum { MOFEM_BC_DIRICHLET = 0, MOFEM_BC_NEUMANN = 1 } mofem_bc;
 
 /* Arithmetic of the iteration.  FP64: every step in double (preconditioner
  * GEMMs through cuBLAS DGEMM).  MIXED_*: operator apply and vectors in FP32,
- * preconditioner GEMMs on tcgen05 tensor cores in TF32 or BF16 with FP32
- * accumulation, CG scalars and dot products accumulated in FP64, and FP64
- * true-residual iterative refinement around the inner FP32 solve. */
-typedef enum { MOFEM_FP64 = 0, MOFEM_MIXED_TF32 = 1, MOFEM_MIXED_BF16 = 2 } mofem_precision;
+ * preconditioner GEMMs on tcgen05 tensor cores with FP32 accumulation and
+ * operands in TF32, BF16 or FP16 (FP16: the residual operand is scaled per
+ * instance to unit RMS and the scale undone on output), CG scalars and
+ * cross-thread dot-product sums in FP64, and FP64 true-residual iterative
+ * refinement around the inner FP32 solve. */
+typedef enum { MOFEM_FP64 = 0, MOFEM_MIXED_TF32 = 1, MOFEM_MIXED_BF16 = 2, MOFEM_MIXED_FP16 = 3 } mofem_precision;
 
 /* Second pencil of the two-term Sylvester preconditioner (see mofem_precond). */
 typedef enum { MOFEM_PENCIL_AVERAGED = 0, MOFEM_PENCIL_DOMINANT = 1 } mofem_pencil;
@@ -137,8 +139,9 @@ mofem_status mofem_rhs(mofem_handle h, const double* F, double* B, int ld_b, cud
 /* Preconditioner Z = P^{-1}(R): the solution of E1 Z F1^T + E2 Z F2^T = R by the
  * reduced approach (Sec. 4, Eq. reduced_formula_for_u):
  *   Z = Q1 ((Q1^T R Q2) ./ (lambda_a + mu_b)) Q2^T.
- * FP64 -> double arrays, four DGEMMs.  MIXED_TF32 / MIXED_BF16 -> float arrays,
- * four tcgen05 GEMMs with operands rounded to TF32 / BF16 and FP32 accumulation. */
+ * FP64 -> double arrays, four DGEMMs.  MIXED_TF32 / MIXED_BF16 / MIXED_FP16 ->
+ * float arrays, four tcgen05 GEMMs with operands rounded to TF32 / BF16 / FP16
+ * and FP32 accumulation. */
 mofem_status mofem_precond(mofem_handle h, const void* R, void* Z, int ld, mofem_precision prec,
                            cudaStream_t stream);
 

@@ -19,11 +19,20 @@
 #include "internal.h"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <type_traits>
 
 namespace {
 
 constexpr int UPD_THREADS = 256;
+
+// RMS of the residual operand in the FP16 preconditioner GEMMs.  The largest
+// spectral coefficient of a smooth residual, (Q1^T R Q2)_00, is about q^2 RMS(R)
+// (eigenvector entries are O(1) under the mass normalisation); with RMS 2e-3
+// the stored intermediates X1^T (~2e-3 q), W^T = T2/(lam+mu) (~1e-4 q^2) and
+// Y (~1.5e-4 q^2) stay far below the FP16 maximum 65504 for q up to ~8000,
+// while R itself stays in the normal FP16 range down to 3% of its RMS.
+constexpr double FP16_RMS = 2e-3;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -64,6 +73,7 @@ struct UpdArgs {
     unsigned* counter;   // [batch] per-instance CTA tickets
     unsigned* gcounter;  // tickets of the whole launch (graph conditional)
     int use_sc, flex, max_iter, fixed;
+    double count;        // q * q (unit-RMS scale of the FP16 operand copy)
     cudaGraphConditionalHandle cond;
     int has_cond;
 };
@@ -77,6 +87,15 @@ __device__ __forceinline__ void axpy_v(float4& u, const float4& q, float a) {
 }
 __device__ __forceinline__ void axpy_v(double2& u, const double2& q, double a) {
     u.x = fma(a, q.x, u.x); u.y = fma(a, q.y, u.y);
+}
+
+__device__ __forceinline__ uint2 pack_f16x4(const float4& r, float sc) {
+    __half2 lo = __floats2half2_rn(r.x * sc, r.y * sc);
+    __half2 hi = __floats2half2_rn(r.z * sc, r.w * sc);
+    uint2 pk;
+    pk.x = *reinterpret_cast<unsigned*>(&lo);
+    pk.y = *reinterpret_cast<unsigned*>(&hi);
+    return pk;
 }
 
 __device__ __forceinline__ uint2 pack_bf16x4(const float4& r) {
@@ -140,14 +159,16 @@ __device__ __forceinline__ float dot32(const float4& a, const float4& b) {
 }
 __device__ __forceinline__ double dot32(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
 
-// ROP: 0 = no operand copy, 1 = BF16 copy of R for the tensor-core GEMM.
+// ROP: 0 = no operand copy, 1 = BF16 copy of R for the tensor-core GEMM,
+// 2 = FP16 copy of R scaled to unit RMS with the previous ||R|| (the scale is
+// recorded in the scalar state and undone by the last GEMM).
 // alpha is read from the scalar state (set by the apply kernel's last CTA).
 // Dot products: working precision within a thread (a few dozen terms), FP64
 // across threads and CTAs (fixed order).
 template <typename T, bool MIXED, int ROP>
 __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
     using V = typename Vec<T>::type;
-    static_assert(ROP == 0 || Vec<T>::W == 4, "BF16 operand copy is produced by the FP32 update only");
+    static_assert(ROP == 0 || Vec<T>::W == 4, "operand copies are produced by the FP32 update only");
     __shared__ double sh[UPD_THREADS / 32];
     __shared__ int last_s, glast_s;
     const int inst = blockIdx.y;
@@ -155,6 +176,13 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
     const bool active = !g.use_sc || sc->active;
     if (active) {
         const T alpha = g.use_sc ? (T)sc->alpha : (T)0.5;
+        double rs = 1.0;   // FP16 operand scale from the residual norm before this update
+        if constexpr (ROP == 2) {
+            const double rr_prev = g.use_sc ? sc->rr : g.count;
+            rs = rr_prev > 0.0 ? FP16_RMS * sqrt(g.count / rr_prev) : 1.0;
+            if (!(rs < 1e30)) rs = 1.0;
+        }
+        const float rsf = (float)rs;
         UVec<T, MIXED> U;
         if constexpr (MIXED) {
             U.ph = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.U) + (size_t)inst * g.bs);
@@ -167,7 +195,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
         const V* LQ = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.LQ) + (size_t)inst * g.bs);
         const V* Zo = reinterpret_cast<const V*>(reinterpret_cast<const T*>(g.Zold) + (size_t)inst * g.bs);
         uint2* Rb = nullptr;
-        if constexpr (ROP == 1)
+        if constexpr (ROP != 0)
             Rb = reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(g.Rop) + (size_t)inst * g.bs);
         T rrt = (T)0, rzt = (T)0;
         const long long stride = (long long)gridDim.x * blockDim.x;
@@ -181,6 +209,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
             rrt += dot32(r, r);
             if (g.flex) rzt += dot32(r, zo);
             if constexpr (ROP == 1) Rb[i] = pack_bf16x4(r);
+            if constexpr (ROP == 2) Rb[i] = pack_f16x4(r, rsf);
         };
         for (; i0 + (UNR - 1) * stride < g.nvec; i0 += UNR * stride) {
             UV u[UNR];
@@ -220,6 +249,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
                     sc->iters = it;
                     sc->rr = rrs;
                     sc->rzo = rzs;
+                    if (ROP == 2) sc->rscale = rs;
                     int act = 1;
                     if (!isfinite(rrs)) {
                         sc->status |= DEV_ERR_NONFINITE;
@@ -260,6 +290,7 @@ struct InitArgs {
     const double* ref2;           // [batch] or nullptr
     int batch;
     double rtol;
+    double count;                 // q * q
 };
 
 __global__ void k_init(InitArgs g) {
@@ -277,6 +308,7 @@ __global__ void k_init(InitArgs g) {
             s->beta = 0.0;
             s->rz = 1.0;
             s->rzo = 0.0;
+            s->rscale = (rr > 0.0 && isfinite(rr)) ? FP16_RMS * sqrt(g.count / rr) : 1.0;
             s->status = isfinite(rr) ? 0 : DEV_ERR_NONFINITE;
             s->active = (rr > s->tol2 && isfinite(rr)) ? 1 : 0;
         }
@@ -349,7 +381,26 @@ __global__ void k_convert(const S* src, long long s_bs, int s_ld, D* dst, long l
     dst += (size_t)inst * d_bs + (size_t)r * d_ld;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
         if constexpr (std::is_same<D, __nv_bfloat16>::value) dst[c] = __float2bfloat16_rn((float)src[c]);
+        else if constexpr (std::is_same<D, __half>::value) dst[c] = __float2half_rn((float)src[c]);
         else dst[c] = (D)src[c];
+    }
+}
+
+__global__ void k_convert_scaled_f16(const float* src, long long s_bs, int s_ld, __half* dst, long long d_bs, int d_ld,
+                                     int cols, const PcgScalars* sc) {
+    const int inst = blockIdx.z, r = blockIdx.y;
+    const float s = (float)sc[inst].rscale;
+    src += (size_t)inst * s_bs + (size_t)r * s_ld;
+    dst += (size_t)inst * d_bs + (size_t)r * d_ld;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
+        dst[c] = __float2half_rn(src[c] * s);
+}
+
+__global__ void k_set_rscale(PcgScalars* sc, const double* part, int nper, int batch, double count) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int inst = warp; inst < batch; inst += nw) {
+        const double ss = warp_sum_partials(part + (size_t)inst * nper, nper);
+        if (lane == 0) sc[inst].rscale = (ss > 0.0 && isfinite(ss)) ? FP16_RMS * sqrt(count / ss) : 1.0;
     }
 }
 
@@ -421,8 +472,10 @@ mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo
     g.has_cond = (cond && use_scalars) ? 1 : 0;
     g.cond = cond ? *cond : 0;
     dim3 grid(c->part.n_upd, c->batch);
+    g.count = (double)c->q * c->q;
     if (fp64) k_update<double, false, 0><<<grid, UPD_THREADS, 0, st>>>(g);
     else if (rop_kind == 1) k_update<float, true, 1><<<grid, UPD_THREADS, 0, st>>>(g);
+    else if (rop_kind == 2) k_update<float, true, 2><<<grid, UPD_THREADS, 0, st>>>(g);
     else k_update<float, true, 0><<<grid, UPD_THREADS, 0, st>>>(g);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
@@ -436,6 +489,7 @@ mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int 
     g.ref2 = ref2;
     g.batch = c->batch;
     g.rtol = rtol;
+    g.count = (double)c->q * c->q;
     k_init<<<1, 256, 0, st>>>(g);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
@@ -473,6 +527,8 @@ mofem_status launch_convert(const void* src, int sk, long long s_bs, int s_ld, v
     else if (sk == 1 && dk == 0) CONV(double, float);
     else if (sk == 1 && dk == 1) CONV(double, double);
     else if (sk == 1 && dk == 2) CONV(double, __nv_bfloat16);
+    else if (sk == 0 && dk == 3) CONV(float, __half);
+    else if (sk == 1 && dk == 3) CONV(double, __half);
     else return MOFEM_ERR_UNSUPPORTED;
 #undef CONV
     MOFEM_CUDA_TRY(cudaGetLastError());
@@ -515,6 +571,21 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
 mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, cudaStream_t st) {
     dim3 grid(592, batch);
     k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_convert_scaled_f16(const float* src, long long s_bs, int s_ld, void* dst, long long d_bs, int d_ld,
+                                       int rows, int cols, int batch, const PcgScalars* sc, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || batch <= 0) return MOFEM_OK;
+    dim3 grid((cols + 255) / 256, rows, batch);
+    k_convert_scaled_f16<<<grid, 256, 0, st>>>(src, s_bs, s_ld, (__half*)dst, d_bs, d_ld, cols, sc);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_set_rscale(PcgScalars* sc, const double* part, int nper, int batch, double count, cudaStream_t st) {
+    k_set_rscale<<<1, 256, 0, st>>>(sc, part, nper, batch, count);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

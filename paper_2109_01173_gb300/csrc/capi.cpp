@@ -16,7 +16,7 @@ mofem_opts default_opts(const mofem_opts* o) {
 }
 
 bool valid_precision(mofem_precision p) {
-    return p == MOFEM_FP64 || p == MOFEM_MIXED_TF32 || p == MOFEM_MIXED_BF16;
+    return p == MOFEM_FP64 || p == MOFEM_MIXED_TF32 || p == MOFEM_MIXED_BF16 || p == MOFEM_MIXED_FP16;
 }
 
 }  // namespace
@@ -105,8 +105,7 @@ mofem_status mofem_precond(mofem_handle h, const void* R, void* Z, int ld, mofem
     if (!h || !R || !Z || ld < h->q || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
     const long long bs = (long long)ld * h->q;
     if (prec == MOFEM_FP64) return precond64(h, (const double*)R, bs, ld, (double*)Z, bs, ld, stream);
-    return precond_tc(h, prec == MOFEM_MIXED_BF16 ? 1 : 0, (const float*)R, bs, ld, (float*)Z, bs, ld, nullptr,
-                      nullptr, stream);
+    return precond_tc(h, plan_of(prec), (const float*)R, bs, ld, (float*)Z, bs, ld, nullptr, nullptr, stream);
 }
 
 mofem_status mofem_pcg_solve(mofem_handle h, const double* F, double* U, double rtol, int max_iter,

@@ -25,6 +25,7 @@
 #include "internal.h"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdio>
 
 namespace {
@@ -39,7 +40,7 @@ constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 enum { EPI_STORE = 0, EPI_DIV = 1, EPI_Z = 2 };
 
 struct GemmArgs {
-    void* out; long long out_bs; int out_ld; int out_bf16;
+    void* out; long long out_bs; int out_ld; int out_bf16;   // out_bf16: 0 FP32, 1 BF16, 2 FP16 output
     int M, N, nk, batch;
     int a_shared, b_shared;
     int epi;
@@ -49,6 +50,7 @@ struct GemmArgs {
     PcgScalars* sc;       // skip inactive instances; with rz_part, last-CTA beta finalisation
     unsigned* counter;    // [batch] CTA tickets (zeroed, self-resetting)
     int flex;
+    const PcgScalars* scl; // FP16 operands: the G4 output is divided by scl[inst].rscale
     int* status;
 };
 
@@ -104,15 +106,21 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = fmt (1 BF16 under kind::f16, 2 TF32
-// under kind::tf32), both K-major, N = BN, M = BM.
+// Instruction descriptor: D = F32, A = B = fmt (0 F16 or 1 BF16 under kind::f16,
+// 2 TF32 under kind::tf32), both K-major, N = BN, M = BM.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
+// KIND: 0 TF32 (kind::tf32), 1 BF16 and 2 FP16 (kind::f16, A and B of the same type)
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    if constexpr (KIND == 1) {
+    if constexpr (KIND == 2) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(0)), "r"(acc)
+            : "memory");
+    } else if constexpr (KIND == 1) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
             ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(1)), "r"(acc)
@@ -193,8 +201,35 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, in
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], lam[j] + mu_m);
     }
+    if (g.epi == EPI_Z && g.scl) {
+        const float inv = (float)(1.0 / g.scl[inst].rscale);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] *= inv;
+    }
     const bool full = vec_ok && nb + 32 <= g.N;
-    if (g.out_bf16) {
+    if (g.out_bf16 == 2) {
+        // FP16 intermediates: saturate instead of overflowing to inf
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = fminf(fmaxf(v[j], -65504.f), 65504.f);
+        __half* o = reinterpret_cast<__half*>(g.out) + obase + nb;
+        if (full) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                uint4 pk;
+                __half2 p0 = __floats2half2_rn(v[j], v[j + 1]);
+                __half2 p1 = __floats2half2_rn(v[j + 2], v[j + 3]);
+                __half2 p2 = __floats2half2_rn(v[j + 4], v[j + 5]);
+                __half2 p3 = __floats2half2_rn(v[j + 6], v[j + 7]);
+                pk.x = *reinterpret_cast<uint32_t*>(&p0);
+                pk.y = *reinterpret_cast<uint32_t*>(&p1);
+                pk.z = *reinterpret_cast<uint32_t*>(&p2);
+                pk.w = *reinterpret_cast<uint32_t*>(&p3);
+                *reinterpret_cast<uint4*>(o + j) = pk;
+            }
+        } else {
+            for (int j = 0; j < 32 && nb + j < g.N; ++j) o[j] = __float2half_rn(v[j]);
+        }
+    } else if (g.out_bf16) {
         __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(g.out) + obase + nb;
         if (full) {
 #pragma unroll
@@ -250,7 +285,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     const int ntn = (g.N + BN - 1) / BN, ntm = (g.M + BM - 1) / BM;
     const int per_inst = ntn * ntm;
     const int total = per_inst * g.batch;
-    constexpr int BK = 128 / (KIND == 1 ? 2 : 4);
+    constexpr int BK = 128 / (KIND == 0 ? 4 : 2);
     auto bar_addr = [&](uint64_t* b) { return smem_u32(b); };
     auto active = [&](int inst) { return !g.sc || g.sc[inst].active; };
 
@@ -421,7 +456,7 @@ EncodeTiledFn encode_fn() {
 // 3D tensor map over [batch][rows][cols] (cols contiguous, leading dimension ld),
 // box = 128 bytes of K x box_rows rows x 1 instance, 128-byte swizzle.
 mofem_status make_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
-                      int box_rows) {
+                      int box_rows, bool fp16 = false) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) {
         mofem_set_last_error("cuTensorMapEncodeTiled entry point unavailable", __FILE__, __LINE__);
@@ -431,8 +466,9 @@ mofem_status make_map(CUtensorMap* m, const void* base, int esize, int cols, int
     cuuint64_t strides[2] = {(cuuint64_t)ld * esize, (cuuint64_t)rows * ld * esize};
     cuuint32_t box[3] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(m, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                     const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    CUresult r = enc(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         char buf[96];
@@ -505,6 +541,13 @@ mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const Gem
 mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
                                    int n, int batch, cudaStream_t st);
 
+mofem_status launch_gemm_kind(int which, const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch,
+                              cudaStream_t st) {
+    if (which == 1) return launch_gemm<1>(mA, mB, g, batch, st);
+    if (which == 2) return launch_gemm<2>(mA, mB, g, batch, st);
+    return launch_gemm<0>(mA, mB, g, batch, st);
+}
+
 int tc_rz_ctas(const mofem_ctx* c) { return ((c->q + BN - 1) / BN) * ((c->q + BM - 1) / BM); }
 
 // Allocate the operand copies of Q1, Q1^T, Q2, Q2^T in the precision `which`
@@ -513,8 +556,9 @@ mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
     TcPlan& p = c->tc[which];
     if (p.ready) return MOFEM_OK;
     const int q = c->q, ld = c->ld, B = c->batch;
-    const int es = which == 1 ? 2 : 4;
-    const int kind = which == 1 ? 2 : 0;   // launch_convert kinds: 0 float, 2 bf16
+    const int es = which == 0 ? 4 : 2;
+    const int kind = conv_kind_of_plan(which);   // launch_convert kinds: 0 float, 2 bf16, 3 f16
+    const bool f16 = which == 2;
     p.esize = es;
     const size_t per = (size_t)q * ld;
     MOFEM_CUDA_TRY(cudaMalloc(&p.Q1, per * B * es));
@@ -543,14 +587,14 @@ mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
     MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(tmp);
     // A maps (box rows BM) and B maps (box rows BN) of the four GEMMs
-    MOFEM_TRY(make_map(&p.mA[0], p.Q2T, es, q, q, 1, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[0], p.Rop, es, q, q, B, ld, BN));
-    MOFEM_TRY(make_map(&p.mA[1], p.X1T, es, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[1], p.Q1T, es, q, q, B, ld, BN));
-    MOFEM_TRY(make_map(&p.mA[2], p.Q1, es, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[2], p.WT, es, q, q, B, ld, BN));
-    MOFEM_TRY(make_map(&p.mA[3], p.Y, es, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&p.mB[3], p.Q2, es, q, q, 1, ld, BN));
+    MOFEM_TRY(make_map(&p.mA[0], p.Q2T, es, q, q, 1, ld, BM, f16));
+    MOFEM_TRY(make_map(&p.mB[0], p.Rop, es, q, q, B, ld, BN, f16));
+    MOFEM_TRY(make_map(&p.mA[1], p.X1T, es, q, q, B, ld, BM, f16));
+    MOFEM_TRY(make_map(&p.mB[1], p.Q1T, es, q, q, B, ld, BN, f16));
+    MOFEM_TRY(make_map(&p.mA[2], p.Q1, es, q, q, B, ld, BM, f16));
+    MOFEM_TRY(make_map(&p.mB[2], p.WT, es, q, q, B, ld, BN, f16));
+    MOFEM_TRY(make_map(&p.mA[3], p.Y, es, q, q, B, ld, BM, f16));
+    MOFEM_TRY(make_map(&p.mB[3], p.Q2, es, q, q, 1, ld, BN, f16));
     p.ready = true;
     return MOFEM_OK;
 }
@@ -559,19 +603,18 @@ mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
 mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaStream_t st) {
     const TcPlan& p = c->tc[which];
     const int q = c->q, ld = c->ld;
-    const int bk = which == 1 ? 64 : 32;
+    const int bk = which == 0 ? 32 : 64;
     GemmArgs g{};
     g.M = q; g.N = q; g.nk = (q + bk - 1) / bk;
     g.status = c->d_status;
     g.lam = c->lam32; g.lam_bs = ld; g.mu = c->mu32;
-    g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = which == 1;
+    g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = which;
     void* outs[4] = {p.X1T, p.WT, p.Y, Z};
     const int epis[4] = {EPI_STORE, EPI_DIV, EPI_STORE, EPI_Z};
     g.out = outs[idx]; g.epi = epis[idx];
     g.a_shared = idx == 0; g.b_shared = idx == 3;
     if (idx == 3) g.out_bf16 = 0;
-    return which == 1 ? launch_gemm<1>(p.mA[idx], p.mB[idx], g, c->batch, st)
-                      : launch_gemm<0>(p.mA[idx], p.mB[idx], g, c->batch, st);
+    return launch_gemm_kind(which, p.mA[idx], p.mB[idx], g, c->batch, st);
 }
 
 // Z = P^{-1}(R) with R already in p.Rop (rounded operand).  R32 (FP32, same
@@ -580,7 +623,7 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
                         long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st) {
     const TcPlan& p = c->tc[which];
     const int q = c->q, ld = c->ld;
-    const int bk = which == 1 ? 64 : 32;
+    const int bk = which == 0 ? 32 : 64;
     GemmArgs g{};
     g.M = q;
     g.N = q;
@@ -592,11 +635,9 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
     g.mu = c->mu32;
     g.out_bs = (long long)q * ld;
     g.out_ld = ld;
-    g.out_bf16 = which == 1;
-    auto run = [&](int i) -> mofem_status {
-        return which == 1 ? launch_gemm<1>(p.mA[i], p.mB[i], g, c->batch, st)
-                          : launch_gemm<0>(p.mA[i], p.mB[i], g, c->batch, st);
-    };
+    g.out_bf16 = which;
+    g.scl = which == 2 ? c->d_sc : nullptr;
+    auto run = [&](int i) -> mofem_status { return launch_gemm_kind(which, p.mA[i], p.mB[i], g, c->batch, st); };
     // G1: X1T = (R Q2)^T
     g.out = p.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
     MOFEM_TRY(run(0));

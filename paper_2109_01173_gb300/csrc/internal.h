@@ -28,6 +28,7 @@ struct PcgScalars {
     double rr0;         // ||R_0||^2 of this (inner) solve
     double rr;          // ||R||^2 after the last update
     double tol2;        // stop when rr <= tol2
+    double rscale;      // scale applied to the FP16 operand copy of R (undone on the GEMM output)
     int iters;          // iterations done in this (inner) solve
     int active;         // 1 while not converged
     int status;         // DEV_ERR_* bits
@@ -74,7 +75,7 @@ struct mofem_ctx {
     double* lam64 = nullptr;   // [batch][ld] (padded with 1)
     double* mu64 = nullptr;    // [ld]
     float* lam32 = nullptr; float* mu32 = nullptr;
-    TcPlan tc[2];              // [0] TF32, [1] BF16
+    TcPlan tc[3];              // [0] TF32, [1] BF16, [2] FP16
 
     // FP64-form workspaces (lazily allocated)
     double* w64 = nullptr;     // 8 matrices [batch][q][ld]
@@ -94,10 +95,10 @@ struct mofem_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
     // captured graphs of one PCG iteration, keyed by precision
-    cudaGraphExec_t it_graph[3] = {nullptr, nullptr, nullptr};
-    cudaGraphExec_t loop_graph[3] = {nullptr, nullptr, nullptr};
-    int it_graph_max_iter[3] = {0, 0, 0};
-    bool host_stepped[3] = {false, false, false};   // conditional graph unavailable for this precision
+    cudaGraphExec_t it_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t loop_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    int it_graph_max_iter[4] = {0, 0, 0, 0};
+    bool host_stepped[4] = {false, false, false, false};   // conditional graph unavailable for this precision
 };
 
 // ---- error helpers -------------------------------------------------------
@@ -163,7 +164,15 @@ mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols,
 // ---- BLAS-1 / control kernels (blas1.cu) ----------------------------------
 mofem_status launch_convert(const void* src, int src_kind, long long s_bs, int s_ld,
                             void* dst, int dst_kind, long long d_bs, int d_ld,
-                            int rows, int cols, int batch, cudaStream_t st);   // kinds: 0 f32, 1 f64, 2 bf16
+                            int rows, int cols, int batch, cudaStream_t st);   // kinds: 0 f32, 1 f64, 2 bf16, 3 f16
+// dst (FP16) = src (FP32) * sc[inst].rscale
+mofem_status launch_convert_scaled_f16(const float* src, long long s_bs, int s_ld, void* dst, long long d_bs, int d_ld,
+                                       int rows, int cols, int batch, const PcgScalars* sc, cudaStream_t st);
+// sc[inst].rscale = sqrt(q*q / sum(partials[inst])) (unit-RMS scale of R)
+mofem_status launch_set_rscale(PcgScalars* sc, const double* part, int nper, int batch, double count, cudaStream_t st);
+// operand kind of a tensor-core plan: 0 TF32 (f32 storage), 1 BF16, 2 FP16
+inline int plan_of(mofem_precision p) { return p == MOFEM_MIXED_BF16 ? 1 : (p == MOFEM_MIXED_FP16 ? 2 : 0); }
+inline int conv_kind_of_plan(int which) { return which == 1 ? 2 : (which == 2 ? 3 : 0); }
 mofem_status launch_transpose64(const double* src, long long s_bs, double* dst, long long d_bs,
                                 int n, int ld, int batch, cudaStream_t st);
 mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs,

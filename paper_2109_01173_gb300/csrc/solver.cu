@@ -247,8 +247,19 @@ mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs,
                         int z_ld, double* rz_partial, PcgScalars* sc, cudaStream_t st) {
     MOFEM_TRY(tc_prepare(c, which, st));
     TcPlan& p = c->tc[which];
-    MOFEM_TRY(launch_convert(R, 0, r_bs, r_ld, p.Rop, which == 1 ? 2 : 0, (long long)per(c), c->ld, c->q, c->q,
-                             c->batch, st));
+    const long long bs = (long long)per(c);
+    if (which == 2) {
+        // FP16 operands: R scaled to unit RMS per instance (scale in the scalar state)
+        MOFEM_TRY(ensure_w32(c, st));
+        float* Rt = w32(c, W32_LQ);   // scratch FP32 copy with zero padding
+        MOFEM_TRY(launch_convert(R, 0, r_bs, r_ld, Rt, 0, bs, c->ld, c->q, c->q, c->batch, st));
+        MOFEM_TRY(launch_dot_partials(Rt, Rt, false, bs, bs, c->batch, c->part.rr, c->part.n_upd, st));
+        MOFEM_TRY(launch_set_rscale(c->d_sc, c->part.rr, c->part.n_upd, c->batch, (double)c->q * c->q, st));
+        MOFEM_TRY(launch_convert_scaled_f16(Rt, bs, c->ld, p.Rop, bs, c->ld, c->q, c->q, c->batch, c->d_sc, st));
+    } else {
+        MOFEM_TRY(launch_convert(R, 0, r_bs, r_ld, p.Rop, conv_kind_of_plan(which), bs, c->ld, c->q, c->q, c->batch,
+                                 st));
+    }
     return tc_precond(c, which, R, r_bs, r_ld, Z, z_ld, z_bs, rz_partial, sc, st);
 }
 
@@ -257,7 +268,7 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
                                   const cudaGraphConditionalHandle* cond, cudaStream_t st) {
     Extra& e = extras()[c];
     const bool fp64 = prec == MOFEM_FP64;
-    const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
+    const int which = plan_of(prec);
     const long long bs = (long long)per(c);
     void *U, *Ulo = nullptr, *R, *Z, *Qn, *Qp, *LQ;
     const CUtensorMap *mZ, *mQp;
@@ -283,7 +294,8 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     MOFEM_TRY(launch_apply_pcg(c->K, c->NT, fp64, *mZ, *mQp, a, c->batch, st));
     // 2) U += alpha Q ; R -= alpha LQ ; convergence (last CTA) ; graph condition
     MOFEM_TRY(launch_pcg_update(c, fp64, U, Ulo, R, Qn, LQ, Z, fp64 ? nullptr : c->tc[which].Rop,
-                                (!fp64 && which == 1) ? 1 : 0, fp64 ? 0 : 1, max_iter, fixed, cond, st, true));
+                                fp64 ? 0 : (which == 1 ? 1 : (which == 2 ? 2 : 0)), fp64 ? 0 : 1, max_iter, fixed,
+                                cond, st, true));
     // 3) Z = P^{-1}(R) ; rz and beta (last CTA)
     if (fp64) {
         MOFEM_TRY(precond64(c, (const double*)R, bs, c->ld, (double*)Z, bs, c->ld, st));
@@ -388,7 +400,7 @@ static mofem_status run_inner(mofem_ctx* c, mofem_precision prec, int max_iter, 
                               double rtol, cudaStream_t st) {
     Extra& e = extras()[c];
     const bool fp64 = prec == MOFEM_FP64;
-    const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
+    const int which = plan_of(prec);
     const long long bs = (long long)per(c);
     void* R = fp64 ? (void*)w64(c, W64_R) : (void*)w32(c, W32_R);
     void* Z = fp64 ? (void*)w64(c, W64_Z) : (void*)w32(c, W32_Z);
@@ -406,8 +418,12 @@ static mofem_status run_inner(mofem_ctx* c, mofem_precision prec, int max_iter, 
                                       c->d_ctr + 2 * c->batch, 0));
     } else {
         MOFEM_TRY(tc_prepare(c, which, st));
-        MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[which].Rop, which == 1 ? 2 : 0, bs, c->ld, c->q, c->q,
-                                 c->batch, st));
+        if (which == 2)   // scale from ||R0|| set by the init kernel
+            MOFEM_TRY(launch_convert_scaled_f16((const float*)R, bs, c->ld, c->tc[2].Rop, bs, c->ld, c->q, c->q,
+                                                c->batch, c->d_sc, st));
+        else
+            MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[which].Rop, conv_kind_of_plan(which), bs, c->ld, c->q,
+                                     c->q, c->batch, st));
         MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st));
     }
     const int pi = (int)prec;
@@ -532,8 +548,8 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
         }
     } else {
         MOFEM_TRY(ensure_w32(c, st));
-        const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
-        MOFEM_TRY(tc_prepare(c, which, st));
+        mofem_precision pe = prec;   // effective inner precision (FP16 may fall back to TF32)
+        MOFEM_TRY(tc_prepare(c, plan_of(pe), st));
         const int max_outer = c->opts.max_outer > 0 ? c->opts.max_outer : 20;
         const double eta0 = c->opts.inner_rtol > 0 ? c->opts.inner_rtol : 1e-4;
         // the FP64 iterate lives in U64m (internal layout) during the solve
@@ -552,9 +568,18 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             // start), folded into the FP64 iterate U64m at the end
             MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_U), 0, sizeof(float) * bs * B, st));
             MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_ULO), 0, sizeof(float) * bs * B, st));
-            MOFEM_TRY(run_inner(c, prec, max_iter, fixed, nullptr, eta, st));
-            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, st));
+            MOFEM_TRY(run_inner(c, pe, max_iter, fixed, nullptr, eta, st));
             MOFEM_TRY(read_scalars(c, sc, st));
+            bool bad = false;
+            for (auto& s : sc) bad = bad || (s.status & DEV_ERR_NONFINITE) || !std::isfinite(s.rr);
+            if (bad && pe == MOFEM_MIXED_FP16) {
+                // FP16 operand range exceeded: redo this step with TF32 operands
+                if (trace) fprintf(stderr, "[mofem] FP16 inner solve non-finite; repeating the step in TF32\n");
+                pe = MOFEM_MIXED_TF32;
+                MOFEM_TRY(tc_prepare(c, plan_of(pe), st));
+                continue;
+            }
+            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, st));
             int it = 0;
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
@@ -617,7 +642,7 @@ mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, 
 mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int reps, cudaStream_t st) {
     MOFEM_TRY(ensure_common(c, st));
     const long long bs = (long long)per(c);
-    const int which = prec == MOFEM_MIXED_BF16 ? 1 : 0;
+    const int which = plan_of(prec);
     if (kernel == 6) {
         for (int r = 0; r < reps; ++r)
             MOFEM_TRY(op_residual64(c, c->Bm64, bs, c->ld, c->R64, extras()[c].res_part, st));

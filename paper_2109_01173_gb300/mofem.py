@@ -16,11 +16,11 @@ LIB_PATH = os.path.join(HERE, "libmofem.so")
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_EIG, ERR_NONFINITE, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT, \
     ERR_OOM, ERR_UNSUPPORTED = range(10)
 DIRICHLET, NEUMANN = 0, 1
-FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
+FP64, MIXED_TF32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
 PENCIL_AVERAGED, PENCIL_DOMINANT = 0, 1
 FLAG_HOST_LOOP, FLAG_FIXED_ITERS = 1, 2
 
-PRECISIONS = {"fp64": FP64, "tf32": MIXED_TF32, "bf16": MIXED_BF16}
+PRECISIONS = {"fp64": FP64, "tf32": MIXED_TF32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
 
 _GFN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
 

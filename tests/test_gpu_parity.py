@@ -11,8 +11,9 @@ Tolerances (written per test) follow from the arithmetic:
 * FP32 apply: forward error of the two-stage sums in difference form
   (row sum x_r + sum A_rj (x_j - x_r)), elementwise
   |err| <= 2 (P + NT P + 2) u32 (|S| |X| |T|^T)  with u32 = 2^-24.
-* tensor-core preconditioner vs FP64: operands rounded to BF16 (u = 2^-9) or
-  truncated to TF32 (2^-10) in four chained GEMMs: Frobenius 2.5e-2 / 1.5e-2.
+* tensor-core preconditioner vs FP64: operands rounded to BF16 (u = 2^-9),
+  truncated to TF32 (2^-10) or rounded to FP16 (2^-11, residual operand scaled
+  to unit RMS) in four chained GEMMs: Frobenius 2.5e-2 / 1.5e-2 / 1.5e-2.
 * solves: relative error <= 1e-8 against the oracle's 1e-13-residual solution
   and FP64 true residual <= rtol = 1e-10.
 """
@@ -119,7 +120,7 @@ def test_precond_parity(mf, k, n, dname, bc):
     assert np.linalg.norm(Z - Zo) <= 1e-9 * np.linalg.norm(Zo)
     back = E1 @ Z @ F1.T + E2 @ Z @ F2.T
     assert np.linalg.norm(back - R) <= 1e-9 * np.linalg.norm(R)
-    for prec, tol in (("bf16", 2.5e-2), ("tf32", 1.5e-2)):
+    for prec, tol in (("bf16", 2.5e-2), ("tf32", 1.5e-2), ("fp16", 1.5e-2)):
         Zf = torch.zeros((h.q, h.q), dtype=torch.float32, device="cuda")
         h.precond(torch.tensor(R, dtype=torch.float32, device="cuda"), Zf, prec)
         Zm = Zf.cpu().numpy().astype(np.float64)
@@ -132,7 +133,7 @@ SOLVE_CASES = [(2, 129, "one", 0, 1.0), (1, 97, "two", 1, 2.0), (4, 81, "two", 0
 
 
 @pytest.mark.parametrize("k,n,dname,bc,gamma", SOLVE_CASES)
-@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16", "tf32", "fp16"])
 def test_solve_parity(mf, k, n, dname, bc, gamma, prec):
     torch = torch_()
     g1, g2 = dom(dname)
