@@ -31,6 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MO-PCG solves/s and ms/iter, P2 N=2049 (mixed vs FP64 GPU form, rel.err<=1e-8)"
+# DRAM bytes per preconditioner-GEMM launch at P2 2049 x 4 (ncu capture of the current kernel;
+# set to None whenever k_gemm_p changes until it is captured again)
+GEMM_DRAM_BYTES = 81.5e6
 UNIT = "solves/s"
 
 
@@ -47,6 +50,9 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="step the inner loop from the host instead of a conditional-node CUDA graph "
+                         "(per-kernel profilers cannot see kernels inside conditional graphs)")
     ap.add_argument("--ref-iters", type=int, default=3, help="oracle MO-PCG iterations per reference sample")
     return ap.parse_args()
 
@@ -191,7 +197,8 @@ def run_mofem(a):
     B, n, k = a.batch, a.n, a.k
     insts = make_inputs(B, n, k, rank)
     t0 = time.perf_counter()
-    h = mf.Handle([i["g1"] for i in insts], [i["g2"] for i in insts], k, n, [i["gamma"] for i in insts])
+    opts = mf.make_opts(flags=mf.FLAG_HOST_LOOP) if a.host_loop else None
+    h = mf.Handle([i["g1"] for i in insts], [i["g2"] for i in insts], k, n, [i["gamma"] for i in insts], opts=opts)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     q = h.q
@@ -222,6 +229,7 @@ def run_mofem(a):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters, launches, rels = [], 0, []
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler restrict itself to the timed region
     ev0.record(stream)
     for _ in range(a.steps):
         info = step(U, F)
@@ -229,6 +237,7 @@ def run_mofem(a):
         launches += info.kernel_launches
         rels.append(info.rel_residual)
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
@@ -326,22 +335,25 @@ def run_mofem(a):
                                f"0<=y<=1+0.25sin(2pi x), 32-mode Fourier f, rtol {a.rtol:g}",
                    "global_batch": B * world, "batch_per_gpu": B, "precision": a.precision,
                    "l2": f"inputs larger than L2 (working set ~{working_set_mb:.0f} MB per GPU)",
-                   "parallelism": f"instances sharded over {world} GPU(s), no collective"},
+                   "parallelism": f"instances sharded over {world} GPU(s), no collective",
+                   "inner_loop": "host-stepped graphs" if a.host_loop else "conditional-node CUDA graph"},
         "ms_per_iter": ms_iter, "iterations_per_solve": statistics.mean(iters),
         "rel_residual_max": max(rels), "setup_s": setup_s,
         "gpu_launches": launches,
         "clocks": clk,
         "roofline": {"bound": "tensor", "kernel": f"k_gemm_p<{prec_k}> (preconditioner GEMM, mean of G1..G4)",
                      "achieved": flops_gemm / tg / 1e12, "peak": peak_t, "unit": "TFLOP/s",
-                     "frac": flops_gemm / tg / 1e12 / peak_t, "traffic": None,
+                     "frac": flops_gemm / tg / 1e12 / peak_t, "traffic": GEMM_DRAM_BYTES,
+                     "traffic_note": "bytes per launch, dram__bytes_read.sum + dram__bytes_write.sum, mean of "
+                                     "G1..G4 from profiles/k_gemm_p_k_apply_pcg2_p2_2049_b4.md",
                      "peak_source": f"{peak_src} bf16_tflops (burst; dense FP16 = BF16 rate)"
                                     + (" / 2 for TF32" if prec_k == "tf32" else ""),
                      "per_gemm_us": [round(t * 1e6, 2) for t in t_gemm],
                      "per_gemm_tflops": [round(x, 1) for x in gemm_tflops]},
-        "roofline_apply": {"bound": "hbm", "kernel": "k_apply<float,K=2,NT=5,QUPDATE>",
+        "roofline_apply": {"bound": "hbm", "kernel": f"k_apply_pcg2<K={k},NT=5> (packed FP32, PCG form)",
                            "achieved": apply_bytes / t_apply / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                            "frac": apply_bytes / t_apply / 1e9 / peaks["hbm_gbs"], "us": t_apply * 1e6},
-        "roofline_update": {"bound": "hbm", "kernel": "k_update<float,bf16>",
+        "roofline_update": {"bound": "hbm", "kernel": f"k_update<float,double-float U,{a.precision} operand copy>",
                             "achieved": upd_bytes / t_upd / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                             "frac": upd_bytes / t_upd / 1e9 / peaks["hbm_gbs"], "us": t_upd * 1e6},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * n * n * 8,

@@ -79,7 +79,8 @@ typedef struct {
     int quad_points;       /* Gauss-Legendre points per element for P_k; 0 -> k + 3 */
     mofem_pencil pencil;   /* default MOFEM_PENCIL_AVERAGED */
     int max_outer;         /* refinement steps of the mixed form; 0 -> 20 */
-    double inner_rtol;     /* residual reduction asked of each inner FP32 solve; 0 -> 1e-4 */
+    double inner_rtol;     /* reduction asked of the first inner FP32 solve; later ones aim at
+                              rtol, no deeper than inner_rtol / 10.  0 -> 1e-5 */
     int flags;             /* MOFEM_FLAG_* */
 } mofem_opts;
 
@@ -145,6 +146,21 @@ mofem_status mofem_rhs(mofem_handle h, const double* F, double* B, int ld_b, cud
 mofem_status mofem_precond(mofem_handle h, const void* R, void* Z, int ld, mofem_precision prec,
                            cudaStream_t stream);
 
+/* One search-direction step of MO-PCG (Sec. 5, the PCG iteration of Eq.
+ * laplace_xnormal_pcg_iteration), by the fused kernel the solver launches every
+ * iteration: for each instance i
+ *   Q = Z + beta[i] Q_prev,  LQ = L(Q),  alpha[i] = rz[i] / <Q, L(Q)>_F.
+ * Z, Q_prev, Q, LQ: device arrays of q x q per instance, leading dimension ld,
+ * batch stride ld*q; FP64 -> double arrays, MIXED_* -> float arrays (FP32
+ * arithmetic, the inner-solve operator).  Base pointers 16-byte aligned and
+ * ld*element size a multiple of 16 bytes; columns q..ld-1 of Q and LQ receive
+ * zeros.  Q must not overlap Z or Q_prev.  beta, rz, alpha: host arrays of
+ * `batch` doubles.  Synchronises `stream` (alpha is copied back).  Returns
+ * MOFEM_ERR_BREAKDOWN (alpha[i] = 0) if <Q, L(Q)> <= 0 for some instance. */
+mofem_status mofem_pcg_direction(mofem_handle h, const void* Z, const void* Q_prev, const double* beta,
+                                 const double* rz, void* Q, void* LQ, int ld, double* alpha,
+                                 mofem_precision prec, cudaStream_t stream);
+
 /* Solve L(U) = B with B = mofem_rhs(F) for every instance by MO-PCG (Sec. 5,
  * Eqs. laplace_xnormal_pcg, laplace_xnormal_pcg_iteration with the standard PCG
  * recurrences) until ||B - L(U)||_F <= rtol ||B||_F, checked on the FP64 true
@@ -171,7 +187,7 @@ mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const doubl
  * times on the handle's internal buffers, asynchronously on `stream`, so that
  * a caller can time it with events on that stream.  kernel:
  *   0 = FP32 operator apply with the fused search-direction update (PCG form),
- *   1..4 = preconditioner GEMM G1..G4 (prec MIXED_TF32 or MIXED_BF16),
+ *   1..4 = preconditioner GEMM G1..G4 (prec MIXED_TF32, MIXED_BF16 or MIXED_FP16),
  *   5 = FP32 PCG update (alpha, U, R, BF16 copy of R, partial sums),
  *   6 = FP64 operator apply (true residual form).
  * The buffers' contents are whatever the last solve left (timing only). */

@@ -1,5 +1,5 @@
 // FP32 instantiations of the banded operator apply (mixed-precision inner solve).
-#include "apply_impl.cuh"
+#include "apply_pcg_f2.cuh"
 
 using namespace mofem_apply_impl;
 
@@ -44,27 +44,54 @@ int apply_rows_per_cta(int K) {
     }
 }
 
+template <int K, int NT>
+static mofem_status pcg_f32(const CUtensorMap& mZ, const CUtensorMap& mQ, const CUtensorMap* mS,
+                           const ApplyPcgArgs& a, int batch, cudaStream_t st) {
+    if constexpr (packed_apply_ok(K, NT)) {
+        if (!mS) return MOFEM_ERR_INVALID_ARG;
+        return launch_pcg2_t<K, NT>(mZ, mQ, *mS, a, batch, st);
+    } else {
+        return launch_pcg_t<float, K, NT, false>(mZ, mQ, a, batch, st);
+    }
+}
+
 template <int K>
-static mofem_status pcg_nt_f32(int nt, const CUtensorMap& mZ, const CUtensorMap& mQ, const ApplyPcgArgs& a, int batch,
-                               cudaStream_t st) {
-    if (nt == 5) return launch_pcg_t<float, K, 5, false>(mZ, mQ, a, batch, st);
-    if (nt == 8) return launch_pcg_t<float, K, 8, false>(mZ, mQ, a, batch, st);
+static mofem_status pcg_nt_f32(int nt, const CUtensorMap& mZ, const CUtensorMap& mQ, const CUtensorMap* mS,
+                               const ApplyPcgArgs& a, int batch, cudaStream_t st) {
+    if (nt == 5) return pcg_f32<K, 5>(mZ, mQ, mS, a, batch, st);
+    if (nt == 8) return pcg_f32<K, 8>(mZ, mQ, mS, a, batch, st);
     return MOFEM_ERR_UNSUPPORTED;
 }
 
 mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, const CUtensorMap& mQ,
-                              const ApplyPcgArgs& a, int batch, cudaStream_t st) {
+                              const CUtensorMap* mS, const ApplyPcgArgs& a, int batch, cudaStream_t st) {
     if (fp64) return launch_apply_pcg_f64(K, nt, mZ, mQ, a, batch, st);
     switch (K) {
-        case 1: return pcg_nt_f32<1>(nt, mZ, mQ, a, batch, st);
-        case 2: return pcg_nt_f32<2>(nt, mZ, mQ, a, batch, st);
-        case 3: return pcg_nt_f32<3>(nt, mZ, mQ, a, batch, st);
-        case 4: return pcg_nt_f32<4>(nt, mZ, mQ, a, batch, st);
+        case 1: return pcg_nt_f32<1>(nt, mZ, mQ, mS, a, batch, st);
+        case 2: return pcg_nt_f32<2>(nt, mZ, mQ, mS, a, batch, st);
+        case 3: return pcg_nt_f32<3>(nt, mZ, mQ, mS, a, batch, st);
+        case 4: return pcg_nt_f32<4>(nt, mZ, mQ, mS, a, batch, st);
         default: return MOFEM_ERR_UNSUPPORTED;
     }
 }
 
-int apply_pcg_rows_per_cta(int K) {
+bool apply_pcg_packed(int K, int nt, bool fp64) { return !fp64 && packed_apply_ok(K, nt); }
+
+template <int K>
+static int geo2_rows(int nt, bool box) {
+    if (nt == 5) return box ? Geo2<K, 5>::CH : Geo2<K, 5>::TA;
+    return box ? Geo2<K, 8>::CH : Geo2<K, 8>::TA;
+}
+
+int apply_pcg_rows_per_cta(int K, int nt, bool fp64) {
+    if (apply_pcg_packed(K, nt, fp64)) {
+        switch (K) {
+            case 1: return geo2_rows<1>(nt, false);
+            case 2: return geo2_rows<2>(nt, false);
+            case 3: return geo2_rows<3>(nt, false);
+            default: return geo2_rows<4>(nt, false);
+        }
+    }
     switch (K) {
         case 1: return Geo<1>::TA_T;
         case 2: return Geo<2>::TA_T;
@@ -72,3 +99,11 @@ int apply_pcg_rows_per_cta(int K) {
         default: return Geo<4>::TA_T;
     }
 }
+
+int apply_pcg_box_rows(int K, int nt, bool fp64) {
+    if (apply_pcg_packed(K, nt, fp64)) return 4;
+    return apply_pcg_rows_per_cta(K, nt, fp64) + 2 * K;
+}
+
+// 2 * SR2 of Geo2: the duplicated S row, an even number of float2 (16-byte rows)
+int apply_s2_row_floats(int K, int nt) { return 2 * (((nt * (2 * K + 1) + 1) / 2) * 2); }

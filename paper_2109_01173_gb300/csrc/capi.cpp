@@ -11,7 +11,7 @@ mofem_opts default_opts(const mofem_opts* o) {
     mofem_opts d{};
     if (o) d = *o;
     if (d.max_outer <= 0) d.max_outer = 20;
-    if (!(d.inner_rtol > 0.0)) d.inner_rtol = 1e-4;
+    if (!(d.inner_rtol > 0.0)) d.inner_rtol = 1e-5;
     return d;
 }
 
@@ -106,6 +106,21 @@ mofem_status mofem_precond(mofem_handle h, const void* R, void* Z, int ld, mofem
     const long long bs = (long long)ld * h->q;
     if (prec == MOFEM_FP64) return precond64(h, (const double*)R, bs, ld, (double*)Z, bs, ld, stream);
     return precond_tc(h, plan_of(prec), (const float*)R, bs, ld, (float*)Z, bs, ld, nullptr, nullptr, stream);
+}
+
+mofem_status mofem_pcg_direction(mofem_handle h, const void* Z, const void* Q_prev, const double* beta,
+                                 const double* rz, void* Q, void* LQ, int ld, double* alpha, mofem_precision prec,
+                                 cudaStream_t stream) {
+    if (!h || !Z || !Q_prev || !beta || !rz || !Q || !LQ || !alpha || ld < h->q || !valid_precision(prec))
+        return MOFEM_ERR_INVALID_ARG;
+    const int esz = prec == MOFEM_FP64 ? 8 : 4;
+    auto misaligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
+    if (((long long)ld * esz) % 16 != 0 || misaligned(Z) || misaligned(Q_prev) || misaligned(Q) || misaligned(LQ)) {
+        mofem_set_last_error("mofem_pcg_direction: buffers must be 16-byte aligned with ld*size a multiple of 16",
+                             __FILE__, __LINE__);
+        return MOFEM_ERR_INVALID_ARG;
+    }
+    return pcg_direction(h, Z, Q_prev, beta, rz, Q, LQ, ld, alpha, prec == MOFEM_FP64, stream);
 }
 
 mofem_status mofem_pcg_solve(mofem_handle h, const double* F, double* U, double rtol, int max_iter,

@@ -13,15 +13,19 @@
 //   G3: D[a][j] = sum_i Q1[a][i] WT[j][i]     -> Y[a][j]     (Y = Q1 W)
 //   G4: D[a][b] = sum_j Y[a][j] Q2[b][j]      -> Z[a][b]     (Z = Y Q2^T), + <R, Z> partials
 //
-// Kernel (k_gemm_p): 128 x 256 output tiles (M = 128 TMEM lanes, N = 256 FP32
-// TMEM columns), a persistent grid of one CTA per SM walking all tiles of all
-// instances.  TMA loads 128-byte-wide K slices (SWIZZLE_128B) into a 4-stage
-// shared-memory ring; one thread issues tcgen05.mma (kind::f16 with BF16
-// operands, or kind::tf32) and releases stages with tcgen05.commit; two TMEM
-// accumulators let the epilogue (tcgen05.ld 32x32b.x32) of one tile overlap the
-// mainloop of the next.  Every mbarrier wait is bounded (2 s of %globaltimer);
-// on expiry the CTA records DEV_ERR_TIMEOUT, stops all roles, frees its TMEM and
-// exits.  No cluster multicast is used.
+// Kernel (k_gemm_p): 128 x 256 output tiles per CTA (M = 128 TMEM lanes, N = 256
+// FP32 TMEM columns), a persistent grid of CTA pairs (2-CTA clusters, one CTA
+// per SM) walking all 256 x 256 pair tiles of all instances.  The two CTAs of a
+// pair compute vertically adjacent tiles with the same B operand: each loads
+// its own A slice and one half of the B slice, multicast into both CTAs' shared
+// memory, so the L2-to-SM traffic per MMA is 2/3 of a lone CTA's.  TMA loads
+// 128-byte-wide K slices (SWIZZLE_128B) into a 4-stage ring; one thread issues
+// tcgen05.mma (kind::f16 with BF16/FP16 operands, or kind::tf32) and releases a
+// stage in both CTAs with a multicast tcgen05.commit; two TMEM accumulators let
+// the epilogue (tcgen05.ld 32x32b.x32) of one tile overlap the mainloop of the
+// next.  Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the CTA
+// records DEV_ERR_TIMEOUT, stops all roles, frees its TMEM and exits (the peer
+// then times out as well).
 #include "internal.h"
 
 #include <cuda_bf16.h>
@@ -131,6 +135,38 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
             ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(2)), "r"(acc)
             : "memory");
     }
+}
+
+// TMA load written to the same shared-memory offset of every CTA in `mask`
+// (cluster multicast); each destination CTA's mbarrier at offset `mbar` receives
+// the transaction bytes.
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
+                                               int c2, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+        : "memory");
+}
+
+// Arrive (once) on the mbarrier at offset `mbar` of every CTA in `mask` when all
+// prior tcgen05.mma of this thread have completed.
+__device__ __forceinline__ void mma_commit_mc(uint32_t mbar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+        ::"r"(mbar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -274,16 +310,23 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, in
     }
 }
 
-template <int KIND>
+// CM CTAs per cluster (1 or 2) share the B slice of each K step; the B tensor
+// map's box is BN / 2 = 128 rows, loaded twice by a lone CTA.
+template <int KIND, int CM>
 __global__ void __launch_bounds__(P_THREADS, 1)
     k_gemm_p(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
+    static_assert(CM == 1 || CM == 2, "pairs at most");
+    constexpr int BH = BN / 2;                  // rows of one B box
+    constexpr uint16_t MASK = (1u << CM) - 1u;  // all CTAs of the cluster
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     PBars* pb = reinterpret_cast<PBars*>(smem + STAGES * STAGE_BYTES);
     volatile int* abort_flag = &pb->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntn = (g.N + BN - 1) / BN, ntm = (g.M + BM - 1) / BM;
-    const int per_inst = ntn * ntm;
+    const int cr = CM > 1 ? (int)cluster_rank() : 0;          // position in the pair (M half)
+    const int cid = blockIdx.x / CM, ncl = gridDim.x / CM;    // pair index, pairs
+    const int ntn = (g.N + BN - 1) / BN, ntm = (g.M + BM * CM - 1) / (BM * CM);
+    const int per_inst = ntn * ntm;           // pair tiles per instance
     const int total = per_inst * g.batch;
     constexpr int BK = 128 / (KIND == 0 ? 4 : 2);
     auto bar_addr = [&](uint64_t* b) { return smem_u32(b); };
@@ -292,7 +335,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(bar_addr(&pb->full[s]), 1);
-            mbar_init(bar_addr(&pb->empty[s]), 1);
+            mbar_init(bar_addr(&pb->empty[s]), CM);   // released by the MMA of every CTA that reads it
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar_addr(&pb->tfull[b]), 1);
@@ -309,6 +352,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     __syncthreads();
+    if constexpr (CM > 1) cluster_sync_all();   // the peer's multicasts may target our barriers from here on
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = pb->tmem_slot;
 
@@ -317,26 +361,32 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB)) : "memory");
             int it = 0;
-            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+            for (int t = cid; t < total && !*abort_flag; t += ncl) {
                 const int inst = t / per_inst, r = t - inst * per_inst;
                 if (!active(inst)) continue;
-                const int m0 = (r / ntn) * BM, n0 = (r % ntn) * BN;
+                const int m0 = (r / ntn) * (BM * CM) + cr * BM, n0 = (r % ntn) * BN;
                 const int za = g.a_shared ? 0 : inst, zb = g.b_shared ? 0 : inst;
                 for (int kb = 0; kb < g.nk; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (it >= STAGES && !pwait(bar_addr(&pb->empty[s]), ph ^ 1u, abort_flag)) break;
                     const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                    mbar_expect_tx(bar_addr(&pb->full[s]), STAGE_BYTES);
-                    tma_load_3d(sa, &mA, bar_addr(&pb->full[s]), kb * BK, m0, za);
-                    tma_load_3d(sa + A_BYTES, &mB, bar_addr(&pb->full[s]), kb * BK, n0, zb);
+                    const uint32_t fb = bar_addr(&pb->full[s]);
+                    mbar_expect_tx(fb, STAGE_BYTES);   // own A + both B halves (one from the peer)
+                    tma_load_3d(sa, &mA, fb, kb * BK, m0, za);
+                    if constexpr (CM == 1) {
+                        tma_load_3d(sa + A_BYTES, &mB, fb, kb * BK, n0, zb);
+                        tma_load_3d(sa + A_BYTES + BH * 128, &mB, fb, kb * BK, n0 + BH, zb);
+                    } else {
+                        tma_load_3d_mc(sa + A_BYTES + cr * BH * 128, &mB, fb, kb * BK, n0 + cr * BH, zb, MASK);
+                    }
                 }
             }
         }
     } else if (warp == 5) {
         if (lane == 0) {   // ---- MMA issuer
             int it = 0, tl = 0;
-            for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+            for (int t = cid; t < total && !*abort_flag; t += ncl) {
                 const int inst = t / per_inst;
                 if (!active(inst)) continue;
                 const int b = tl & 1;
@@ -357,7 +407,8 @@ __global__ void __launch_bounds__(P_THREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         mma<KIND>(d, make_desc(sa + 32 * kk), make_desc(sa + A_BYTES + 32 * kk), (kb | kk) != 0);
-                    mma_commit(bar_addr(&pb->empty[s]));
+                    if constexpr (CM == 1) mma_commit(bar_addr(&pb->empty[s]));
+                    else mma_commit_mc(bar_addr(&pb->empty[s]), MASK);   // the stage is free in both CTAs
                 }
                 mma_commit(bar_addr(&pb->tfull[b]));
                 ++tl;
@@ -366,10 +417,12 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         }
     } else {   // ---- epilogue warps 0-3: thread = TMEM lane = output row within the tile
         int tl = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int cta_per_inst = per_inst * CM;   // <R, Z> partial slots (one per CTA tile)
+        for (int t = cid; t < total; t += ncl) {
             const int inst = t / per_inst, r = t - inst * per_inst;
             if (!active(inst)) continue;
-            const int m0 = (r / ntn) * BM, n0 = (r % ntn) * BN;
+            const int m0 = (r / ntn) * (BM * CM) + cr * BM, n0 = (r % ntn) * BN;
+            const int ct = ((r / ntn) * CM + cr) * ntn + (r % ntn);
             const int b = tl & 1;
             const uint32_t use = (uint32_t)(tl >> 1);
             const bool ok = pwait(bar_addr(&pb->tfull[b]), use & 1u, abort_flag);
@@ -400,18 +453,19 @@ __global__ void __launch_bounds__(P_THREADS, 1)
                     int last = 0;
                     if (lane == 0) {
                         const double* rd = pb->red[tl & 1];
-                        g.rz_part[(size_t)inst * per_inst + r] = rd[0] + rd[1] + rd[2] + rd[3];
+                        g.rz_part[(size_t)inst * cta_per_inst + ct] = rd[0] + rd[1] + rd[2] + rd[3];
                         if (g.sc && g.counter) {
                             __threadfence();
                             const unsigned tk = atomicAdd(g.counter + inst, 1u);
-                            last = (tk == (unsigned)per_inst - 1) ? 1 : 0;
+                            last = (tk == (unsigned)cta_per_inst - 1) ? 1 : 0;
                         }
                     }
                     last = __shfl_sync(0xffffffffu, last, 0);
                     if (last) {   // fixed-order sum of this instance's partials: rz and beta
                         __threadfence();
                         double rz = 0.0;
-                        for (int i = lane; i < per_inst; i += 32) rz += __ldcg(g.rz_part + (size_t)inst * per_inst + i);
+                        for (int i = lane; i < cta_per_inst; i += 32)
+                            rz += __ldcg(g.rz_part + (size_t)inst * cta_per_inst + i);
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) rz += __shfl_xor_sync(0xffffffffu, rz, o);
                         if (lane == 0) {
@@ -429,6 +483,8 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         }
     }
     __syncthreads();
+    // no CTA leaves while its peer may still multicast into it or arrive on its barriers
+    if constexpr (CM > 1) cluster_sync_all();
     if (threadIdx.x == 0 && pb->abort && g.status) atomicOr(g.status, DEV_ERR_TIMEOUT);
     if (warp == 5) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -519,20 +575,42 @@ int num_sms() {
     return n;
 }
 
+constexpr int GEMM_CM = 2;   // CTAs per cluster sharing B
+
 template <int KIND>
 mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g0, int batch, cudaStream_t st) {
-    static bool attr = false;
+    constexpr int CM = GEMM_CM;
+    auto kern = k_gemm_p<KIND, CM>;
+    static int max_pairs = 0;
     const int smem = STAGES * STAGE_BYTES + 1024 + (int)sizeof(PBars) + 64;
-    if (!attr) {
-        MOFEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_p<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CM;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(P_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (!max_pairs) {
+        MOFEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        cfg.gridDim = dim3(CM * (num_sms() / CM));
+        int n = 0;
+        MOFEM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, kern, &cfg));
+        if (n <= 0) {
+            mofem_set_last_error("no CTA pair of the tensor-core GEMM fits on this GPU", __FILE__, __LINE__);
+            return MOFEM_ERR_UNSUPPORTED;
+        }
+        max_pairs = n;
     }
     GemmArgs g = g0;
     g.batch = batch;
-    const int total = ((g.N + BN - 1) / BN) * ((g.M + BM - 1) / BM) * batch;
-    const int grid = total < num_sms() ? total : num_sms();
-    k_gemm_p<KIND><<<grid, P_THREADS, smem, st>>>(mA, mB, g);
-    MOFEM_CUDA_TRY(cudaGetLastError());
+    const int total = ((g.N + BN - 1) / BN) * ((g.M + BM * CM - 1) / (BM * CM)) * batch;   // pair tiles
+    const int pairs = total < max_pairs ? total : max_pairs;
+    cfg.gridDim = dim3(CM * pairs);
+    MOFEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, mA, mB, g));
     return MOFEM_OK;
 }
 
@@ -548,7 +626,10 @@ mofem_status launch_gemm_kind(int which, const CUtensorMap& mA, const CUtensorMa
     return launch_gemm<0>(mA, mB, g, batch, st);
 }
 
-int tc_rz_ctas(const mofem_ctx* c) { return ((c->q + BN - 1) / BN) * ((c->q + BM - 1) / BM); }
+// <R, Z> partial slots per instance: one per CTA tile of the paired grid
+int tc_rz_ctas(const mofem_ctx* c) {
+    return ((c->q + BN - 1) / BN) * ((c->q + BM * GEMM_CM - 1) / (BM * GEMM_CM)) * GEMM_CM;
+}
 
 // Allocate the operand copies of Q1, Q1^T, Q2, Q2^T in the precision `which`
 // (0 TF32 = FP32 storage, 1 BF16), the intermediates, and the tensor maps.
@@ -586,15 +667,15 @@ mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
     }
     MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(tmp);
-    // A maps (box rows BM) and B maps (box rows BN) of the four GEMMs
+    // A maps and B maps (box rows BM = BN / 2: B slices arrive in two halves) of the four GEMMs
     MOFEM_TRY(make_map(&p.mA[0], p.Q2T, es, q, q, 1, ld, BM, f16));
-    MOFEM_TRY(make_map(&p.mB[0], p.Rop, es, q, q, B, ld, BN, f16));
+    MOFEM_TRY(make_map(&p.mB[0], p.Rop, es, q, q, B, ld, BN / 2, f16));
     MOFEM_TRY(make_map(&p.mA[1], p.X1T, es, q, q, B, ld, BM, f16));
-    MOFEM_TRY(make_map(&p.mB[1], p.Q1T, es, q, q, B, ld, BN, f16));
+    MOFEM_TRY(make_map(&p.mB[1], p.Q1T, es, q, q, B, ld, BN / 2, f16));
     MOFEM_TRY(make_map(&p.mA[2], p.Q1, es, q, q, B, ld, BM, f16));
-    MOFEM_TRY(make_map(&p.mB[2], p.WT, es, q, q, B, ld, BN, f16));
+    MOFEM_TRY(make_map(&p.mB[2], p.WT, es, q, q, B, ld, BN / 2, f16));
     MOFEM_TRY(make_map(&p.mA[3], p.Y, es, q, q, B, ld, BM, f16));
-    MOFEM_TRY(make_map(&p.mB[3], p.Q2, es, q, q, 1, ld, BN, f16));
+    MOFEM_TRY(make_map(&p.mB[3], p.Q2, es, q, q, 1, ld, BN / 2, f16));
     p.ready = true;
     return MOFEM_OK;
 }
@@ -665,13 +746,13 @@ mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z
     const int q = c->q, ld = b.ld, B = c->batch;
     CUtensorMap mA[4], mB[4];
     MOFEM_TRY(make_map(&mA[0], b.Q2T, 2, q, q, 1, ld, BM));
-    MOFEM_TRY(make_map(&mB[0], b.Rop, 2, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&mB[0], b.Rop, 2, q, q, B, ld, BN / 2));
     MOFEM_TRY(make_map(&mA[1], b.X1T, 2, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&mB[1], b.Q1T, 2, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&mB[1], b.Q1T, 2, q, q, B, ld, BN / 2));
     MOFEM_TRY(make_map(&mA[2], b.Q1, 2, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&mB[2], b.WT, 2, q, q, B, ld, BN));
+    MOFEM_TRY(make_map(&mB[2], b.WT, 2, q, q, B, ld, BN / 2));
     MOFEM_TRY(make_map(&mA[3], b.Y, 2, q, q, B, ld, BM));
-    MOFEM_TRY(make_map(&mB[3], b.Q2, 2, q, q, 1, ld, BN));
+    MOFEM_TRY(make_map(&mB[3], b.Q2, 2, q, q, 1, ld, BN / 2));
     GemmArgs g{};
     g.M = q; g.N = q; g.nk = (q + 63) / 64;
     g.status = c->d_status;

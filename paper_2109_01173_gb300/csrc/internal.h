@@ -66,6 +66,8 @@ struct mofem_ctx {
 
     // banded tables, diagonal-major: tab[term][j][row] = S_term[row][row + j - K]
     double* S64 = nullptr;  float* S32 = nullptr;   // [batch][NT][P][q]
+    float* S2dup = nullptr;   // [batch][q][2*SR2] FP32 S rows, each coefficient twice (packed apply)
+    int s2_row = 0;           // floats per S2dup row
     double* T64 = nullptr;  float* T32 = nullptr;   // [NT][P][q]
     double* Sr64 = nullptr; double* Tr64 = nullptr; // RHS mass factors: [batch][P][q], [P][q] (offset off)
 
@@ -155,9 +157,17 @@ struct ApplyPcgArgs {
     PcgScalars* sc; int use_sc;
     int* status;
 };
+mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const double* beta, const double* rz,
+                           void* Q, void* LQ, int ld, double* alpha, bool fp64, cudaStream_t st);
 mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, const CUtensorMap& mQ,
+                              const CUtensorMap* mS,
                               const ApplyPcgArgs& a, int batch, cudaStream_t st);
-int apply_pcg_rows_per_cta(int K);
+// Geometry of the PCG-form apply launched for (K, nt, precision): output rows
+// per CTA, rows per staging box (TMA map), floats per duplicated S row.
+int apply_pcg_rows_per_cta(int K, int nt, bool fp64);
+int apply_pcg_box_rows(int K, int nt, bool fp64);
+bool apply_pcg_packed(int K, int nt, bool fp64);
+int apply_s2_row_floats(int K, int nt);
 mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
                           int box_cols, int box_rows);
 

@@ -61,6 +61,7 @@ def _load():
         "mofem_apply": [vp, vp, vp, c_int, c_int, vp],
         "mofem_rhs": [vp, vp, vp, c_int, vp],
         "mofem_precond": [vp, vp, vp, c_int, c_int, vp],
+        "mofem_pcg_direction": [vp, vp, vp, P(c_double), P(c_double), vp, vp, c_int, P(c_double), c_int, vp],
         "mofem_pcg_solve": [vp, vp, vp, c_double, c_int, c_int, P(SolveInfo), vp],
         "mofem_imex_step": [vp, c_double, c_double, vp, vp, vp, c_int, P(SolveInfo), vp],
         "mofem_destroy": [vp],
@@ -82,6 +83,7 @@ def _load():
 LIB = _load()
 
 EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply", "mofem_rhs", "mofem_precond",
+            "mofem_pcg_direction",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
             "mofem_host_tables", "mofem_bench_kernel"]
 
@@ -183,6 +185,18 @@ class Handle:
         _check("mofem_precond", LIB.mofem_precond(self.h, _ptr(R), _ptr(Z), ld or R.shape[-1],
                                                   PRECISIONS[precision], _stream()))
         return Z
+
+    def pcg_direction(self, Z, Qprev, beta, rz, Q, LQ, precision="fp64", ld=None, check=True):
+        """Q = Z + beta_i Qprev, LQ = L(Q) and alpha_i = rz_i / <Q, LQ> per instance
+        (one search-direction step of MO-PCG).  Returns (alpha list, status code)."""
+        n = len(beta)
+        arr = ctypes.c_double * n
+        b_, r_, a_ = arr(*[float(v) for v in beta]), arr(*[float(v) for v in rz]), arr()
+        code = LIB.mofem_pcg_direction(self.h, _ptr(Z), _ptr(Qprev), b_, r_, _ptr(Q), _ptr(LQ),
+                                       ld or Z.shape[-1], a_, PRECISIONS[precision], _stream())
+        if check:
+            _check("mofem_pcg_direction", code)
+        return list(a_), code
 
     def pcg_solve(self, F, U, rtol=1e-10, max_iter=500, precision="bf16", check=True):
         info = SolveInfo()

@@ -62,6 +62,7 @@ def test_invalid_arguments_rejected_without_gpu(mofem):
         mofem.host_tables(SIN_TOP, ZERO, 2, 9, 1.0)
     assert L.mofem_apply(None, None, None, 0, 0, None) == 1
     assert L.mofem_precond(None, None, None, 0, 0, None) == 1
+    assert L.mofem_pcg_direction(None, None, None, None, None, None, None, 0, None, 0, None) == 1
     assert L.mofem_pcg_solve(None, None, None, 1e-10, 10, 0, None, None) == 1
     assert L.mofem_imex_step(None, 1.0, 1.0, None, None, None, 0, None, None) == 1
     assert L.mofem_destroy(None) == 1

@@ -128,6 +128,91 @@ def test_precond_parity(mf, k, n, dname, bc):
     h.close()
 
 
+# ---- one search-direction step: Q = Z + beta Q_prev, LQ = L(Q), alpha = rz / <Q, LQ> ----------
+# FP32 cases run the packed-FP32 kernel (K = 1..3 with 5 terms, K = 1, 2 with 8 terms) or the
+# scalar one (larger bands); FP64 runs the FP64 kernel.  Several 128-column and 40-row tiles
+# with ragged tails, ld > q (padding must come back zero), two instances per handle.
+DIRECTION_CASES = [(2, 301, "one", 0), (2, 263, "two", 1), (1, 200, "two", 1), (0, 150, "one", 0),
+                   (3, 151, "one", 1), (4, 161, "two", 0), (2, 5, "one", 0), (1, 7, "two", 1)]
+
+
+def _direction_case(mf, k, n, dname, bc, prec, ld_extra):
+    torch = torch_()
+    g1, g2 = dom(dname)
+    gam = [0.7, 2.5]
+    h = mf.Handle([g1, g1], [g2, g2], k, n, gam, bc=bc)
+    q = h.q
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    npdt = np.float64 if prec == "fp64" else np.float32
+    ld = ((q + 3) // 4) * 4 + ld_extra
+    rng = np.random.default_rng(7 * n + k)
+    Z = rng.standard_normal((2, q, q)).astype(npdt)
+    Qp = rng.standard_normal((2, q, q)).astype(npdt)
+    beta, rz = [0.37, -1.25], [2.0, 0.5]
+
+    def dev(A):
+        t = torch.zeros((2, q, ld), dtype=dt, device="cuda")
+        t[:, :, :q] = torch.tensor(A, device="cuda")
+        return t
+    Zt, Qpt = dev(Z), dev(Qp)
+    Qt = torch.full((2, q, ld), 7.0, dtype=dt, device="cuda")
+    LQt = torch.full((2, q, ld), 7.0, dtype=dt, device="cuda")
+    alpha, code = h.pcg_direction(Zt, Qpt, beta, rz, Qt, LQt, precision=prec, ld=ld)
+    assert code == 0
+    Qg = Qt[:, :, :q].cpu().numpy().astype(np.float64)
+    LQg = LQt[:, :, :q].cpu().numpy().astype(np.float64)
+    u = 2.0 ** -53 if prec == "fp64" else U32
+    Pw = 2 * max(k, 1) + 1
+    for i in range(2):
+        P = Problem(g1, g2, k, n, gam[i], bc="dirichlet" if bc == 0 else "neumann")
+        b = float(npdt(beta[i]))
+        Qe = Z[i].astype(np.float64) + b * Qp[i].astype(np.float64)
+        # one rounding on the GPU (two in the FP64 reference): relative to the operands
+        mag = np.abs(Z[i].astype(np.float64)) + np.abs(b * Qp[i].astype(np.float64))
+        assert np.all(np.abs(Qg[i] - Qe) <= 2 * u * mag + 1e-300), i
+        Yo = apply_terms(live(P), Qg[i])
+        absb = apply_terms([(abs(S), abs(T)) for S, T in live(P)], np.abs(Qg[i]))
+        bound = 2 * (Pw + h.n_terms * Pw + 2) * u * absb
+        assert np.all(np.abs(LQg[i] - Yo) <= bound + 1e-300), i
+        qlq = float(np.sum(Qg[i] * LQg[i]))
+        tol = 64 * u * float(np.sum(np.abs(Qg[i] * LQg[i])))
+        assert abs(rz[i] / alpha[i] - qlq) <= tol, (i, rz[i] / alpha[i], qlq)
+    # padding columns: zero where the kernel's tiles reach, untouched beyond
+    for T in (Qt, LQt):
+        pad = T[:, :, q:].cpu().numpy()
+        reach = min(ld, ((q + 127) // 128) * 128) - q
+        assert np.all((pad[:, :, :reach] == 0) | (pad[:, :, :reach] == 7.0))
+        assert np.all(pad[:, :, reach:] == 7.0)
+    h.close()
+
+
+@pytest.mark.parametrize("k,n,dname,bc", DIRECTION_CASES)
+@pytest.mark.parametrize("prec", ["fp16", "fp64"])
+def test_pcg_direction_parity(mf, k, n, dname, bc, prec):
+    _direction_case(mf, k, n, dname, bc, prec, ld_extra=0)
+
+
+def test_pcg_direction_wide_ld(mf):
+    _direction_case(mf, 2, 301, "one", 0, "tf32", ld_extra=200)
+
+
+def test_pcg_direction_breakdown(mf):
+    """<Q, L(Q)> = 0 (zero direction): BREAKDOWN, alpha = 0, nothing non-finite."""
+    torch = torch_()
+    h = mf.Handle([ZERO, ZERO], [SIN_TOP, SIN_TOP], 2, 65, [1.0, 1.0])
+    q = h.q
+    ld = ((q + 3) // 4) * 4
+    Zt = torch.zeros((2, q, ld), dtype=torch.float32, device="cuda")
+    Zt[1, 3, 5] = 1.0
+    Qp = torch.zeros_like(Zt)
+    Qt, LQt = torch.zeros_like(Zt), torch.zeros_like(Zt)
+    alpha, code = h.pcg_direction(Zt, Qp, [0.0, 0.0], [1.0, 1.0], Qt, LQt, precision="bf16", ld=ld, check=False)
+    assert code == mf.ERR_BREAKDOWN
+    assert alpha[0] == 0.0 and alpha[1] > 0.0
+    assert torch.isfinite(LQt).all()
+    h.close()
+
+
 SOLVE_CASES = [(2, 129, "one", 0, 1.0), (1, 97, "two", 1, 2.0), (4, 81, "two", 0, 0.0), (0, 101, "one", 0, 1.0),
                (3, 64, "one", 1, 0.5)]
 
@@ -271,3 +356,46 @@ def test_full_size_solve(mf, full):
     info64, code64 = h.pcg_solve(F, U64, rtol=1e-10, max_iter=500, precision="fp64")
     assert code64 == 0
     assert float(((U64 - U).norm() / U64.norm()).item()) <= 1e-8
+
+
+def test_full_size_direction_batched(mf):
+    """The PCG-form apply in the launch configuration of bench.py (P2, 2049 x 2049 nodes,
+    four instances, FP32): new direction and L(Q) at sampled entries against the oracle's
+    entry-wise apply, alpha against the FP64 dot of the returned arrays."""
+    torch = torch_()
+    n, k, B = 2049, 2, 4
+    insts = [metric_instance(n=n, k=k, seed=s) for s in range(B)]
+    h = mf.Handle([I["g1"] for I in insts], [I["g2"] for I in insts], k, n, [1.0] * B)
+    q = h.q
+    ld = ((q + 63) // 64) * 64
+    g = torch.Generator(device="cuda").manual_seed(5)
+    Zt = torch.zeros((B, q, ld), dtype=torch.float32, device="cuda")
+    Qp = torch.zeros_like(Zt)
+    Zt[:, :, :q] = torch.randn((B, q, q), generator=g, device="cuda")
+    Qp[:, :, :q] = torch.randn((B, q, q), generator=g, device="cuda")
+    Qt, LQt = torch.empty_like(Zt), torch.empty_like(Zt)
+    beta, rz = [0.5, -0.25, 1.5, 0.0], [1.0, 2.0, 3.0, 4.0]
+    alpha, code = h.pcg_direction(Zt, Qp, beta, rz, Qt, LQt, precision="fp16", ld=ld)
+    assert code == 0
+    rng = np.random.default_rng(13)
+    pts = [(0, 0), (q - 1, q - 1), (0, q - 1), (q - 1, 0), (39, 127), (40, 128), (1919, 1920), (2046, 1023)]
+    pts += [tuple(p) for p in rng.integers(0, q, size=(24, 2))]
+    for i in range(B):
+        P = Problem(insts[i]["g1"], insts[i]["g2"], k, n, 1.0)
+        terms = live(P)
+        Qg = Qt[i, :, :q].double().cpu().numpy()
+        Zi = Zt[i, :, :q].double().cpu().numpy()
+        Qpi = Qp[i, :, :q].double().cpu().numpy()
+        b = float(np.float32(beta[i]))
+        Qe = Zi + b * Qpi
+        assert np.all(np.abs(Qg - Qe) <= 2 * U32 * (np.abs(Zi) + np.abs(b * Qpi)) + 1e-300)
+        LQg = LQt[i, :, :q].double().cpu().numpy()
+        absterms = [(abs(S), abs(T)) for S, T in terms]
+        for a_, b_ in pts:
+            ref = apply_entry(terms, Qg, a_, b_)
+            bnd = 2 * (5 + h.n_terms * 5 + 2) * U32 * apply_entry(absterms, np.abs(Qg), a_, b_)
+            assert abs(LQg[a_, b_] - ref) <= bnd + 1e-300, (i, a_, b_)
+        qlq = float(np.sum(Qg * LQg))
+        assert abs(rz[i] / alpha[i] - qlq) <= 64 * U32 * float(np.sum(np.abs(Qg * LQg))), i
+        assert torch.all(Qt[i, :, q:] == 0) and torch.all(LQt[i, :, q:] == 0)
+    h.close()
