@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MO-PCG solves/s and ms/iter, P2 N=2049 (mixed vs FP64 GPU form, rel.err<=1e-8)"
 # DRAM bytes per preconditioner-GEMM launch at P2 2049 x 4 (ncu capture of the current kernel;
-# set to None whenever k_gemm_p changes until it is captured again)
-GEMM_DRAM_BYTES = 81.5e6
+# set to None whenever k_gemm_2sm changes until it is captured again)
+GEMM_DRAM_BYTES = 81.1e6
 UNIT = "solves/s"
 
 
@@ -341,11 +341,11 @@ def run_mofem(a):
         "rel_residual_max": max(rels), "setup_s": setup_s,
         "gpu_launches": launches,
         "clocks": clk,
-        "roofline": {"bound": "tensor", "kernel": f"k_gemm_p<{prec_k}> (preconditioner GEMM, mean of G1..G4)",
+        "roofline": {"bound": "tensor", "kernel": f"k_gemm_2sm<{prec_k}> (tcgen05 cta_group::2 preconditioner GEMM, mean of G1..G4)",
                      "achieved": flops_gemm / tg / 1e12, "peak": peak_t, "unit": "TFLOP/s",
                      "frac": flops_gemm / tg / 1e12 / peak_t, "traffic": GEMM_DRAM_BYTES,
                      "traffic_note": "bytes per launch, dram__bytes_read.sum + dram__bytes_write.sum, mean of "
-                                     "G1..G4 from profiles/k_gemm_p_k_apply_pcg2_p2_2049_b4.md",
+                                     "G1..G4 from profiles/k_gemm_2sm_p2_2049_b4.md",
                      "peak_source": f"{peak_src} bf16_tflops (burst; dense FP16 = BF16 rate)"
                                     + (" / 2 for TF32" if prec_k == "tf32" else ""),
                      "per_gemm_us": [round(t * 1e6, 2) for t in t_gemm],

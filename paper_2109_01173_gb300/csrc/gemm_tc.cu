@@ -13,19 +13,17 @@
 //   G3: D[a][j] = sum_i Q1[a][i] WT[j][i]     -> Y[a][j]     (Y = Q1 W)
 //   G4: D[a][b] = sum_j Y[a][j] Q2[b][j]      -> Z[a][b]     (Z = Y Q2^T), + <R, Z> partials
 //
-// Kernel (k_gemm_p): 128 x 256 output tiles per CTA (M = 128 TMEM lanes, N = 256
-// FP32 TMEM columns), a persistent grid of CTA pairs (2-CTA clusters, one CTA
-// per SM) walking all 256 x 256 pair tiles of all instances.  The two CTAs of a
-// pair compute vertically adjacent tiles with the same B operand: each loads
-// its own A slice and one half of the B slice, multicast into both CTAs' shared
-// memory, so the L2-to-SM traffic per MMA is 2/3 of a lone CTA's.  TMA loads
-// 128-byte-wide K slices (SWIZZLE_128B) into a 4-stage ring; one thread issues
-// tcgen05.mma (kind::f16 with BF16/FP16 operands, or kind::tf32) and releases a
-// stage in both CTAs with a multicast tcgen05.commit; two TMEM accumulators let
-// the epilogue (tcgen05.ld 32x32b.x32) of one tile overlap the mainloop of the
-// next.  Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the CTA
-// records DEV_ERR_TIMEOUT, stops all roles, frees its TMEM and exits (the peer
-// then times out as well).
+// Kernel (k_gemm_2sm): a persistent grid of CTA pairs (2-CTA clusters, one CTA
+// per SM) walking all 256 x 256 output tiles of all instances.  Each pair
+// computes one tile with tcgen05.mma.cta_group::2 (M = 256 split over the two
+// SMs' TMEM lanes, N = 256 FP32 TMEM columns): CTA r stages rows 128 r .. of the
+// A and of the B slice of every 128-byte K step (SWIZZLE_128B TMA boxes, 6-stage
+// ring of 32 KB), the leader CTA issues the MMAs (kind::f16 with FP16/BF16
+// operands, or kind::tf32), and two TMEM accumulators let the epilogue
+// (tcgen05.ld 32x32b.x32) of one tile overlap the mainloop of the next.  Every
+// mbarrier wait is bounded (2 s of %globaltimer); on expiry the CTA records
+// DEV_ERR_TIMEOUT, stops all roles, frees its TMEM and exits (the peer then
+// times out as well).
 #include "internal.h"
 
 #include <cuda_bf16.h>
@@ -34,11 +32,7 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 4;
-constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int BM = 128, BN = 256;   // output rows per CTA (TMEM lanes), columns per tile
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 
 enum { EPI_STORE = 0, EPI_DIV = 1, EPI_Z = 2 };
@@ -110,54 +104,6 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = fmt (0 F16 or 1 BF16 under kind::f16,
-// 2 TF32 under kind::tf32), both K-major, N = BN, M = BM.
-__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-// KIND: 0 TF32 (kind::tf32), 1 BF16 and 2 FP16 (kind::f16, A and B of the same type)
-template <int KIND>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    if constexpr (KIND == 2) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(0)), "r"(acc)
-            : "memory");
-    } else if constexpr (KIND == 1) {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(1)), "r"(acc)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc(2)), "r"(acc)
-            : "memory");
-    }
-}
-
-// TMA load written to the same shared-memory offset of every CTA in `mask`
-// (cluster multicast); each destination CTA's mbarrier at offset `mbar` receives
-// the transaction bytes.
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
-                                               int c2, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4, %5}], [%2], %6;"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-        : "memory");
-}
-
-// Arrive (once) on the mbarrier at offset `mbar` of every CTA in `mask` when all
-// prior tcgen05.mma of this thread have completed.
-__device__ __forceinline__ void mma_commit_mc(uint32_t mbar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-        ::"r"(mbar), "h"(mask)
-        : "memory");
-}
-
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -167,11 +113,6 @@ __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -191,23 +132,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent, warp-specialised variant (the one launched): one CTA per SM walks
-// the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of all instances.
+// Shared pieces of the persistent, warp-specialised GEMM: 192 threads,
 //   warps 0-3 : epilogue (TMEM lanes 0-127 = output rows), overlapping the next
 //               tile's mainloop thanks to two TMEM accumulators (2 x 256 columns)
-//   warp 4    : TMA producer (4-stage ring, 128-byte swizzled K slices)
+//   warp 4    : TMA producer
 //   warp 5    : TMEM allocation and tcgen05.mma issue (one elected lane)
-// Barriers: full/empty per stage, tfull/tempty per accumulator.  Every wait is
-// bounded; a timeout raises a CTA-wide abort flag that ends all roles.
+// Every wait is bounded; a timeout raises a CTA-wide abort flag that ends all roles.
 constexpr int P_THREADS = 192;
 constexpr uint32_t TMEM_COLS_P = 512;
-
-struct PBars {
-    uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
-    uint32_t tmem_slot;
-    int abort;
-    double red[2][4];
-};
 
 __device__ __forceinline__ bool pwait(uint32_t a, uint32_t parity, volatile int* abort) {
     if (mbar_try(a, parity)) return true;
@@ -310,81 +242,137 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, in
     }
 }
 
-// CM CTAs per cluster (1 or 2) share the B slice of each K step; the B tensor
-// map's box is BN / 2 = 128 rows, loaded twice by a lone CTA.
-template <int KIND, int CM>
+// ---------------------------------------------------------------------------
+// k_gemm_2sm: each 2-CTA cluster computes one 256 x 256 tile with
+// tcgen05.mma.cta_group::2 (M = 256 across the pair, N = 256).  CTA r holds rows
+// 128 r .. 128 r + 127 of the A slice and of the B slice of every K step in its
+// own shared memory (32 KB per stage, 6 stages); the leader CTA (rank 0) issues
+// the MMAs, which read both CTAs' halves and write D rows 128 r .. 128 r + 127
+// (all 256 columns) into CTA r's TMEM.  Both CTAs' TMA loads complete on the
+// leader's stage barrier; the leader's commits release the stage and the
+// finished accumulator in both CTAs (multicast); both CTAs' epilogue warps
+// release an accumulator on the leader's barrier.  Each SM receives 32 KB per
+// 512 tensor cycles instead of 48 KB (the K-slice bytes per MMA are what bound
+// the 1-SM tiles).
+constexpr int ST2 = 6;
+constexpr int A2_BYTES = 128 * 128, B2_BYTES = 128 * 128;
+constexpr int STAGE2_BYTES = A2_BYTES + B2_BYTES;
+
+struct PBars2 {
+    uint64_t full[ST2], empty[ST2], tfull[2], tempty[2];
+    uint32_t tmem_slot;
+    int abort;
+    double red[2][4];
+};
+
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on an
+// mbarrier of either CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, uint32_t mbar_cluster, int c0,
+                                                 int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar_cluster), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+__host__ __device__ constexpr uint32_t make_idesc2(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+template <int KIND>
+__device__ __forceinline__ void mma2(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    if constexpr (KIND == 0) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc2(2)), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d), "l"(a), "l"(b), "r"(make_idesc2(KIND == 2 ? 0u : 1u)), "r"(acc)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void commit2_mc(uint32_t mbar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+        ::"r"(mbar), "h"(mask)
+        : "memory");
+}
+
+template <int KIND>
 __global__ void __launch_bounds__(P_THREADS, 1)
-    k_gemm_p(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
-    static_assert(CM == 1 || CM == 2, "pairs at most");
-    constexpr int BH = BN / 2;                  // rows of one B box
-    constexpr uint16_t MASK = (1u << CM) - 1u;  // all CTAs of the cluster
+    k_gemm_2sm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    PBars* pb = reinterpret_cast<PBars*>(smem + STAGES * STAGE_BYTES);
+    PBars2* pb = reinterpret_cast<PBars2*>(smem + ST2 * STAGE2_BYTES);
     volatile int* abort_flag = &pb->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cr = CM > 1 ? (int)cluster_rank() : 0;          // position in the pair (M half)
-    const int cid = blockIdx.x / CM, ncl = gridDim.x / CM;    // pair index, pairs
-    const int ntn = (g.N + BN - 1) / BN, ntm = (g.M + BM * CM - 1) / (BM * CM);
-    const int per_inst = ntn * ntm;           // pair tiles per instance
+    const int cr = (int)cluster_rank();
+    const bool leader = cr == 0;
+    const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
+    const int ntn = (g.N + 255) / 256, ntm = (g.M + 255) / 256;
+    const int per_inst = ntn * ntm;   // pair tiles per instance
     const int total = per_inst * g.batch;
     constexpr int BK = 128 / (KIND == 0 ? 4 : 2);
     auto bar_addr = [&](uint64_t* b) { return smem_u32(b); };
     auto active = [&](int inst) { return !g.sc || g.sc[inst].active; };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < ST2; ++s) {
             mbar_init(bar_addr(&pb->full[s]), 1);
-            mbar_init(bar_addr(&pb->empty[s]), CM);   // released by the MMA of every CTA that reads it
+            mbar_init(bar_addr(&pb->empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(bar_addr(&pb->tfull[b]), 1);
-            mbar_init(bar_addr(&pb->tempty[b]), 4);
+            mbar_init(bar_addr(&pb->tempty[b]), 8);   // 4 epilogue warps in each CTA
         }
         pb->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+    if (warp == 5) {   // joint allocation: one warp in each CTA of the pair
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&pb->tmem_slot)),
                      "r"(TMEM_COLS_P)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     __syncthreads();
-    if constexpr (CM > 1) cluster_sync_all();   // the peer's multicasts may target our barriers from here on
+    cluster_sync_all();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = pb->tmem_slot;
 
     if (warp == 4) {
-        if (lane == 0) {   // ---- TMA producer
+        if (lane == 0) {   // ---- TMA producer (both CTAs): own halves of A and B
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB)) : "memory");
             int it = 0;
             for (int t = cid; t < total && !*abort_flag; t += ncl) {
                 const int inst = t / per_inst, r = t - inst * per_inst;
                 if (!active(inst)) continue;
-                const int m0 = (r / ntn) * (BM * CM) + cr * BM, n0 = (r % ntn) * BN;
+                const int m0 = (r / ntn) * 256 + cr * 128, nh = (r % ntn) * 256 + cr * 128;
                 const int za = g.a_shared ? 0 : inst, zb = g.b_shared ? 0 : inst;
                 for (int kb = 0; kb < g.nk; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (it >= STAGES && !pwait(bar_addr(&pb->empty[s]), ph ^ 1u, abort_flag)) break;
-                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-                    const uint32_t fb = bar_addr(&pb->full[s]);
-                    mbar_expect_tx(fb, STAGE_BYTES);   // own A + both B halves (one from the peer)
-                    tma_load_3d(sa, &mA, fb, kb * BK, m0, za);
-                    if constexpr (CM == 1) {
-                        tma_load_3d(sa + A_BYTES, &mB, fb, kb * BK, n0, zb);
-                        tma_load_3d(sa + A_BYTES + BH * 128, &mB, fb, kb * BK, n0 + BH, zb);
-                    } else {
-                        tma_load_3d_mc(sa + A_BYTES + cr * BH * 128, &mB, fb, kb * BK, n0 + cr * BH, zb, MASK);
-                    }
+                    const int s = it % ST2;
+                    const uint32_t ph = (uint32_t)(it / ST2) & 1u;
+                    if (it >= ST2 && !pwait(bar_addr(&pb->empty[s]), ph ^ 1u, abort_flag)) break;
+                    const uint32_t sa = smem_u32(smem + s * STAGE2_BYTES);
+                    const uint32_t fl = mapa_shared(bar_addr(&pb->full[s]), 0);
+                    if (leader) mbar_expect_tx(bar_addr(&pb->full[s]), 2 * STAGE2_BYTES);   // both CTAs' halves
+                    tma_load_3d_pair(sa, &mA, fl, kb * BK, m0, za);
+                    tma_load_3d_pair(sa + A2_BYTES, &mB, fl, kb * BK, nh, zb);
                 }
             }
         }
     } else if (warp == 5) {
-        if (lane == 0) {   // ---- MMA issuer
+        if (lane == 0 && leader) {   // ---- MMA issuer (leader CTA only)
             int it = 0, tl = 0;
             for (int t = cid; t < total && !*abort_flag; t += ncl) {
                 const int inst = t / per_inst;
@@ -396,33 +384,32 @@ __global__ void __launch_bounds__(P_THREADS, 1)
                 const uint32_t d = tmem + (uint32_t)(b * 256);
                 bool ok = true;
                 for (int kb = 0; kb < g.nk; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    const int s = it % ST2;
+                    const uint32_t ph = (uint32_t)(it / ST2) & 1u;
                     if (!pwait(bar_addr(&pb->full[s]), ph, abort_flag)) {
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t sa = smem_u32(smem + s * STAGE2_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        mma<KIND>(d, make_desc(sa + 32 * kk), make_desc(sa + A_BYTES + 32 * kk), (kb | kk) != 0);
-                    if constexpr (CM == 1) mma_commit(bar_addr(&pb->empty[s]));
-                    else mma_commit_mc(bar_addr(&pb->empty[s]), MASK);   // the stage is free in both CTAs
+                        mma2<KIND>(d, make_desc(sa + 32 * kk), make_desc(sa + A2_BYTES + 32 * kk), (kb | kk) != 0);
+                    commit2_mc(bar_addr(&pb->empty[s]), 3);   // stage free in both CTAs
                 }
-                mma_commit(bar_addr(&pb->tfull[b]));
+                commit2_mc(bar_addr(&pb->tfull[b]), 3);       // accumulator ready in both CTAs
                 ++tl;
                 if (!ok) break;
             }
         }
-    } else {   // ---- epilogue warps 0-3: thread = TMEM lane = output row within the tile
+    } else {   // ---- epilogue warps 0-3 (both CTAs): thread = TMEM lane = output row
         int tl = 0;
-        const int cta_per_inst = per_inst * CM;   // <R, Z> partial slots (one per CTA tile)
+        const int cta_per_inst = per_inst * 2;
         for (int t = cid; t < total; t += ncl) {
             const int inst = t / per_inst, r = t - inst * per_inst;
             if (!active(inst)) continue;
-            const int m0 = (r / ntn) * (BM * CM) + cr * BM, n0 = (r % ntn) * BN;
-            const int ct = ((r / ntn) * CM + cr) * ntn + (r % ntn);
+            const int m0 = (r / ntn) * 256 + cr * 128, n0 = (r % ntn) * 256;
+            const int ct = ((r / ntn) * 2 + cr) * ntn + (r % ntn);
             const int b = tl & 1;
             const uint32_t use = (uint32_t)(tl >> 1);
             const bool ok = pwait(bar_addr(&pb->tfull[b]), use & 1u, abort_flag);
@@ -435,7 +422,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             if (g.epi == EPI_DIV && m_ok) mu_m = g.mu[m];
             double acc = 0.0;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = 0; c < 256 / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256 + c * 32), v);
                 const int nb = n0 + c * 32;
@@ -443,7 +430,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar_addr(&pb->tempty[b]));
+            if (lane == 0) mbar_arrive_cluster(mapa_shared(bar_addr(&pb->tempty[b]), 0));
             if (g.epi == EPI_Z && g.rz_part) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -483,12 +470,11 @@ __global__ void __launch_bounds__(P_THREADS, 1)
         }
     }
     __syncthreads();
-    // no CTA leaves while its peer may still multicast into it or arrive on its barriers
-    if constexpr (CM > 1) cluster_sync_all();
+    cluster_sync_all();   // the peer's copies, commits and arrivals have all landed
     if (threadIdx.x == 0 && pb->abort && g.status) atomicOr(g.status, DEV_ERR_TIMEOUT);
     if (warp == 5) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS_P) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS_P) : "memory");
     }
 }
 
@@ -575,14 +561,14 @@ int num_sms() {
     return n;
 }
 
-constexpr int GEMM_CM = 2;   // CTAs per cluster sharing B
+constexpr int GEMM_CM = 2;   // CTAs per cluster: one tcgen05 CTA pair
 
 template <int KIND>
 mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g0, int batch, cudaStream_t st) {
     constexpr int CM = GEMM_CM;
-    auto kern = k_gemm_p<KIND, CM>;
+    auto kern = k_gemm_2sm<KIND>;
     static int max_pairs = 0;
-    const int smem = STAGES * STAGE_BYTES + 1024 + (int)sizeof(PBars) + 64;
+    const int smem = ST2 * STAGE2_BYTES + 1024 + (int)sizeof(PBars2) + 64;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
