@@ -61,6 +61,27 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x, world):
+    """MAX of a per-rank float over all ranks: a device tensor under NCCL, a CPU tensor under gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_config(a, B, world):
+    """The `config` object shared by both arms (instances of the metric workload, sharded by rank)."""
+    q = a.n - 2
+    return {"workload": f"P{a.k} elliptic -Lap u + u = f, {a.n}x{a.n} nodes (q={q}), Dirichlet, domain "
+                        f"0<=y<=1+0.25sin(2pi x), 32-mode Fourier f, rtol {a.rtol:g}",
+            "global_batch": B * world, "batch_per_gpu": B, "precision": a.precision,
+            "parallelism": f"instances sharded over {world} GPU(s), no collective"}
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
 
@@ -157,8 +178,8 @@ def run_reference(a):
     if world > 1 and rank != 0:
         return 0
     inst = make_inputs(1, a.n, a.k, 0)[0]
-    # iterations the method needs at this size (FP64 MO-PCG, same preconditioner)
-    iters_needed = 45
+    # iterations of FP64 MO-PCG with the same preconditioner at this size (the FP64 GPU form: 43)
+    iters_needed = 43
     samples = []
     t_setup = None
     for s in range(a.warmup + a.steps):
@@ -172,8 +193,9 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t_iter * a.ref_iters * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"P{a.k} elliptic, {a.n}x{a.n} nodes, q={a.n - 2}, curved domain 1+0.25sin(2pi x), "
-                               f"32-mode Fourier f", "global_batch": 1, "l2": "inputs larger than L2 (CPU)"},
+        "config": dict(workload_config(a, a.batch, world), precision="fp64",
+                       l2="inputs larger than L2 (CPU)",
+                       instances="solved one after another on the host: solves/s does not depend on the batch"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                          "sample": f"{a.ref_iters} oracle MO-PCG iterations per step (numpy/scipy FP64, reduced "
                                    f"preconditioner, setup {t_setup:.1f}s excluded); solves/s = 1/(s_per_iter x "
@@ -242,11 +264,7 @@ def run_mofem(a):
     barrier()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, world)
     value = B * world * a.steps / elapsed
     ms_step = elapsed / a.steps * 1e3
     ms_iter = elapsed * 1e3 / max(sum(iters), 1)
@@ -266,11 +284,7 @@ def run_mofem(a):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_elapsed = e0.elapsed_time(e1) / 1e3
-    t = torch.tensor([e2e_elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = B * world * a.steps / float(t.item())
+    e2e_value = B * world * a.steps / max_over_ranks(e2e_elapsed, world)
     err_e2e = float((U_host.cuda() - U).abs().max().item())
 
     # ---- hot-kernel timing (CUDA events on the launching stream) ---------------------
@@ -331,12 +345,9 @@ def run_mofem(a):
         "dtype": {"fp16": "f16-gemm/f32-vec/f64-refine", "bf16": "bf16-gemm/f32-vec/f64-refine",
                   "tf32": "tf32-gemm/f32-vec/f64-refine", "fp64": "f64"}[a.precision],
         "data": "synthetic",
-        "config": {"workload": f"P{k} elliptic -Lap u + u = f, {n}x{n} nodes (q={q}), Dirichlet, domain "
-                               f"0<=y<=1+0.25sin(2pi x), 32-mode Fourier f, rtol {a.rtol:g}",
-                   "global_batch": B * world, "batch_per_gpu": B, "precision": a.precision,
-                   "l2": f"inputs larger than L2 (working set ~{working_set_mb:.0f} MB per GPU)",
-                   "parallelism": f"instances sharded over {world} GPU(s), no collective",
-                   "inner_loop": "host-stepped graphs" if a.host_loop else "conditional-node CUDA graph"},
+        "config": dict(workload_config(a, B, world),
+                       l2=f"inputs larger than L2 (working set ~{working_set_mb:.0f} MB per GPU)",
+                       inner_loop="host-stepped graphs" if a.host_loop else "conditional-node CUDA graph"),
         "ms_per_iter": ms_iter, "iterations_per_solve": statistics.mean(iters),
         "rel_residual_max": max(rels), "setup_s": setup_s,
         "gpu_launches": launches,
@@ -350,7 +361,8 @@ def run_mofem(a):
                                     + (" / 2 for TF32" if prec_k == "tf32" else ""),
                      "per_gemm_us": [round(t * 1e6, 2) for t in t_gemm],
                      "per_gemm_tflops": [round(x, 1) for x in gemm_tflops]},
-        "roofline_apply": {"bound": "hbm", "kernel": f"k_apply_pcg2<K={k},NT=5> (packed FP32, PCG form)",
+        "roofline_apply": {"bound": "hbm", "kernel": (f"k_apply_pcg2<K={k},NT=5> (packed FP32, PCG form)" if k <= 3 else
+                                      f"k_apply_pcg<float,K={k},NT=5> (scalar FP32, PCG form)"),
                            "achieved": apply_bytes / t_apply / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                            "frac": apply_bytes / t_apply / 1e9 / peaks["hbm_gbs"], "us": t_apply * 1e6},
         "roofline_update": {"bound": "hbm", "kernel": f"k_update<float,double-float U,{a.precision} operand copy>",

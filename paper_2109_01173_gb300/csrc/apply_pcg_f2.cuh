@@ -208,28 +208,33 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, 3)
         for (int u = 0; u < P; ++u) {
             const int al = lr0 + m * P + u;   // tile-local output row
             tpass(al + 2 * K, (u + P - 1) % P);
-            const float2* srow = S2s + al * SR2;
+            // row coefficients as 16-byte broadcasts: float4 e/2 holds coefficients e, e+1 (SR2 even)
+            const float4* srow4 = reinterpret_cast<const float4*>(S2s + al * SR2);
+            auto sc2 = [&](int e) -> float2 {
+                const float4 v = srow4[e >> 1];
+                return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+            };
             float2 yt[NT];
             {
                 const float2 xc = xr0[(u + K) % P], wc = ring[0][(u + K) % P];
-                float2 ya = f2mul(srow[K], xc), yb = f2mul(srow[K], wc);
+                float2 ya = f2mul(sc2(K), xc), yb = f2mul(sc2(K), wc);
 #pragma unroll
                 for (int j = 0; j < P; ++j)
                     if (j != K) {
-                        ya = f2fma(srow[j], f2sub(xr0[(u + j) % P], xc), ya);
-                        yb = f2fma(srow[j], f2sub(ring[0][(u + j) % P], wc), yb);
+                        ya = f2fma(sc2(j), f2sub(xr0[(u + j) % P], xc), ya);
+                        yb = f2fma(sc2(j), f2sub(ring[0][(u + j) % P], wc), yb);
                     }
                 yt[0] = f2mul(d0, f2add(ya, yb));
             }
 #pragma unroll
             for (int i = 1; i < NT; ++i) {
                 const float2 wc = ring[i][(u + K) % P];
-                float2 y = f2mul(srow[i * P + K], wc);
+                float2 y = f2mul(sc2(i * P + K), wc);
 #pragma unroll
                 for (int j = 0; j < P; ++j)
                     if (j != K) {
-                        if ((DM >> i) & 1u) y = f2fma(srow[i * P + j], f2sub(ring[i][(u + j) % P], wc), y);
-                        else y = f2fma(srow[i * P + j], ring[i][(u + j) % P], y);
+                        if ((DM >> i) & 1u) y = f2fma(sc2(i * P + j), f2sub(ring[i][(u + j) % P], wc), y);
+                        else y = f2fma(sc2(i * P + j), ring[i][(u + j) % P], y);
                     }
                 yt[i] = y;
             }

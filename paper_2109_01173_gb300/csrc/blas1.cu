@@ -431,16 +431,23 @@ __global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const d
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) row[j] /= (li + mu[j]);
 }
 
-// U64 += hi + lo (end of an inner solve of the mixed form), then hi = lo = 0.
-__global__ void k_fold_df(double* U, long long bs, float* hi, float* lo, long long n) {
+// U64 += hi + lo at the end of an inner solve of the mixed form (the pair is
+// cleared before the next inner solve starts).  16-byte vectors: n % 4 == 0.
+__global__ void k_fold_df(double* U, long long bs, const float* hi, const float* lo, long long n) {
     const int inst = blockIdx.y;
-    U += (size_t)inst * bs;
-    hi += (size_t)inst * bs;
-    lo += (size_t)inst * bs;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        U[i] += (double)hi[i] + (double)lo[i];
-        hi[i] = 0.f;
-        lo[i] = 0.f;
+    double2* U2 = reinterpret_cast<double2*>(U + (size_t)inst * bs);
+    const float4* h4 = reinterpret_cast<const float4*>(hi + (size_t)inst * bs);
+    const float4* l4 = reinterpret_cast<const float4*>(lo + (size_t)inst * bs);
+    const long long nv = n / 4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+        const float4 h = h4[i], l = l4[i];
+        double2 a = U2[2 * i], b = U2[2 * i + 1];
+        a.x += (double)h.x + (double)l.x;
+        a.y += (double)h.y + (double)l.y;
+        b.x += (double)h.z + (double)l.z;
+        b.y += (double)h.w + (double)l.w;
+        U2[2 * i] = a;
+        U2[2 * i + 1] = b;
     }
 }
 
@@ -569,6 +576,7 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
 }
 
 mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, cudaStream_t st) {
+    if (bs % 4 != 0) return MOFEM_ERR_INVALID_ARG;   // internal layout: ld is a multiple of 64
     dim3 grid(592, batch);
     k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs);
     MOFEM_CUDA_TRY(cudaGetLastError());
