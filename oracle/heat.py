@@ -1,0 +1,93 @@
+"""IMEX Euler for the heat equation and its discrete adjoint (oracle).
+
+Test infrastructure only: only tests/, the package's smoke check and the bench's
+CPU baseline may import it.
+
+Sec. 6 (Eqs. semilinear_heat_equation_fully_discrete_sylvester_pk and _R_pk):
+u_t - d_u Lap u = f(u) with the diffusion implicit and f explicit,
+
+    (M~ + d_u tau A~) U_{n+1} = M~ (U_n + tau F(U_n)),
+
+where, in the matrix-oriented form of Sec. 5, A~ is the multiterm operator
+U -> sum_i S_i U T_i^T of the Laplacian (Problem with gamma = 0) and
+M~ : U -> M_s[h] U M_t^T the mass operator, both on the interior (Dirichlet) or
+all (Neumann) nodes.  Here both are assembled as sparse Kronecker matrices acting
+on vec(U) (row-major: kron(S, T) vec(U) = vec(S U T^T)) and every step is a direct
+sparse solve: no iteration, no preconditioner.
+
+For f = 0 one step is the linear map U_{n+1} = S^{-1} M U_n with the symmetric
+positive definite S = M + d_u tau A.  For a loss J(U_N) of the final state the
+discrete adjoint (derived here; the paper does not differentiate) is
+
+    lam_N = dJ/dU_N,
+    for n = N-1 .. 0:   y = S^{-1} lam_{n+1},   lam_n = M y,
+                        dJ/dd_u += -tau <y, A U_{n+1}>_F,
+    dJ/dU_0 = lam_0,
+
+from differentiating S U_{n+1} = M U_n:  S dU_{n+1} = M dU_n - tau dd_u A U_{n+1}.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .fem1d import trim
+from .operator import Problem
+
+
+def kron_operator(terms):
+    """Sparse matrix of U -> sum_i S_i U T_i^T on row-major vec(U)."""
+    out = None
+    for S, T in terms:
+        K = sp.kron(sp.csr_matrix(S), sp.csr_matrix(T), format='csr')
+        out = K if out is None else out + K
+    return out.tocsc()
+
+
+class HeatOperators:
+    """A (stiffness, gamma = 0) and M (mass) of a domain as sparse q^2 x q^2 matrices."""
+
+    def __init__(self, g1, g2, k, n, bc='dirichlet'):
+        P = Problem(g1, g2, k, n, 0.0, bc=bc)
+        self.problem = P
+        self.q = P.q
+        self.A = kron_operator(P.terms())
+        f = P.factors()
+        self.M = sp.kron(trim(f['Ms_h'], P.idx), trim(f['Mt'], P.idx), format='csc')
+
+    def system(self, d_u, tau):
+        """Factorised S = M + d_u tau A."""
+        return spla.splu((self.M + (d_u * tau) * self.A).tocsc())
+
+
+def imex_forward(ops, d_u, tau, U0, n_steps, F=None):
+    """States U_0 .. U_N of IMEX Euler; F(U) -> nodal f on the q x q unknowns (None: f = 0)."""
+    lu = ops.system(d_u, tau)
+    q = ops.q
+    U = np.asarray(U0, dtype=np.float64).reshape(q, q)
+    states = [U]
+    for _ in range(n_steps):
+        rhs_v = U.ravel()
+        if F is not None:
+            rhs_v = rhs_v + tau * np.asarray(F(U), dtype=np.float64).ravel()
+        U = lu.solve(ops.M @ rhs_v).reshape(q, q)
+        states.append(U)
+    return states
+
+
+def imex_adjoint(ops, d_u, tau, states, dJ_dUN):
+    """(dJ/dU_0, dJ/dd_u) for f = 0 by the discrete adjoint recursion of the module docstring."""
+    lu = ops.system(d_u, tau)
+    q = ops.q
+    lam = np.asarray(dJ_dUN, dtype=np.float64).ravel()
+    g_du = 0.0
+    for n in range(len(states) - 2, -1, -1):
+        y = lu.solve(lam)           # S symmetric: S^T = S
+        g_du -= tau * float(y @ (ops.A @ states[n + 1].ravel()))
+        lam = ops.M @ y
+    return lam.reshape(q, q), g_du
+
+
+def loss(UN, target):
+    """J = ||U_N - U_target||_F^2 and dJ/dU_N."""
+    D = np.asarray(UN) - np.asarray(target)
+    return float(np.sum(D * D)), 2.0 * D
