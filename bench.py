@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-heat", action="store_true", help="skip the differentiation workload (heat IMEX + adjoint)")
     ap.add_argument("--host-loop", action="store_true",
                     help="step the inner loop from the host instead of a conditional-node CUDA graph "
                          "(per-kernel profilers cannot see kernels inside conditional graphs)")
@@ -147,6 +148,46 @@ def measured_peaks():
 def make_inputs(B, n, k, rank):
     from paper_2109_01173_gb300.inputs import metric_instance
     return [metric_instance(n=n, k=k, seed=rank * B + i) for i in range(B)]
+
+
+# ----------------------------------------------------------------------------------
+def measure_heat():
+    """Differentiation workload: 400 IMEX Euler heat steps (P2, 513 x 513, Neumann, two
+    profiles) forward with checkpoints every 50 steps, then the adjoint backward pass
+    (recomputation + 400 adjoint solves), timed with CUDA events; host-driven step loop."""
+    import torch
+    import paper_2109_01173_gb300.mofem as mf
+    from paper_2109_01173_gb300 import adjoint as adj
+    from paper_2109_01173_gb300.inputs import heat_config, smoothed_uniform
+    cfg = heat_config()
+    q, steps, every = cfg["n"], cfg["steps"], cfg["every"]
+    setup = adj.HeatSetup(cfg["g1"], cfg["g2"], cfg["k"], cfg["n"], cfg["tau"], bc=mf.NEUMANN, precision="fp16",
+                          rtol=1e-11)
+    setup.handle(cfg["d_u"])   # setup (eigendecompositions) outside the timed region
+    T = torch.tensor(smoothed_uniform(q, 1)[None], device="cuda")
+
+    def run(n_steps):
+        U0 = torch.tensor(smoothed_uniform(q, 0)[None], device="cuda", requires_grad=True)
+        du = torch.tensor(cfg["d_u"], dtype=torch.float64, device="cuda", requires_grad=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        UN = adj.heat_imex(U0, du, setup, n_steps, every)
+        ev[1].record()
+        ((UN - T) ** 2).sum().backward()
+        ev[2].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), float(du.grad.item())
+
+    run(10)   # warm-up
+    fwd, bwd, g = run(steps)
+    setup.close()
+    return {"workload": f"u_t - d_u Lap u = 0, P{cfg['k']} {q}x{q} nodes, Neumann, 0.1x^2<=y<=1+0.2cos(pi x), "
+                        f"dt {cfg['tau']:g}, {steps} steps, d_u {cfg['d_u']:g}, checkpoints every {every}",
+            "precision": "fp16-gemm/f32-vec/f64-refine, every solve to rel. residual 1e-11",
+            "forward_ms": fwd, "backward_ms": bwd, "forward_steps_per_s": steps / (fwd / 1e3),
+            "backward_steps_per_s": steps / (bwd / 1e3), "dJ_ddu": g,
+            "check": "gradients vs central differences to 1e-5: tests/test_gpu_heat.py"}
 
 
 # ----------------------------------------------------------------------------------
@@ -373,6 +414,8 @@ def run_mofem(a):
         "fp64_form": fp64,
         "cpu_baseline": cpu,
     }
+    if not a.no_heat and rank == 0:
+        line["heat_adjoint"] = measure_heat()
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

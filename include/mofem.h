@@ -183,6 +183,29 @@ mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const doubl
                              const double* F_n, double* U_np1, mofem_precision prec,
                              mofem_solve_info* info, cudaStream_t stream);
 
+/* mofem_imex_step with an explicit stopping rule: rtol > 0 stops at
+ * ||B - (M~ + d_u tau A~) U_np1||_F <= rtol ||B||_F on the FP64 true residual
+ * (B = M~ (U_n + tau F_n)), as the elliptic solve does; rtol = 0 is the paper's
+ * rule of mofem_imex_step.  Tight tolerances make the step a smooth function of
+ * its inputs (finite-difference and adjoint checks of a time integration). */
+mofem_status mofem_imex_step_tol(mofem_handle h, double d_u, double tau, const double* U_n,
+                                 const double* F_n, double* U_np1, double rtol, mofem_precision prec,
+                                 mofem_solve_info* info, cudaStream_t stream);
+
+/* One backward step of the discrete adjoint of IMEX Euler with f = 0 (no
+ * counterpart in the paper, which does not differentiate; derived from Sec. 6's
+ * step S U_np1 = M~ U_n with S = M~ + d_u tau A~ symmetric):
+ *   Y = S^{-1} Lam_np1   (the same MO-PCG solve, ||Lam_np1 - S Y|| <= rtol ||Lam_np1||),
+ *   Lam_n = M~ Y,
+ *   dd_u[i] = -tau <Y, A~ U_np1>_F   (this step's contribution to dJ/dd_u).
+ * For a loss J(U_N) start from Lam_N = dJ/dU_N and go n = N-1 .. 0 with U_np1 the
+ * forward state after step n; Lam_0 = dJ/dU_0.  Lam_np1, U_np1, Lam_n: q x q per
+ * instance (ld q), FP64, device; Lam_n must not alias Lam_np1.  dd_u: host array
+ * of `batch` doubles.  The handle must have gamma = 1/(d_u tau).  Synchronises. */
+mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, const double* Lam_np1,
+                                     const double* U_np1, double* Lam_n, double* dd_u, double rtol,
+                                     mofem_precision prec, mofem_solve_info* info, cudaStream_t stream);
+
 /* Benchmark hook (no counterpart in the paper): launch one hot kernel `reps`
  * times on the handle's internal buffers, asynchronously on `stream`, so that
  * a caller can time it with events on that stream.  kernel:

@@ -1,0 +1,107 @@
+"""Differentiable IMEX Euler heat integration on the MO-PCG solver (Sec. 6).
+
+``HeatIMEX`` is a ``torch.autograd.Function``.  Its forward integrates
+u_t - d_u Lap u = 0 for ``n_steps`` IMEX Euler steps from U_0, each step one
+mixed-precision MO-PCG solve of (M~ + d_u tau A~) U_{n+1} = M~ U_n
+(``mofem_imex_step_tol``), and keeps every ``every``-th state as a checkpoint.
+Its backward runs the discrete adjoint (``mofem_imex_adjoint_step``: the same
+symmetric solve, a mass product and the d_u inner product), segment by
+segment from the last checkpoint, recomputing each segment's states from its
+checkpoint, and returns dJ/dU_0 and dJ/dd_u.  All arithmetic runs in libmofem;
+this module sequences the calls and holds the checkpoints.
+
+d_u enters the operator (the handle is set up with gamma = 1/(d_u tau)), so a
+``HeatSetup`` keeps one handle per d_u value it has seen.
+"""
+import torch
+
+from . import mofem as mf
+
+
+class HeatSetup:
+    """Domain, discretisation and solver settings of a heat integration.
+
+    ``batch`` independent initial states share d_u (the loss is their sum).
+    ``rtol`` is the FP64 relative residual of every forward and adjoint solve.
+    """
+
+    def __init__(self, g1, g2, k, n, tau, bc=mf.NEUMANN, precision="fp16", rtol=1e-11, batch=1):
+        self.g1, self.g2, self.k, self.n, self.tau, self.bc = g1, g2, k, n, float(tau), bc
+        self.precision, self.rtol, self.batch = precision, float(rtol), batch
+        self._handles = {}
+        self.F0 = None
+
+    def handle(self, d_u):
+        key = float(d_u)
+        h = self._handles.get(key)
+        if h is None:
+            gam = 1.0 / (key * self.tau)
+            B = self.batch
+            h = mf.Handle([self.g1] * B, [self.g2] * B, self.k, self.n, [gam] * B, bc=self.bc)
+            self._handles[key] = h
+            if self.F0 is None:
+                self.F0 = torch.zeros((B, self.n, self.n), dtype=torch.float64, device="cuda")
+        return h
+
+    def step(self, h, d_u, U):
+        """One forward step from U (B x q x q, FP64, device); f = 0."""
+        out = torch.empty_like(U)
+        h.imex_step_tol(float(d_u), self.tau, U, self.F0, out, self.rtol, self.precision)
+        return out
+
+    def adjoint_step(self, h, d_u, lam, U1):
+        """(M~ S^{-1} lam, this step's dJ/dd_u) with U1 the state after the step."""
+        out = torch.empty_like(lam)
+        dd, _, _ = h.imex_adjoint_step(float(d_u), self.tau, lam, U1, out, self.rtol, self.precision)
+        return out, float(sum(dd))
+
+    def close(self):
+        for h in self._handles.values():
+            h.close()
+        self._handles.clear()
+
+
+class HeatIMEX(torch.autograd.Function):
+    """U_N = HeatIMEX.apply(U0, d_u, setup, n_steps, every).
+
+    U0: (B, q, q) FP64 CUDA tensor; d_u: 0-dim tensor.  Gradients flow to both.
+    """
+
+    @staticmethod
+    def forward(ctx, U0, d_u, setup, n_steps, every):
+        du = float(d_u)
+        h = setup.handle(du)
+        U = U0.detach().to(torch.float64).contiguous()
+        ckpt = [U]
+        for i in range(n_steps):
+            U = setup.step(h, du, U)
+            if (i + 1) % every == 0 and i + 1 < n_steps:
+                ckpt.append(U)
+        ctx.setup, ctx.n_steps, ctx.every, ctx.du = setup, n_steps, every, du
+        ctx.ckpt = ckpt
+        ctx.du_meta = (d_u.dtype, d_u.device)
+        return U
+
+    @staticmethod
+    def backward(ctx, gU):
+        setup, N, M, du = ctx.setup, ctx.n_steps, ctx.every, ctx.du
+        h = setup.handle(du)
+        lam = gU.detach().to(torch.float64).contiguous()
+        g_du = 0.0
+        for s in range(len(ctx.ckpt) - 1, -1, -1):
+            start, stop = s * M, min(s * M + M, N)
+            states = [ctx.ckpt[s]]
+            for _ in range(start, stop):
+                states.append(setup.step(h, du, states[-1]))
+            for n in range(stop - 1, start - 1, -1):
+                lam, dd = setup.adjoint_step(h, du, lam, states[n + 1 - start])
+                g_du += dd
+        ctx.ckpt = None
+        gu0 = lam if ctx.needs_input_grad[0] else None
+        gdu = torch.tensor(g_du, dtype=ctx.du_meta[0], device=ctx.du_meta[1]) if ctx.needs_input_grad[1] else None
+        return gu0, gdu, None, None, None
+
+
+def heat_imex(U0, d_u, setup, n_steps, every=50):
+    """Differentiable U_N of IMEX Euler (see HeatIMEX)."""
+    return HeatIMEX.apply(U0, d_u, setup, n_steps, every)

@@ -24,13 +24,20 @@
 
 namespace mofem_apply_impl {
 
+#ifndef MOFEM_APPLY_ROWS
+#define MOFEM_APPLY_ROWS 20   // target output rows per row group (rounded up to whole ring periods)
+#endif
+#ifndef MOFEM_APPLY_MINB
+#define MOFEM_APPLY_MINB 3    // resident CTAs per SM the register budget is sized for
+#endif
+
 template <int K, int NT>
 struct Geo2 {
     static constexpr int P = 2 * K + 1;
     static constexpr int NPAIR = TB / 2;                 // column pairs per CTA
     static constexpr int RG = 2;                         // row groups
     static constexpr int NTH = NPAIR * RG;               // threads per CTA
-    static constexpr int MRG = (20 + P - 1) / P;         // ring periods per group
+    static constexpr int MRG = (MOFEM_APPLY_ROWS + P - 1) / P;   // ring periods per group
     static constexpr int TAG = MRG * P;                  // output rows per group
     static constexpr int TA = RG * TAG;                  // output rows per CTA
     static constexpr int HR = TA + 2 * K;                // staged rows
@@ -56,7 +63,7 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(
 __device__ __forceinline__ float2 f2sub(float2 a, float2 c) { return __ffma2_rn(c, make_float2(-1.f, -1.f), a); }
 
 template <int K, int NT>
-__global__ void __launch_bounds__(Geo2<K, NT>::NTH, 3)
+__global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     k_apply_pcg2(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mQ,
                  const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a) {
     using G = Geo2<K, NT>;

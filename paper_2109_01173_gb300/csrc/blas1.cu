@@ -458,6 +458,15 @@ __global__ void k_axpy_into64(double* U, long long u_bs, int u_ld, const float* 
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q; c += gridDim.x * blockDim.x) u[c] += (double)dv[c];
 }
 
+// dst = s * src over rows x cols (FP64, own leading dimensions).
+__global__ void k_scale_copy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
+                               int cols, double s) {
+    const int inst = blockIdx.z, r = blockIdx.y;
+    const double* a = src + (size_t)inst * s_bs + (size_t)r * s_ld;
+    double* b = dst + (size_t)inst * d_bs + (size_t)r * d_ld;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) b[c] = s * a[c];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -594,6 +603,15 @@ mofem_status launch_convert_scaled_f16(const float* src, long long s_bs, int s_l
 
 mofem_status launch_set_rscale(PcgScalars* sc, const double* part, int nper, int batch, double count, cudaStream_t st) {
     k_set_rscale<<<1, 256, 0, st>>>(sc, part, nper, batch, count);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
+
+mofem_status launch_scale_copy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
+                                 int rows, int cols, int batch, double scale, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || batch <= 0) return MOFEM_OK;
+    dim3 grid((cols + 255) / 256, rows, batch);
+    k_scale_copy64<<<grid, 256, 0, st>>>(src, s_bs, s_ld, dst, d_bs, d_ld, cols, scale);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

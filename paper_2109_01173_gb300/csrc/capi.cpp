@@ -129,14 +129,35 @@ mofem_status mofem_pcg_solve(mofem_handle h, const double* F, double* U, double 
     return solve_elliptic(h, F, U, rtol, max_iter, prec, info, stream);
 }
 
-mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const double* U_n, const double* F_n,
-                             double* U_np1, mofem_precision prec, mofem_solve_info* info, cudaStream_t stream) {
-    if (!h || !U_n || !F_n || !U_np1 || !(d_u > 0.0) || !(tau > 0.0) || !valid_precision(prec))
-        return MOFEM_ERR_INVALID_ARG;
+static bool imex_gamma_ok(mofem_handle h, double d_u, double tau) {
     const double want = 1.0 / (d_u * tau);
     for (int i = 0; i < h->batch; ++i)
-        if (std::fabs(h->gamma[i] - want) > 1e-12 * want) return MOFEM_ERR_INVALID_ARG;
-    return solve_imex(h, d_u, tau, U_n, F_n, U_np1, prec, info, stream);
+        if (std::fabs(h->gamma[i] - want) > 1e-12 * want) return false;
+    return true;
+}
+
+mofem_status mofem_imex_step(mofem_handle h, double d_u, double tau, const double* U_n, const double* F_n,
+                             double* U_np1, mofem_precision prec, mofem_solve_info* info, cudaStream_t stream) {
+    return mofem_imex_step_tol(h, d_u, tau, U_n, F_n, U_np1, 0.0, prec, info, stream);
+}
+
+mofem_status mofem_imex_step_tol(mofem_handle h, double d_u, double tau, const double* U_n, const double* F_n,
+                                 double* U_np1, double rtol, mofem_precision prec, mofem_solve_info* info,
+                                 cudaStream_t stream) {
+    if (!h || !U_n || !F_n || !U_np1 || !(d_u > 0.0) || !(tau > 0.0) || !(rtol >= 0.0) || !valid_precision(prec))
+        return MOFEM_ERR_INVALID_ARG;
+    if (!imex_gamma_ok(h, d_u, tau)) return MOFEM_ERR_INVALID_ARG;
+    return solve_imex(h, d_u, tau, U_n, F_n, U_np1, rtol, prec, info, stream);
+}
+
+mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, const double* Lam_np1,
+                                     const double* U_np1, double* Lam_n, double* dd_u, double rtol,
+                                     mofem_precision prec, mofem_solve_info* info, cudaStream_t stream) {
+    if (!h || !Lam_np1 || !U_np1 || !Lam_n || !dd_u || !(d_u > 0.0) || !(tau > 0.0) || !(rtol > 0.0) ||
+        !valid_precision(prec) || Lam_n == Lam_np1)
+        return MOFEM_ERR_INVALID_ARG;
+    if (!imex_gamma_ok(h, d_u, tau)) return MOFEM_ERR_INVALID_ARG;
+    return solve_imex_adjoint(h, d_u, tau, Lam_np1, U_np1, Lam_n, dd_u, rtol, prec, info, stream);
 }
 
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps, cudaStream_t stream) {

@@ -220,5 +220,8 @@ mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs,
 mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rtol, int max_iter,
                             mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
 mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
-                        mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
+                        double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
+mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const double* Lam1, const double* U1,
+                                double* Lam0, double* dd, double rtol, mofem_precision prec, mofem_solve_info* info,
+                                cudaStream_t st);
 void mofem_free_extra(mofem_ctx* c);

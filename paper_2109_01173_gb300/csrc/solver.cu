@@ -33,6 +33,8 @@ mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo
                                bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st,
                                bool use_scalars = true);
 mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, cudaStream_t st);
+mofem_status launch_scale_copy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
+                                 int rows, int cols, int batch, double scale, cudaStream_t st);
 mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
                              cudaStream_t st);
 mofem_status launch_dot_partials(const void* A, const void* B, bool fp64, long long bs, long long n, int batch,
@@ -202,6 +204,20 @@ mofem_status op_rhs(mofem_ctx* c, const double* F, double* Bout, long long b_bs,
     a.rows_in = a.cols_in = c->n;
     a.rows_out = a.cols_out = c->q;
     a.off = c->off;
+    return launch_apply(c->K, 1, true, APPLY_PLAIN, a, c->batch, st);
+}
+
+// Y = M~ X for q x q unknowns (FP64): the right-hand-side kernel with the mass
+// factors' boundary columns dropped (interior indexing, so they meet zeros).
+static mofem_status op_mass(mofem_ctx* c, const double* X, long long x_bs, int x_ld, double* Y, long long y_bs, int y_ld,
+                            cudaStream_t st) {
+    ApplyArgs a{};
+    a.X = X; a.x_bs = x_bs; a.x_ld = x_ld;
+    a.Y = Y; a.y_bs = y_bs; a.y_ld = y_ld;
+    a.S = c->Sr64; a.s_bs = (long long)c->P * c->q; a.T = c->Tr64;
+    a.rows_in = a.cols_in = c->q;
+    a.rows_out = a.cols_out = c->q;
+    a.off = 0;
     return launch_apply(c->K, 1, true, APPLY_PLAIN, a, c->batch, st);
 }
 
@@ -634,7 +650,7 @@ mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rto
 }
 
 mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
-                        mofem_precision prec, mofem_solve_info* info, cudaStream_t st) {
+                        double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st) {
     MOFEM_TRY(ensure_common(c, st));
     const double gam = c->gamma[0];
     double* Fbar = nullptr;
@@ -647,7 +663,45 @@ mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, 
     const long long qq = (long long)c->q * c->q;
     if (Unp1 != Un)
         MOFEM_CUDA_TRY(cudaMemcpyAsync(Unp1, Un, sizeof(double) * qq * c->batch, cudaMemcpyDeviceToDevice, st));
+    // rtol > 0: ||B - S U||_F <= rtol ||B||_F; else the paper's ||R_s|| <= tau ||R_0|| (Sec. 6)
+    if (rtol > 0) return solve_core(c, Unp1, qq, c->q, rtol, 100000, prec, 0, info, st);
     return solve_core(c, Unp1, qq, c->q, tau, 100000, prec, 1, info, st);
+}
+
+// One backward step of IMEX Euler with f = 0 (discrete adjoint of solve_imex):
+// S = M~ + d_u tau A~ = d_u tau L with L the handle's operator (gamma = 1/(d_u tau)),
+//   Y = S^{-1} Lam_np1,  Lam_n = M~ Y,  dd[i] = -tau <Y, A~ U_np1> = -tau (<Y, L U> - gamma <Y, M~ U>).
+mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const double* Lam1, const double* U1,
+                                double* Lam0, double* dd, double rtol, mofem_precision prec, mofem_solve_info* info,
+                                cudaStream_t st) {
+    MOFEM_TRY(ensure_common(c, st));
+    Extra& e = extras()[c];
+    const int q = c->q, B = c->batch;
+    const long long qq = (long long)q * q;
+    double* buf = nullptr;
+    MOFEM_CUDA_TRY(cudaMallocAsync((void**)&buf, sizeof(double) * (size_t)qq * B * 3, st));
+    double *Y = buf, *LU = buf + qq * B, *MU = buf + 2 * qq * B;
+    mofem_status s = launch_scale_copy64(Lam1, qq, q, c->Bm64, (long long)per(c), c->ld, q, q, B, 1.0 / (d_u * tau), st);
+    if (s == MOFEM_OK) s = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)qq * B, st) == cudaSuccess ? MOFEM_OK
+                                                                                                    : MOFEM_ERR_CUDA;
+    mofem_status solve = MOFEM_OK;
+    if (s == MOFEM_OK) {
+        solve = solve_core(c, Y, qq, q, rtol, 100000, prec, 0, info, st);
+        if (solve != MOFEM_OK && solve != MOFEM_ERR_NOT_CONVERGED) s = solve;
+    }
+    if (s == MOFEM_OK) s = op_mass(c, Y, qq, q, Lam0, qq, q, st);
+    if (s == MOFEM_OK) s = op_apply(c, true, U1, qq, q, LU, qq, q, nullptr, st);
+    if (s == MOFEM_OK) s = op_mass(c, U1, qq, q, MU, qq, q, st);
+    std::vector<double> yl, ym;
+    if (s == MOFEM_OK) s = launch_dot_partials(Y, LU, true, qq, qq, B, e.bb_part, c->part.n_rz, st);
+    if (s == MOFEM_OK) s = sum_partials(e.bb_part, c->part.n_rz, B, yl, st);
+    if (s == MOFEM_OK) s = launch_dot_partials(Y, MU, true, qq, qq, B, e.bb_part, c->part.n_rz, st);
+    if (s == MOFEM_OK) s = sum_partials(e.bb_part, c->part.n_rz, B, ym, st);
+    cudaFreeAsync(buf, st);
+    MOFEM_TRY(s);
+    for (int i = 0; i < B; ++i) dd[i] = -tau * (yl[i] - c->gamma[i] * ym[i]);
+    if (info) info->kernel_launches += 6;
+    return solve;
 }
 
 // Benchmark hook: repeated launches of one hot kernel on internal buffers.

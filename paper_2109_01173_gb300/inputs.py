@@ -142,3 +142,28 @@ def batch_instances(B, n=2049, k=2, seed0=0):
         out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet',
                         F=fourier_f(ZERO, g2, n, seed0 + i)))
     return out
+
+
+def smoothed_uniform(q, seed, sweeps=5, batch=None):
+    """Seeded uniform[0, 1] field on q x q nodes smoothed by `sweeps` Jacobi sweeps.
+
+    One sweep of weighted Jacobi (weight 2/3) for the 5-point Laplacian with zero
+    right-hand side and reflecting edges: U <- U + (2/3) (mean of the 4 neighbours - U).
+    The initial condition of the heat-equation differentiation workload.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shape = (q, q) if batch is None else (batch, q, q)
+    U = rng.uniform(0.0, 1.0, shape)
+    for _ in range(sweeps):
+        P = np.pad(U, [(0, 0)] * (U.ndim - 2) + [(1, 1), (1, 1)], mode="reflect")
+        nb = 0.25 * (P[..., :-2, 1:-1] + P[..., 2:, 1:-1] + P[..., 1:-1, :-2] + P[..., 1:-1, 2:])
+        U = U + (2.0 / 3.0) * (nb - U)
+    return U
+
+
+def heat_config():
+    """Differentiation workload: u_t - d_u Lap u = 0, homogeneous Neumann BC, domain
+    {0 <= x <= 1, 0.1 x^2 <= y <= 1 + 0.2 cos(pi x)}, P2 with 513 nodes per direction,
+    IMEX Euler dt = 1e-3 for 400 steps, d_u = 0.05, checkpoints every 50 steps."""
+    return dict(g1=Profile(c2=0.1), g2=Profile(c0=1.0, ca=0.2, cf=1.0), k=2, n=513, bc="neumann",
+                d_u=0.05, tau=1e-3, steps=400, every=50)

@@ -64,6 +64,9 @@ def _load():
         "mofem_pcg_direction": [vp, vp, vp, P(c_double), P(c_double), vp, vp, c_int, P(c_double), c_int, vp],
         "mofem_pcg_solve": [vp, vp, vp, c_double, c_int, c_int, P(SolveInfo), vp],
         "mofem_imex_step": [vp, c_double, c_double, vp, vp, vp, c_int, P(SolveInfo), vp],
+        "mofem_imex_step_tol": [vp, c_double, c_double, vp, vp, vp, c_double, c_int, P(SolveInfo), vp],
+        "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
+                                    vp],
         "mofem_destroy": [vp],
         "mofem_bench_kernel": [vp, c_int, c_int, c_int, vp],
         "mofem_host_tables": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), P(c_int), P(c_int),
@@ -83,7 +86,7 @@ def _load():
 LIB = _load()
 
 EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply", "mofem_rhs", "mofem_precond",
-            "mofem_pcg_direction",
+            "mofem_pcg_direction", "mofem_imex_step_tol", "mofem_imex_adjoint_step",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
             "mofem_host_tables", "mofem_bench_kernel"]
 
@@ -213,6 +216,24 @@ class Handle:
         if check:
             _check("mofem_imex_step", code)
         return info, code
+
+    def imex_step_tol(self, d_u, tau, Un, Fn, Unp1, rtol, precision="fp16", check=True):
+        info = SolveInfo()
+        code = LIB.mofem_imex_step_tol(self.h, d_u, tau, _ptr(Un), _ptr(Fn), _ptr(Unp1), rtol, PRECISIONS[precision],
+                                       ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_imex_step_tol", code)
+        return info, code
+
+    def imex_adjoint_step(self, d_u, tau, Lam1, U1, Lam0, rtol, precision="fp16", check=True):
+        """Lam0 = M~ S^{-1} Lam1; returns (dJ/dd_u contributions per instance, info, code)."""
+        dd = (ctypes.c_double * self.batch)()
+        info = SolveInfo()
+        code = LIB.mofem_imex_adjoint_step(self.h, d_u, tau, _ptr(Lam1), _ptr(U1), _ptr(Lam0), dd, rtol,
+                                           PRECISIONS[precision], ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_imex_adjoint_step", code)
+        return list(dd), info, code
 
     def bench_kernel(self, kernel, precision="bf16", reps=1):
         """Launch one hot kernel `reps` times on internal buffers (timing hook)."""
