@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-heat", action="store_true", help="skip the differentiation workload (heat IMEX + adjoint)")
+    ap.add_argument("--no-dib", action="store_true", help="skip the reaction-diffusion (DIB) workload")
     ap.add_argument("--host-loop", action="store_true",
                     help="step the inner loop from the host instead of a conditional-node CUDA graph "
                          "(per-kernel profilers cannot see kernels inside conditional graphs)")
@@ -188,6 +189,38 @@ def measure_heat():
             "forward_ms": fwd, "backward_ms": bwd, "forward_steps_per_s": steps / (fwd / 1e3),
             "backward_steps_per_s": steps / (bwd / 1e3), "dJ_ddu": g,
             "check": "gradients vs central differences to 1e-5: tests/test_gpu_heat.py"}
+
+
+def measure_dib(steps=300):
+    """Reaction-diffusion workload: the DIB model (cap parameters), lumped P1, 1025 x 1025
+    nodes, zero Neumann, on 0 <= y <= 1 + 0.25 sin(2 pi x), rho = 1, dt = 1e-2, the two
+    species batched in every IMEX step, the paper's per-step stopping rule; `steps` of the
+    10^4 steps to T = 100 are timed (CUDA events around the library's own time loop)."""
+    import numpy as np
+    import torch
+    import paper_2109_01173_gb300.mofem as mf
+    from paper_2109_01173_gb300.inputs import ZERO, SIN_TOP, dib_params_cap, dib_initial
+    n, tau, rho = 1025, 1e-2, 1.0
+    p = dib_params_cap()
+    h = mf.Handle([ZERO, ZERO], [SIN_TOP, SIN_TOP], 0, n, [1.0 / tau, 1.0 / (p["d_theta"] * tau)], bc=mf.NEUMANN)
+    eq = mf.dib_equilibrium(p)
+    U = torch.tensor(dib_initial(n, eq[0], eq[1], seed=0), device="cuda")
+    h.dib_run(p, rho, tau, 5, U)   # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    info, code, inc = h.dib_run(p, rho, tau, steps, U, increments=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    h.close()
+    return {"workload": f"DIB (cap parameters), lumped P1 {n}x{n} nodes, Neumann, 0<=y<=1+0.25sin(2pi x), "
+                        f"rho {rho:g}, dt {tau:g}, eta and theta batched per step, paper's stopping rule",
+            "steps": steps, "ms": ms, "steps_per_s": steps / (ms / 1e3),
+            "projected_s_to_T100": 1e4 / (steps / (ms / 1e3)),
+            "inner_iterations_per_step": info.iterations / max(steps, 1),
+            "last_increment": inc[-1] if inc else None,
+            "check": "states vs the FP64 oracle at checkpoints: tests/test_gpu_dib.py"}
 
 
 # ----------------------------------------------------------------------------------
@@ -416,6 +449,8 @@ def run_mofem(a):
     }
     if not a.no_heat and rank == 0:
         line["heat_adjoint"] = measure_heat()
+    if not a.no_dib and rank == 0:
+        line["reaction_diffusion"] = measure_dib()
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -65,7 +65,14 @@ typedef enum { MOFEM_BC_DIRICHLET = 0, MOFEM_BC_NEUMANN = 1 } mofem_bc;
 typedef enum { MOFEM_FP64 = 0, MOFEM_MIXED_TF32 = 1, MOFEM_MIXED_BF16 = 2, MOFEM_MIXED_FP16 = 3 } mofem_precision;
 
 /* Second pencil of the two-term Sylvester preconditioner (see mofem_precond). */
-typedef enum { MOFEM_PENCIL_AVERAGED = 0, MOFEM_PENCIL_DOMINANT = 1 } mofem_pencil;
+/* Preconditioner of MO-PCG.  AVERAGED / DOMINANT: the two-term Sylvester
+ * preconditioner E1 Z F1^T + E2 Z F2^T = R (E1 = K_s[h] + gamma M_s[h], F1 = M_t,
+ * F2 = K_t, E2 = M_s[e2] with e2 the t-average of H^_tt or its t-free part).
+ * PRODUCT: the paper's single-term preconditioner of Sec. 5, Eq.
+ * vector_preconditioner, P(Z) = K_s[h] Z (K_t + K_t[t^2])^T (B1 U (A + B2) in the
+ * paper's orientation), Dirichlet only; applied by the same reduced approach with
+ * standard eigenpairs on each side and the divisor lambda_a mu_b. */
+typedef enum { MOFEM_PENCIL_AVERAGED = 0, MOFEM_PENCIL_DOMINANT = 1, MOFEM_PENCIL_PRODUCT = 2 } mofem_pencil;
 
 /* Domain profile y = g(x) on [0, 1]: host callbacks for g and g', called during
  * setup only (at the quadrature points). */
@@ -205,6 +212,45 @@ mofem_status mofem_imex_step_tol(mofem_handle h, double d_u, double tau, const d
 mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, const double* Lam_np1,
                                      const double* U_np1, double* Lam_n, double* dd_u, double rtol,
                                      mofem_precision prec, mofem_solve_info* info, cudaStream_t stream);
+
+/* One IMEX Euler step of a batch of reaction-diffusion species (Sec. 6 applied
+ * to each species of a system such as Sec. 7's): instance i solves
+ *   (M~ + d_i tau A~) U_np1 = M~ (U_n + tau F_n),  d_i = 1/(gamma_i tau),
+ * with gamma_i the handle's value for that instance (so species with different
+ * diffusion coefficients share one batched solve).  Layouts and stopping rule as
+ * mofem_imex_step_tol (rtol = 0: the paper's ||R_s|| <= tau ||R_0||). */
+mofem_status mofem_rds_step(mofem_handle h, double tau, const double* U_n, const double* F_n, double* U_np1,
+                            double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t stream);
+
+/* Parameters of the DIB kinetics (Sec. 7, Eqs. dib_kinetics_f, dib_kinetics_g;
+ * Eq. dib_parameters_mixed and the per-domain A2, B, C of Sec. 7.1-7.2). */
+typedef struct {
+    double alpha, gamma, A1, A2, B, C, D, k2, k3, d_theta;
+} mofem_dib_params;
+
+/* f = rho f(eta, theta), g = rho g(eta, theta) elementwise over `count` FP64
+ * device values (Sec. 7, Eqs. dib_kinetics_f, dib_kinetics_g). */
+mofem_status mofem_dib_kinetics(const mofem_dib_params* p, double rho, const double* eta, const double* theta,
+                                double* f, double* g, long long count, cudaStream_t stream);
+
+/* Homogeneous equilibrium of the DIB kinetics, f(eta, theta) = g(eta, theta) = 0,
+ * by Newton's method from (0, 1/2) on the host.  The paper states (0, 0.5) as the
+ * equilibrium for its printed parameters, which holds only for C = 4; for other C
+ * this returns the actual zero (e.g. (-0.2852, 0.4670) for the cap parameters).
+ * Returns MOFEM_ERR_NONFINITE if Newton breaks down. */
+mofem_status mofem_dib_equilibrium(const mofem_dib_params* p, double* eta, double* theta);
+
+/* n_steps of IMEX Euler for the DIB model (Sec. 7, Eq. dib_model) with zero
+ * Neumann data: reaction explicit (mofem_dib_kinetics), diffusion implicit, both
+ * species in one batched MO-PCG solve per step.  The handle must be a Neumann
+ * handle with batch 2 and gamma = {1/tau, 1/(d_theta tau)} (eta, theta).
+ * U: [eta; theta], q x q each (ld q), FP64 device, in: initial data, out: state
+ * after n_steps.  rtol as mofem_rds_step.  incr: host array of n_steps doubles
+ * receiving ||eta_{k+1} - eta_k||_F (the paper's increment plot), or NULL.
+ * info accumulates iterations over the run.  Synchronises `stream`. */
+mofem_status mofem_dib_run(mofem_handle h, const mofem_dib_params* p, double rho, double tau, int n_steps,
+                           double* U, double rtol, mofem_precision prec, double* incr, mofem_solve_info* info,
+                           cudaStream_t stream);
 
 /* Benchmark hook (no counterpart in the paper): launch one hot kernel `reps`
  * times on the handle's internal buffers, asynchronously on `stream`, so that

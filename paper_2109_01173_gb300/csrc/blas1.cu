@@ -424,11 +424,12 @@ __global__ void k_transpose64(const double* src, long long s_bs, double* dst, lo
 }
 
 __global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const double* lam, long long lam_bs,
-                                 const double* mu) {
+                                 const double* mu, int product) {
     const int inst = blockIdx.z, i = blockIdx.y;
     const double li = lam[(size_t)inst * lam_bs + i];
     double* row = W + (size_t)inst * bs + (size_t)i * ld;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x) row[j] /= (li + mu[j]);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q; j += gridDim.x * blockDim.x)
+        row[j] /= product ? li * mu[j] : li + mu[j];
 }
 
 // U64 += hi + lo at the end of an inner solve of the mixed form (the pair is
@@ -569,9 +570,9 @@ mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, 
 }
 
 mofem_status launch_hadamard_div64(double* W, long long bs, int ld, int q, const double* lam, long long lam_bs,
-                                   const double* mu, int batch, cudaStream_t st) {
+                                   const double* mu, int batch, int product, cudaStream_t st) {
     dim3 grid((q + 255) / 256, q, batch);
-    k_hadamard_div64<<<grid, 256, 0, st>>>(W, bs, ld, q, lam, lam_bs, mu);
+    k_hadamard_div64<<<grid, 256, 0, st>>>(W, bs, ld, q, lam, lam_bs, mu, product);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

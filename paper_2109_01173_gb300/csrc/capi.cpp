@@ -54,6 +54,13 @@ mofem_status mofem_setup_batched(int batch, const mofem_profile* g1, const mofem
         if (bc == MOFEM_BC_NEUMANN && !(gamma[i] > 0.0)) return MOFEM_ERR_INVALID_ARG;   // singular operator
     }
     if (opts && (opts->quad_points < 0 || opts->quad_points > 16)) return MOFEM_ERR_INVALID_ARG;
+    if (opts && (opts->pencil < MOFEM_PENCIL_AVERAGED || opts->pencil > MOFEM_PENCIL_PRODUCT))
+        return MOFEM_ERR_INVALID_ARG;
+    if (opts && opts->pencil == MOFEM_PENCIL_PRODUCT && bc != MOFEM_BC_DIRICHLET) {
+        mofem_set_last_error("product preconditioner: K_s[h] and K_t + K_t[t^2] are singular under Neumann BC",
+                             __FILE__, __LINE__);
+        return MOFEM_ERR_INVALID_ARG;
+    }
     mofem_ctx* c = new (std::nothrow) mofem_ctx();
     if (!c) return MOFEM_ERR_OOM;
     c->batch = batch;
@@ -105,7 +112,8 @@ mofem_status mofem_precond(mofem_handle h, const void* R, void* Z, int ld, mofem
     if (!h || !R || !Z || ld < h->q || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
     const long long bs = (long long)ld * h->q;
     if (prec == MOFEM_FP64) return precond64(h, (const double*)R, bs, ld, (double*)Z, bs, ld, stream);
-    return precond_tc(h, plan_of(prec), (const float*)R, bs, ld, (float*)Z, bs, ld, nullptr, nullptr, stream);
+    const mofem_precision pe = (prec == MOFEM_MIXED_FP16 && h->div_product) ? MOFEM_MIXED_TF32 : prec;
+    return precond_tc(h, plan_of(pe), (const float*)R, bs, ld, (float*)Z, bs, ld, nullptr, nullptr, stream);
 }
 
 mofem_status mofem_pcg_direction(mofem_handle h, const void* Z, const void* Q_prev, const double* beta,
@@ -158,6 +166,45 @@ mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, con
         return MOFEM_ERR_INVALID_ARG;
     if (!imex_gamma_ok(h, d_u, tau)) return MOFEM_ERR_INVALID_ARG;
     return solve_imex_adjoint(h, d_u, tau, Lam_np1, U_np1, Lam_n, dd_u, rtol, prec, info, stream);
+}
+
+mofem_status mofem_rds_step(mofem_handle h, double tau, const double* U_n, const double* F_n, double* U_np1,
+                            double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t stream) {
+    if (!h || !U_n || !F_n || !U_np1 || !(tau > 0.0) || !(rtol >= 0.0) || !valid_precision(prec))
+        return MOFEM_ERR_INVALID_ARG;
+    for (int i = 0; i < h->batch; ++i)
+        if (!(h->gamma[i] > 0.0)) return MOFEM_ERR_INVALID_ARG;
+    return solve_imex(h, 0.0, tau, U_n, F_n, U_np1, rtol, prec, info, stream);
+}
+
+mofem_status mofem_dib_kinetics(const mofem_dib_params* p, double rho, const double* eta, const double* theta,
+                                double* f, double* g, long long count, cudaStream_t stream) {
+    if (!p || !eta || !theta || !f || !g || count < 0 || !std::isfinite(rho)) return MOFEM_ERR_INVALID_ARG;
+    return launch_dib_kinetics(*p, rho, eta, theta, f, g, count, stream);
+}
+
+mofem_status mofem_dib_equilibrium(const mofem_dib_params* p, double* eta, double* theta) {
+    if (!p || !eta || !theta) return MOFEM_ERR_INVALID_ARG;
+    return dib_equilibrium(*p, eta, theta);
+}
+
+mofem_status mofem_dib_run(mofem_handle h, const mofem_dib_params* p, double rho, double tau, int n_steps,
+                           double* U, double rtol, mofem_precision prec, double* incr, mofem_solve_info* info,
+                           cudaStream_t stream) {
+    if (!h || !p || !U || !(tau > 0.0) || n_steps < 0 || !(rtol >= 0.0) || !valid_precision(prec) ||
+        !std::isfinite(rho))
+        return MOFEM_ERR_INVALID_ARG;
+    if (h->batch != 2 || h->q != h->n || !(p->d_theta > 0.0)) {
+        mofem_set_last_error("mofem_dib_run: needs a Neumann handle with two instances (eta, theta)", __FILE__,
+                             __LINE__);
+        return MOFEM_ERR_INVALID_ARG;
+    }
+    const double ge = 1.0 / tau, gt = 1.0 / (p->d_theta * tau);
+    if (std::fabs(h->gamma[0] - ge) > 1e-12 * ge || std::fabs(h->gamma[1] - gt) > 1e-12 * gt) {
+        mofem_set_last_error("mofem_dib_run: handle gamma must be {1/tau, 1/(d_theta tau)}", __FILE__, __LINE__);
+        return MOFEM_ERR_INVALID_ARG;
+    }
+    return dib_run(h, *p, rho, tau, n_steps, U, rtol, prec, incr, info, stream);
 }
 
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps, cudaStream_t stream) {

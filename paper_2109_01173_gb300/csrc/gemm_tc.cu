@@ -48,6 +48,7 @@ struct GemmArgs {
     PcgScalars* sc;       // skip inactive instances; with rz_part, last-CTA beta finalisation
     unsigned* counter;    // [batch] CTA tickets (zeroed, self-resetting)
     int flex;
+    int div_product;       // EPI_DIV divisor lambda_i * mu_j (product preconditioner) instead of lambda_i + mu_j
     const PcgScalars* scl; // FP16 operands: the G4 output is divided by scl[inst].rscale
     int* status;
 };
@@ -167,7 +168,7 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, in
     if (g.epi == EPI_DIV) {
         const float* lam = g.lam + (size_t)inst * g.lam_bs + nb;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], lam[j] + mu_m);
+        for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], g.div_product ? lam[j] * mu_m : lam[j] + mu_m);
     }
     if (g.epi == EPI_Z && g.scl) {
         const float inv = (float)(1.0 / g.scl[inst].rscale);
@@ -674,7 +675,7 @@ mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaS
     GemmArgs g{};
     g.M = q; g.N = q; g.nk = (q + bk - 1) / bk;
     g.status = c->d_status;
-    g.lam = c->lam32; g.lam_bs = ld; g.mu = c->mu32;
+    g.lam = c->lam32; g.lam_bs = ld; g.mu = c->mu32; g.div_product = c->div_product;
     g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = which;
     void* outs[4] = {p.X1T, p.WT, p.Y, Z};
     const int epis[4] = {EPI_STORE, EPI_DIV, EPI_STORE, EPI_Z};
@@ -700,6 +701,7 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
     g.lam = c->lam32;
     g.lam_bs = ld;
     g.mu = c->mu32;
+    g.div_product = c->div_product;
     g.out_bs = (long long)q * ld;
     g.out_ld = ld;
     g.out_bf16 = which;
@@ -742,7 +744,7 @@ mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z
     GemmArgs g{};
     g.M = q; g.N = q; g.nk = (q + 63) / 64;
     g.status = c->d_status;
-    g.lam = c->lam32; g.lam_bs = c->ld; g.mu = c->mu32;
+    g.lam = c->lam32; g.lam_bs = c->ld; g.mu = c->mu32; g.div_product = c->div_product;
     g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = 1;
     g.out = b.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
     MOFEM_TRY(launch_gemm<1>(mA[0], mB[0], g, B, st));

@@ -60,6 +60,7 @@ struct mofem_ctx {
     mofem_bc bc = MOFEM_BC_DIRICHLET;
     mofem_opts opts{};
     int ld = 0;                  // leading dimension of internal q x q matrices (multiple of 64)
+    int div_product = 0;         // preconditioner divisor: lambda_a * mu_b (product form) instead of lambda_a + mu_b
     int off = 1;                 // node index of trimmed row 0 (1 Dirichlet, 0 Neumann)
     std::vector<double> gamma;   // per instance
     int dev = 0;
@@ -188,7 +189,7 @@ mofem_status launch_transpose64(const double* src, long long s_bs, double* dst, 
 mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs,
                                    int d_ld, int n, int batch, cudaStream_t st);
 mofem_status launch_hadamard_div64(double* W, long long bs, int ld, int q, const double* lam,
-                                   long long lam_bs, const double* mu, int batch, cudaStream_t st);
+                                   long long lam_bs, const double* mu, int batch, int product, cudaStream_t st);
 mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const float* dU, long long d_bs,
                                 int d_ld, int q, int batch, cudaStream_t st);
 
@@ -221,6 +222,11 @@ mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rto
                             mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
 mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
                         double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
+mofem_status dib_run(mofem_ctx* c, const mofem_dib_params& p, double rho, double tau, int n_steps, double* U,
+                     double rtol, mofem_precision prec, double* incr, mofem_solve_info* info, cudaStream_t st);
+mofem_status dib_equilibrium(const mofem_dib_params& p, double* eta, double* theta);
+mofem_status launch_dib_kinetics(const mofem_dib_params& p, double rho, const double* eta, const double* theta,
+                                 double* f, double* g, long long n, cudaStream_t st);
 mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const double* Lam1, const double* U1,
                                 double* Lam0, double* dd, double rtol, mofem_precision prec, mofem_solve_info* info,
                                 cudaStream_t st);

@@ -194,7 +194,15 @@ struct HostTables {
     std::vector<double> S, T, Srh, Trh;   // [B][NT][P][q], [NT][P][q], [B][P][q], [P][q]
     std::vector<Band> E1s, E2s;
     Band Mt, Kt;
+    Band F1, F2;                          // t-pencil F2 Q2 = F1 Q2 diag(mu)
 };
+
+// Identity as a band of half-width K.
+static Band identity_band(int n, int K) {
+    Band I(n, K);
+    for (int r = 0; r < n; ++r) I.at(r, r) = 1.0;
+    return I;
+}
 
 static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mofem_opts& opts,
                                       const mofem_profile* g1, const mofem_profile* g2, const double* gamma,
@@ -255,6 +263,9 @@ static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mo
     Band Ctt = assemble(Qd, n, KIND_G, tw);
     H.Mt = Mt;
     H.Kt = Kt;
+    const bool product = opts.pencil == MOFEM_PENCIL_PRODUCT;
+    H.F1 = product ? identity_band(n, Mt.K) : Mt;
+    H.F2 = product ? add(Kt, Ktt2, 1.0) : Kt;
 
     std::vector<double>& Th = H.T;
     Th.assign((size_t)NT * P * q, 0.0);
@@ -313,8 +324,13 @@ static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mo
             trimmed_table(Gdh, q, off, lo, hi, true, -1.0, sslot(7));
         }
         trimmed_table(Msh, q, off, 0, n - 1, false, 1.0, H.Srh.data() + (size_t)i * P * q);
-        H.E1s[i] = S0;
-        H.E2s[i] = (opts.pencil == MOFEM_PENCIL_DOMINANT) ? Msa : assemble(Qd, n, KIND_M, we2[i]);
+        if (product) {   // K_s[h] Z (K_t + K_t[t^2])^T: standard eigenpairs on each side
+            H.E1s[i] = Ksh;
+            H.E2s[i] = identity_band(n, Ksh.K);
+        } else {
+            H.E1s[i] = S0;
+            H.E2s[i] = (opts.pencil == MOFEM_PENCIL_DOMINANT) ? Msa : assemble(Qd, n, KIND_M, we2[i]);
+        }
     }
     return MOFEM_OK;
 }
@@ -454,8 +470,9 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
             MOFEM_CUDA_TRY(cudaMemcpyAsync(lamout, dW, sizeof(double) * q, cudaMemcpyDeviceToDevice, st));
             return MOFEM_OK;
         };
-        // t-pencil (shared): K_t x = mu M_t x
-        if ((result = solve_pencil(Kt, Mt, c->Q2_64, c->mu64)) != MOFEM_OK) break;
+        // t-pencil (shared): K_t x = mu M_t x (product form: (K_t + K_t[t^2]) x = mu x)
+        if ((result = solve_pencil(H.F2, H.F1, c->Q2_64, c->mu64)) != MOFEM_OK) break;
+        c->div_product = c->opts.pencil == MOFEM_PENCIL_PRODUCT ? 1 : 0;
         for (int i = 0; i < B && result == MOFEM_OK; ++i)
             result = solve_pencil(E1s[i], E2s[i], c->Q1_64 + (size_t)i * q * ld, c->lam64 + (size_t)i * ld);
         if (result != MOFEM_OK) break;

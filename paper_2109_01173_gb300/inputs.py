@@ -167,3 +167,16 @@ def heat_config():
     IMEX Euler dt = 1e-3 for 400 steps, d_u = 0.05, checkpoints every 50 steps."""
     return dict(g1=Profile(c2=0.1), g2=Profile(c0=1.0, ca=0.2, cf=1.0), k=2, n=513, bc="neumann",
                 d_u=0.05, tau=1e-3, steps=400, every=50)
+
+
+def dib_params_cap():
+    """DIB kinetics parameters: Eq. dib_parameters_mixed with the cap-domain A2, B, C (Sec. 7.1)."""
+    return dict(alpha=0.5, gamma=0.2, A1=10.0, A2=30.0, B=25.0, C=7.0, D=3.2727, k2=2.5, k3=1.5, d_theta=20.0)
+
+
+def dib_initial(n, eta_e, theta_e, seed=0, amplitude=1e-3):
+    """[eta0; theta0] on n x n nodes: the given homogeneous state plus a seeded uniform
+    perturbation in [-amplitude, amplitude] (initial data of the reaction-diffusion runs)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.stack([eta_e + rng.uniform(-amplitude, amplitude, (n, n)),
+                     theta_e + rng.uniform(-amplitude, amplitude, (n, n))])

@@ -17,7 +17,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_EIG, ERR_NONFINITE, ERR_BREAKDOWN, ERR_NOT_CO
     ERR_OOM, ERR_UNSUPPORTED = range(10)
 DIRICHLET, NEUMANN = 0, 1
 FP64, MIXED_TF32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
-PENCIL_AVERAGED, PENCIL_DOMINANT = 0, 1
+PENCIL_AVERAGED, PENCIL_DOMINANT, PENCIL_PRODUCT = 0, 1, 2
 FLAG_HOST_LOOP, FLAG_FIXED_ITERS = 1, 2
 
 PRECISIONS = {"fp64": FP64, "tf32": MIXED_TF32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
@@ -48,6 +48,15 @@ class MofemError(RuntimeError):
         self.code = code
 
 
+class DibParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("alpha", "gamma", "A1", "A2", "B", "C", "D", "k2", "k3", "d_theta")]
+
+
+def dib_params(d):
+    """mofem_dib_params from a dict with the keys of DibParams."""
+    return DibParams(*[float(d[n]) for n, _ in DibParams._fields_])
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libmofem.so not built ({LIB_PATH}); run paper_2109_01173_gb300.build.build()")
@@ -65,6 +74,11 @@ def _load():
         "mofem_pcg_solve": [vp, vp, vp, c_double, c_int, c_int, P(SolveInfo), vp],
         "mofem_imex_step": [vp, c_double, c_double, vp, vp, vp, c_int, P(SolveInfo), vp],
         "mofem_imex_step_tol": [vp, c_double, c_double, vp, vp, vp, c_double, c_int, P(SolveInfo), vp],
+        "mofem_rds_step": [vp, c_double, vp, vp, vp, c_double, c_int, P(SolveInfo), vp],
+        "mofem_dib_kinetics": [P(DibParams), c_double, vp, vp, vp, vp, ctypes.c_longlong, vp],
+        "mofem_dib_equilibrium": [P(DibParams), P(c_double), P(c_double)],
+        "mofem_dib_run": [vp, P(DibParams), c_double, c_double, c_int, vp, c_double, c_int, P(c_double),
+                          P(SolveInfo), vp],
         "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
                                     vp],
         "mofem_destroy": [vp],
@@ -86,7 +100,8 @@ def _load():
 LIB = _load()
 
 EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply", "mofem_rhs", "mofem_precond",
-            "mofem_pcg_direction", "mofem_imex_step_tol", "mofem_imex_adjoint_step",
+            "mofem_pcg_direction", "mofem_imex_step_tol", "mofem_imex_adjoint_step", "mofem_rds_step",
+            "mofem_dib_kinetics", "mofem_dib_run", "mofem_dib_equilibrium",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
             "mofem_host_tables", "mofem_bench_kernel"]
 
@@ -235,6 +250,25 @@ class Handle:
             _check("mofem_imex_adjoint_step", code)
         return list(dd), info, code
 
+    def rds_step(self, tau, Un, Fn, Unp1, rtol=0.0, precision="fp16", check=True):
+        info = SolveInfo()
+        code = LIB.mofem_rds_step(self.h, tau, _ptr(Un), _ptr(Fn), _ptr(Unp1), rtol, PRECISIONS[precision],
+                                  ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_rds_step", code)
+        return info, code
+
+    def dib_run(self, params, rho, tau, n_steps, U, rtol=0.0, precision="fp16", increments=False, check=True):
+        """n_steps of the DIB model on U = [eta; theta] in place; returns (info, code, increments or None)."""
+        info = SolveInfo()
+        inc = (ctypes.c_double * max(n_steps, 1))() if increments else None
+        p = dib_params(params)
+        code = LIB.mofem_dib_run(self.h, ctypes.byref(p), rho, tau, n_steps, _ptr(U), rtol, PRECISIONS[precision],
+                                 inc, ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_dib_run", code)
+        return info, code, (list(inc)[:n_steps] if increments else None)
+
     def bench_kernel(self, kernel, precision="bf16", reps=1):
         """Launch one hot kernel `reps` times on internal buffers (timing hook)."""
         _check("mofem_bench_kernel", LIB.mofem_bench_kernel(self.h, kernel, PRECISIONS[precision], reps, _stream()))
@@ -249,3 +283,18 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+def dib_kinetics(params, rho, eta, theta, f, g):
+    """f = rho f(eta, theta), g = rho g(eta, theta) elementwise on device tensors."""
+    p = dib_params(params)
+    _check("mofem_dib_kinetics", LIB.mofem_dib_kinetics(ctypes.byref(p), rho, _ptr(eta), _ptr(theta), _ptr(f),
+                                                         _ptr(g), eta.numel(), _stream()))
+
+
+def dib_equilibrium(params):
+    """(eta_e, theta_e): zero of the DIB kinetics (host Newton in libmofem)."""
+    p = dib_params(params)
+    e, t = ctypes.c_double(), ctypes.c_double()
+    _check("mofem_dib_equilibrium", LIB.mofem_dib_equilibrium(ctypes.byref(p), ctypes.byref(e), ctypes.byref(t)))
+    return e.value, t.value

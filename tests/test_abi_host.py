@@ -67,6 +67,9 @@ def test_invalid_arguments_rejected_without_gpu(mofem):
     assert L.mofem_imex_step(None, 1.0, 1.0, None, None, None, 0, None, None) == 1
     assert L.mofem_imex_step_tol(None, 1.0, 1.0, None, None, None, 1e-10, 0, None, None) == 1
     assert L.mofem_imex_adjoint_step(None, 1.0, 1.0, None, None, None, None, 1e-10, 0, None, None) == 1
+    assert L.mofem_rds_step(None, 1.0, None, None, None, 0.0, 0, None, None) == 1
+    assert L.mofem_dib_kinetics(None, 1.0, None, None, None, None, 0, None) == 1
+    assert L.mofem_dib_run(None, None, 1.0, 1.0, 1, None, 0.0, 0, None, None, None) == 1
     assert L.mofem_destroy(None) == 1
 
 
@@ -110,3 +113,15 @@ def test_host_tables_match_oracle(mofem, k, bc, dom):
     off = 1 if bc == "dirichlet" else 0
     assert np.abs(band_to_dense(t["Srh"], q, K, n, off) - Ms.toarray()).max() <= 1e-14 * n
     assert np.abs(band_to_dense(t["Trh"], q, K, n, off) - Mt.toarray()).max() <= 1e-14 * n
+
+
+def test_dib_equilibrium_matches_oracle(mofem):
+    """Host Newton of the library vs the oracle's (cap and jar parameters; C = 4 gives (0, 1/2))."""
+    from oracle import dib
+    for p in (dib.CAP, dib.JAR, dict(dib.CAP, C=4.0)):
+        e, t = mofem.dib_equilibrium(p)
+        eo, to = dib.equilibrium(p)
+        assert abs(e - eo) <= 1e-13 and abs(t - to) <= 1e-13
+    # D = 3.2727 is printed to 4 decimals: g(0, 1/2) = 1.5e-5, so the zero moves by O(1e-5 / |J|)
+    e, t = mofem.dib_equilibrium(dict(dib.CAP, C=4.0))
+    assert abs(e) <= 1e-4 and abs(t - 0.5) <= 1e-4

@@ -1,0 +1,114 @@
+"""GPU parity of the DIB reaction-diffusion run (Sec. 7) against the FP64 oracle.
+
+* Kinetics kernel = the oracle's f, g elementwise.
+* Homogeneous equilibrium is a fixed point of the GPU time loop (paper's stopping rule).
+* Coupled IMEX Euler (lumped P1, zero Neumann, rho = 1, tau = 1e-2, equilibrium +
+  seeded uniform +-1e-3 perturbation), both species batched per step: states at
+  checkpoints and the increment ||eta_{k+1} - eta_k||_F against the oracle's sparse
+  direct solves, on the unit square and on 0 <= y <= 1 + 0.25 sin(2 pi x).
+  Tight solves (rtol 1e-11): relative error <= 1e-8.  The paper's stopping rule
+  (||R_s|| <= tau ||R_0||): the deviation from the direct solves is reported
+  (it is the method's, not rounding) and bounded loosely.
+"""
+import numpy as np
+import pytest
+
+from oracle import dib
+from oracle.heat import HeatOperators
+from paper_2109_01173_gb300.inputs import Profile, ZERO, SIN_TOP
+
+pytestmark = pytest.mark.gpu
+
+ONE = Profile(c0=1.0)
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    torch.cuda.set_device(0)
+    import paper_2109_01173_gb300.mofem as mf
+    return torch, mf
+
+
+def _initial(q, p, seed):
+    e, t = dib.equilibrium(p)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eta0 = e + rng.uniform(-1e-3, 1e-3, (q, q))
+    theta0 = t + rng.uniform(-1e-3, 1e-3, (q, q))
+    return eta0, theta0
+
+
+def _handle(mf, g2, n, tau, p):
+    return mf.Handle([ZERO, ZERO], [g2, g2], 0, n, [1.0 / tau, 1.0 / (p["d_theta"] * tau)], bc=mf.NEUMANN)
+
+
+def test_kinetics_kernel_vs_oracle(mods):
+    torch, mf = mods
+    rng = np.random.default_rng(3)
+    e = rng.uniform(-1, 1, 100003)
+    t = rng.uniform(0, 1, 100003)
+    for p in (dib.CAP, dib.JAR):
+        E, T = torch.tensor(e, device="cuda"), torch.tensor(t, device="cuda")
+        F, G = torch.empty_like(E), torch.empty_like(E)
+        mf.dib_kinetics(p, 2.5, E, T, F, G)
+        fo, go = 2.5 * dib.f(e, t, p), 2.5 * dib.g(e, t, p)
+        assert np.abs(F.cpu().numpy() - fo).max() <= 1e-13 * 2.5 * (p["A1"] + p["A2"] + p["B"])
+        assert np.abs(G.cpu().numpy() - go).max() <= 1e-13 * 2.5 * 10 * (p["C"] + p["D"])
+
+
+def test_equilibrium_is_a_fixed_point(mods):
+    torch, mf = mods
+    p, tau, n = dib.CAP, 1e-2, 33
+    h = _handle(mf, SIN_TOP, n, tau, p)
+    e, t = dib.equilibrium(p)
+    U = torch.empty((2, n, n), dtype=torch.float64, device="cuda")
+    U[0], U[1] = e, t
+    info, code, inc = h.dib_run(p, 1.0, tau, 10, U, rtol=0.0, increments=True)
+    assert code == 0
+    # the steady state's FP64 residual is rounding noise (~1e-12 of ||B||): each step either
+    # meets the rule at once or stops when refinement no longer reduces it
+    assert abs(U[0] - e).max().item() <= 1e-10 and abs(U[1] - t).max().item() <= 1e-10
+    assert max(inc) <= 1e-8
+    h.close()
+
+
+@pytest.mark.parametrize("g2,prec", [(ONE, "fp16"), (SIN_TOP, "bf16"), (SIN_TOP, "fp64")])
+def test_dib_run_vs_oracle(mods, g2, prec):
+    torch, mf = mods
+    p, tau, rho, n, steps = dib.CAP, 1e-2, 1.0, 33, 40
+    ops = HeatOperators(ZERO, g2, 0, n, "neumann")
+    eta0, theta0 = _initial(n, p, 11)
+    _, _, rec = dib.imex(ops, p, rho, tau, eta0, theta0, steps, record_every=20)
+    h = _handle(mf, g2, n, tau, p)
+    U = torch.tensor(np.stack([eta0, theta0]), device="cuda")
+    for (k, eo, to) in rec:
+        info, code, inc = h.dib_run(p, rho, tau, 20, U, rtol=1e-11, precision=prec, increments=True)
+        assert code == 0
+        eg, tg = U[0].cpu().numpy(), U[1].cpu().numpy()
+        assert np.linalg.norm(eg - eo) <= 1e-8 * np.linalg.norm(eo), k
+        assert np.linalg.norm(tg - to) <= 1e-8 * np.linalg.norm(to), k
+    # increment of the last step against the oracle's last two states
+    _, _, rec2 = dib.imex(ops, p, rho, tau, eta0, theta0, steps, record_every=1)
+    ref_inc = np.linalg.norm(rec2[-1][1] - rec2[-2][1])
+    assert abs(inc[-1] - ref_inc) <= 1e-6 * ref_inc
+    h.close()
+
+
+def test_dib_paper_stopping_rule_deviation(mods):
+    """With the paper's rule the per-step solve is loose; the run stays close to the
+    direct-solve trajectory (deviation reported in the assertion message)."""
+    torch, mf = mods
+    p, tau, rho, n, steps = dib.CAP, 1e-2, 1.0, 129, 100
+    ops = HeatOperators(ZERO, SIN_TOP, 0, n, "neumann")
+    eta0, theta0 = _initial(n, p, 12)
+    eo, to, _ = dib.imex(ops, p, rho, tau, eta0, theta0, steps)
+    h = _handle(mf, SIN_TOP, n, tau, p)
+    U = torch.tensor(np.stack([eta0, theta0]), device="cuda")
+    info, code, _ = h.dib_run(p, rho, tau, steps, U, rtol=0.0)
+    assert code == 0
+    e = np.linalg.norm(U[0].cpu().numpy() - eo) / np.linalg.norm(eo)
+    t = np.linalg.norm(U[1].cpu().numpy() - to) / np.linalg.norm(to)
+    assert e <= 1e-3 and t <= 1e-3, (e, t)
+    h.close()

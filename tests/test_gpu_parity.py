@@ -399,3 +399,46 @@ def test_full_size_direction_batched(mf):
         assert abs(rz[i] / alpha[i] - qlq) <= 64 * U32 * float(np.sum(np.abs(Qg * LQg))), i
         assert torch.all(Qt[i, :, q:] == 0) and torch.all(LQt[i, :, q:] == 0)
     h.close()
+
+
+# ---- the paper's single-term product preconditioner (Sec. 5, Eq. vector_preconditioner) ----------
+@pytest.mark.parametrize("k,n,dname", [(2, 65, "one"), (1, 97, "two"), (0, 64, "one"), (4, 81, "two")])
+def test_product_preconditioner_parity(mf, k, n, dname):
+    """Z = K_s[h]^-1 R (K_t + K_t[t^2])^-T by the reduced approach (standard eigenpairs,
+    divisor lambda mu) against the oracle's banded direct solves."""
+    torch = torch_()
+    g1, g2 = dom(dname)
+    P = Problem(g1, g2, k, n, 0.7)
+    h = mf.Handle(g1, g2, k, n, 0.7, opts=mf.make_opts(pencil=mf.PENCIL_PRODUCT))
+    R = np.random.default_rng(4).standard_normal((h.q, h.q))
+    Zo = pcg.ProductPreconditioner(*P.product_factors())(R)
+    Zt = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    h.precond(torch.tensor(R, device="cuda"), Zt, "fp64")
+    assert np.linalg.norm(Zt.cpu().numpy() - Zo) <= 1e-9 * np.linalg.norm(Zo)
+    for prec, tol in (("tf32", 2e-2), ("bf16", 3e-2), ("fp16", 2e-2)):   # fp16 runs as TF32 for this form
+        Zf = torch.zeros((h.q, h.q), dtype=torch.float32, device="cuda")
+        h.precond(torch.tensor(R, dtype=torch.float32, device="cuda"), Zf, prec)
+        Zm = Zf.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(Zm - Zo) <= tol * np.linalg.norm(Zo), prec
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "fp16"])
+def test_product_preconditioner_solve(mf, prec):
+    """MO-PCG with the product preconditioner: the solution of the oracle and, in the FP64
+    form, the oracle's iteration count (same recurrences and stopping rule; the GPU form may add a
+    residual-replacement restart) within two."""
+    torch = torch_()
+    k, n = 2, 65
+    P = Problem(ZERO, SIN_TOP, k, n, 1.0)
+    F = fourier_f(ZERO, SIN_TOP, n, 0)
+    Uo, info_o = pcg.solve(P, F, precond='product', rtol=1e-13)
+    _, info_10 = pcg.solve(P, F, precond='product', rtol=1e-10)
+    h = mf.Handle(ZERO, SIN_TOP, k, n, 1.0, opts=mf.make_opts(pencil=mf.PENCIL_PRODUCT))
+    U = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(torch.tensor(F, device="cuda"), U, rtol=1e-10, max_iter=2000, precision=prec)
+    assert code == 0
+    assert np.linalg.norm(U.cpu().numpy() - Uo) <= 1e-8 * np.linalg.norm(Uo)
+    if prec == "fp64":
+        assert abs(info.iterations - info_10["iterations"]) <= 2, (info.iterations, info_10["iterations"])
+    h.close()
