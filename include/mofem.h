@@ -252,13 +252,57 @@ mofem_status mofem_dib_run(mofem_handle h, const mofem_dib_params* p, double rho
                            double* U, double rtol, mofem_precision prec, double* incr, mofem_solve_info* info,
                            cudaStream_t stream);
 
+/* ---- heterogeneous batches ------------------------------------------------
+ * Many independent elliptic problems of different (k, n, bc, profiles, gamma)
+ * solved together: problems of equal (k, n, bc) form one batched handle (as
+ * mofem_setup_batched); the groups are solved concurrently, one CUDA stream each,
+ * from host threads.  No counterpart in the paper (it solves one problem at a
+ * time); the arithmetic per problem is that of mofem_pcg_solve. */
+typedef struct {
+    mofem_profile g1, g2;   /* host callbacks, used during setup only */
+    int k, n_nodes;
+    double gamma;
+    mofem_bc bc;
+} mofem_problem;
+
+typedef struct mofem_group_ctx* mofem_group;
+
+/* Grouping of `count` problems without touching the GPU: *n_groups receives the
+ * number of (k, n, bc) groups, group_of[i] (may be NULL) the group of problem i;
+ * groups are ordered by decreasing work (n^3 times size). */
+mofem_status mofem_group_layout(int count, const mofem_problem* problems, int* n_groups, int* group_of);
+
+/* Set up every group (validation and errors as mofem_setup_batched). */
+mofem_status mofem_group_setup(int count, const mofem_problem* problems, const mofem_opts* opts,
+                               mofem_group* out);
+
+/* Solve all problems: F[i] nodal n_i x n_i, U[i] q_i x q_i (in: initial guess,
+ * out: solution), FP64 device pointers, as mofem_pcg_solve.  infos (may be NULL):
+ * `count` records, each the info of the problem's group.  Work starts after prior
+ * work on `stream`; returns when all groups are done.  Returns the first error
+ * other than MOFEM_ERR_NOT_CONVERGED, else that, else MOFEM_OK. */
+mofem_status mofem_group_solve(mofem_group g, const double* const* F, double* const* U, double rtol,
+                               int max_iter, mofem_precision prec, mofem_solve_info* infos, cudaStream_t stream);
+
+/* Run-time tuning of the number of groups solved at once: one warm-up solve, then
+ * one timed solve per candidate (1, 2, 4, 8, 16 groups, all), each from the
+ * caller's initial guesses; the fastest is kept for later solves and written to
+ * *chosen (may be NULL).  U holds the caller's initial guesses again on return. */
+mofem_status mofem_group_autotune(mofem_group g, const double* const* F, double* const* U, double rtol,
+                                  int max_iter, mofem_precision prec, int* chosen);
+
+mofem_status mofem_group_destroy(mofem_group g);
+
 /* Benchmark hook (no counterpart in the paper): launch one hot kernel `reps`
  * times on the handle's internal buffers, asynchronously on `stream`, so that
  * a caller can time it with events on that stream.  kernel:
  *   0 = FP32 operator apply with the fused search-direction update (PCG form),
  *   1..4 = preconditioner GEMM G1..G4 (prec MIXED_TF32, MIXED_BF16 or MIXED_FP16),
- *   5 = FP32 PCG update (alpha, U, R, BF16 copy of R, partial sums),
- *   6 = FP64 operator apply (true residual form).
+ *   5 = FP32 PCG update of an even iteration (R, FP16 copy of R, partial sums;
+ *       the correction term alpha Q is deferred),
+ *   6 = FP64 operator apply (true residual form),
+ *   7 = FP32 PCG update of an odd iteration (R, FP16 copy, and the correction
+ *       U += alpha_prev Q_prev + alpha Q in double-float).
  * The buffers' contents are whatever the last solve left (timing only). */
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps,
                                 cudaStream_t stream);

@@ -78,18 +78,17 @@ mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, c
 bool apply_pcg_packed(int K, int nt, bool fp64) { return !fp64 && packed_apply_ok(K, nt); }
 
 template <int K>
-static int geo2_rows(int nt, bool box) {
-    if (nt == 5) return box ? Geo2<K, 5>::CH : Geo2<K, 5>::TA;
-    return box ? Geo2<K, 8>::CH : Geo2<K, 8>::TA;
+static int geo2_rows(int nt) {
+    return nt == 5 ? Geo2<K, 5>::TA : Geo2<K, 8>::TA;
 }
 
 int apply_pcg_rows_per_cta(int K, int nt, bool fp64) {
     if (apply_pcg_packed(K, nt, fp64)) {
         switch (K) {
-            case 1: return geo2_rows<1>(nt, false);
-            case 2: return geo2_rows<2>(nt, false);
-            case 3: return geo2_rows<3>(nt, false);
-            default: return geo2_rows<4>(nt, false);
+            case 1: return geo2_rows<1>(nt);
+            case 2: return geo2_rows<2>(nt);
+            case 3: return geo2_rows<3>(nt);
+            default: return geo2_rows<4>(nt);
         }
     }
     switch (K) {
@@ -101,8 +100,7 @@ int apply_pcg_rows_per_cta(int K, int nt, bool fp64) {
 }
 
 int apply_pcg_box_rows(int K, int nt, bool fp64) {
-    if (apply_pcg_packed(K, nt, fp64)) return 4;
-    return apply_pcg_rows_per_cta(K, nt, fp64) + 2 * K;
+    return apply_pcg_rows_per_cta(K, nt, fp64) + 2 * K;   // the tile and its K-row halo, one box
 }
 
 // 2 * SR2 of Geo2: the duplicated S row, an even number of float2 (16-byte rows)

@@ -9,16 +9,20 @@
 //   * the CTA is 128 columns x TA rows, 128 threads = 64 column pairs x 2 row
 //     groups; each group streams down its own TA/2 output rows with a register
 //     ring of the last 2K+1 t-pass rows (compile-time slots after unrolling);
-//   * Z and Q_prev arrive by TMA in 4-row chunks, one mbarrier per chunk, so the
-//     t-pass starts on the first rows while the rest are in flight; the search
-//     direction X = Z + beta Q_prev is formed on the fly from both staged tiles
-//     and the owned rows of the new direction are written from registers;
+//   * Z and Q_prev arrive by TMA as one box each (the tile with its K-row halo)
+//     together with the tile's S rows, all on one mbarrier waited once (a
+//     per-row wait on 4-row chunks measured 4% slower: overlap between the 3
+//     resident CTAs of an SM hides the load better than overlap within one); the
+//     search direction X = Z + beta Q_prev is formed on the fly from both staged
+//     tiles and the owned rows of the new direction are written from registers;
 //   * the s-pass coefficients arrive by TMA as well, from a copy of the S tables
 //     laid out per row with every coefficient duplicated into both lanes of a
 //     float2, so a shared-memory broadcast feeds a paired FMA directly.
 //
-// Fused epilogue: per-CTA FP64 partial of <X, L(X)> and, in the last CTA of
-// each instance, alpha = <R, Z> / <Q, L(Q)> (fixed-order sum of the partials).
+// Fused epilogue: per-CTA FP64 partials of <X, L(X)> and <L(X), Z> and, in the
+// last CTA of each instance, alpha = <R, Z> / <Q, L(Q)> and the flexible-beta
+// numerator term <R_new, Z> = <R, Z> - alpha <L(Q), Z> (fixed-order sums of the
+// partials), so the residual update never reads Z again.
 #pragma once
 #include "apply_impl.cuh"
 
@@ -41,9 +45,7 @@ struct Geo2 {
     static constexpr int TAG = MRG * P;                  // output rows per group
     static constexpr int TA = RG * TAG;                  // output rows per CTA
     static constexpr int HR = TA + 2 * K;                // staged rows
-    static constexpr int CH = 4;                         // rows per TMA chunk (4 x 544 B: 128-byte multiple)
-    static constexpr int NCH = (HR + CH - 1) / CH;       // chunks (one mbarrier each)
-    static constexpr int ROWS = NCH * CH;                // staged rows incl. the last chunk's tail
+    static constexpr int ROWS = (HR + 3) / 4 * 4;        // staging rows (4 x 544 B: 128-byte multiple)
     static constexpr int ZBUF = ROWS * WCT;              // floats per staging buffer
     static constexpr int SR2 = ((NT * P + 1) / 2) * 2;   // float2 per duplicated S row (16-byte rows)
     static constexpr bool TREG = NT * P <= 25;           // T coefficients in registers, else shared
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     k_apply_pcg2(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mQ,
                  const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a) {
     using G = Geo2<K, NT>;
-    constexpr int P = G::P, TAG = G::TAG, TA = G::TA, NCH = G::NCH, CH = G::CH, SR2 = G::SR2, KE = G::KE;
+    constexpr int P = G::P, TAG = G::TAG, TA = G::TA, HR = G::HR, SR2 = G::SR2, KE = G::KE;
     constexpr int NPAIR = G::NPAIR, MRG = G::MRG;
     constexpr unsigned DM = DiffMask<NT>::value;
     extern __shared__ unsigned char smem_raw[];
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     float* Qs = Zs + G::ZBUF;                                   // [ROWS][WCT]
     float2* S2s = reinterpret_cast<float2*>(Qs + G::ZBUF);      // [TA][SR2]
     float2* T2s = S2s + TA * SR2;                               // [NT*P][NPAIR] (!TREG)
-    __shared__ __align__(8) unsigned long long bars[NCH];
+    __shared__ __align__(8) unsigned long long bar;
     __shared__ double red[G::NTH / 32];
     __shared__ float beta_s;
     __shared__ int fail_s, last_s;
@@ -85,11 +87,9 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     PcgScalars* sc = a.sc + inst;
     if (a.use_sc && !sc->active) return;
     const int a0 = blockIdx.y * TA, b0 = blockIdx.x * TB;
-    const uint32_t bar0 = smem_u32(&bars[0]);
+    const uint32_t bar0 = smem_u32(&bar);
     if (tid == 0) {
-#pragma unroll 1
-        for (int c = 0; c < NCH; ++c)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * c) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail_s = 0;
         beta_s = (a.use_sc && sc->iters > 0) ? (float)sc->beta : 0.f;
@@ -98,27 +98,21 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     if (tid == 0) {
         const uint64_t pz = reinterpret_cast<uint64_t>(&mZ), pq = reinterpret_cast<uint64_t>(&mQ),
                        ps = reinterpret_cast<uint64_t>(&mS);
-        const int x0 = b0 - XPAD;
-#pragma unroll 1
-        for (int c = 0; c < NCH; ++c) {
-            const uint32_t bar = bar0 + 8u * c;
-            const uint32_t bytes = 2u * CH * WCT * 4u + (c == 0 ? (uint32_t)(TA * SR2 * 8) : 0u);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-            if (c == 0)
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-                    ::"r"(smem_u32(S2s)), "l"(ps), "r"(bar), "r"(0), "r"(a0), "r"(inst)
-                    : "memory");
-            const int y0 = a0 - K + c * CH;
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-                ::"r"(smem_u32(Zs + c * CH * WCT)), "l"(pz), "r"(bar), "r"(x0), "r"(y0), "r"(inst)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-                ::"r"(smem_u32(Qs + c * CH * WCT)), "l"(pq), "r"(bar), "r"(x0), "r"(y0), "r"(inst)
-                : "memory");
-        }
+        const int x0 = b0 - XPAD, y0 = a0 - K;
+        const uint32_t bytes = 2u * HR * WCT * 4u + (uint32_t)(TA * SR2 * 8);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar0), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+            ::"r"(smem_u32(S2s)), "l"(ps), "r"(bar0), "r"(0), "r"(a0), "r"(inst)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+            ::"r"(smem_u32(Zs)), "l"(pz), "r"(bar0), "r"(x0), "r"(y0), "r"(inst)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+            ::"r"(smem_u32(Qs)), "l"(pq), "r"(bar0), "r"(x0), "r"(y0), "r"(inst)
+            : "memory");
     }
     const int cp = tid % NPAIR, grp = tid / NPAIR;
     const int b = b0 + 2 * cp;
@@ -160,16 +154,10 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     float* LQ = reinterpret_cast<float*>(a.LQ) + (size_t)inst * a.bs;
     const bool col_ok = b < a.ld;   // pad columns [q, ld) receive zeros
     const int lr0 = grp * TAG;      // first staged row of this group's window
-    // chunk 0 also carries the S rows, which both groups read: every thread waits for it
-    bool failed = !mbar_wait_bounded(bar0, 0);
-    int ready = CH;                 // staged rows below this are known to have landed
+    const bool failed = !mbar_wait_bounded(bar0, 0);   // the whole tile, its halo and the S rows
     float2 ring[NT][P];
     float2 xr0[P];
     auto tpass = [&](int lr, int slot) {
-        if (lr >= ready) {
-            if (!mbar_wait_bounded(bar0 + 8u * (uint32_t)(lr / CH), 0)) failed = true;
-            ready = (lr / CH + 1) * CH;
-        }
         const float2* z2 = reinterpret_cast<const float2*>(Zs + lr * WCT + XPAD + 2 * cp - KE);
         const float2* q2 = reinterpret_cast<const float2*>(Qs + lr * WCT + XPAD + 2 * cp - KE);
         float xs[2 * KE + 2];
@@ -208,7 +196,7 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     };
 #pragma unroll
     for (int r = 0; r < 2 * K; ++r) tpass(lr0 + r, r);
-    float2 acc = make_float2(0.f, 0.f);
+    float2 acc = make_float2(0.f, 0.f), acz = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int m = 0; m < MRG; ++m) {
 #pragma unroll
@@ -255,15 +243,19 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
             if (gr < a.q && col_ok) {
                 *reinterpret_cast<float2*>(LQ + (size_t)gr * a.ld + b) = y;
                 acc = f2fma(xr0[(u + K) % P], y, acc);
+                acz = f2fma(*reinterpret_cast<const float2*>(Zs + (al + K) * WCT + XPAD + 2 * cp), y, acz);
             }
         }
     }
     if (failed) atomicOr(&fail_s, 1);
     double s = block_sum<G::NTH>((double)acc.x + (double)acc.y, red);
+    __syncthreads();   // red[] is reused
+    const double s2 = a.partial2 ? block_sum<G::NTH>((double)acz.x + (double)acz.y, red) : 0.0;
     const int nblk = gridDim.x * gridDim.y;
     if (tid == 0) {
         if (fail_s) atomicOr(a.status, DEV_ERR_TIMEOUT);
         a.partial[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s;
+        if (a.partial2) a.partial2[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s2;
         __threadfence();
         const unsigned t = atomicAdd(a.counter + inst, 1u);
         last_s = (t == (unsigned)nblk - 1) ? 1 : 0;
@@ -272,6 +264,7 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     if (last_s && tid < 32) {
         __threadfence();
         const double qlq = warp_sum_partials(a.partial + (size_t)inst * nblk, nblk);
+        const double lqz = a.partial2 ? warp_sum_partials(a.partial2 + (size_t)inst * nblk, nblk) : 0.0;
         if (tid == 0) {
             a.counter[inst] = 0;
             double al = sc->rz / qlq;
@@ -283,6 +276,7 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
                 al = 0.0;
             }
             sc->alpha = al;
+            if (a.partial2) sc->rzo = sc->rz - al * lqz;   // <R - alpha L(Q), Z>
         }
     }
 }

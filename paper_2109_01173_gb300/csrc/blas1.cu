@@ -66,6 +66,9 @@ struct UpdArgs {
     void* U;             // iterate: T (FP64 form) or the hi part of the double-float correction (mixed)
     void* Ulo;           // lo part (mixed form)
     void* R; const void* Q; const void* LQ; const void* Zold; void* Rop;
+    const void* Qprev;   // lazy mode: the previous iteration's direction (the other ping-pong buffer)
+    int lazy;            // mixed form: add alpha Q to the correction every second iteration, two at a time
+    int lazy_phase;      // timing only (no scalar state): force the even (0) or odd (1) form; -1 otherwise
     long long bs;        // batch stride (elements) = q * ld
     long long nvec;      // 16-byte vectors per instance
     double* rr_part; double* rzo_part; int n_upd;
@@ -154,6 +157,14 @@ struct UVec<float, true> {   // double-float correction
     }
 };
 
+// u += a1 q1 + a2 q2 on a double-float pair (two exact products, TwoSum each)
+__device__ __forceinline__ void df_axpy2(DF& u, const float4& q1, float a1, const float4& q2, float a2) {
+    df_add_prod(u.h.x, u.l.x, a1, q1.x); df_add_prod(u.h.x, u.l.x, a2, q2.x);
+    df_add_prod(u.h.y, u.l.y, a1, q1.y); df_add_prod(u.h.y, u.l.y, a2, q2.y);
+    df_add_prod(u.h.z, u.l.z, a1, q1.z); df_add_prod(u.h.z, u.l.z, a2, q2.z);
+    df_add_prod(u.h.w, u.l.w, a1, q1.w); df_add_prod(u.h.w, u.l.w, a2, q2.w);
+}
+
 __device__ __forceinline__ float dot32(const float4& a, const float4& b) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
 }
@@ -166,7 +177,7 @@ __device__ __forceinline__ double dot32(const double2& a, const double2& b) { re
 // Dot products: working precision within a thread (a few dozen terms), FP64
 // across threads and CTAs (fixed order).
 template <typename T, bool MIXED, int ROP>
-__global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
+__global__ void __launch_bounds__(UPD_THREADS, 2) k_update(UpdArgs g) {
     using V = typename Vec<T>::type;
     static_assert(ROP == 0 || Vec<T>::W == 4, "operand copies are produced by the FP32 update only");
     __shared__ double sh[UPD_THREADS / 32];
@@ -201,6 +212,78 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
         const long long stride = (long long)gridDim.x * blockDim.x;
         constexpr int UNR = 4;   // independent 16-byte loads in flight per thread and array
         long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        // Lazy correction (mixed form): an even iteration only updates R and leaves
+        // alpha Q pending; the odd one adds alpha_prev Q_prev + alpha Q in one pass.
+        const bool lazy = MIXED && g.lazy && (g.use_sc || g.lazy_phase >= 0);
+        const bool pair = lazy && (g.lazy_phase >= 0 ? g.lazy_phase == 1 : (sc->iters & 1) != 0);
+        if constexpr (MIXED) {
+            if (lazy) {
+                const float4* Qp4 = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(g.Qprev) +
+                                                                    (size_t)inst * g.bs);
+                const float ap = pair ? (g.use_sc ? (float)sc->alpha_pend : 0.25f) : 0.f;
+                auto rbody = [&](long long i, float4 r, const float4& lq, const float4& zo) {
+                    axpy_v(r, lq, -alpha);
+                    R[i] = r;
+                    rrt += dot32(r, r);
+                    if (g.flex) rzt += dot32(r, zo);
+                    if constexpr (ROP == 1) Rb[i] = pack_bf16x4(r);
+                    if constexpr (ROP == 2) Rb[i] = pack_f16x4(r, rsf);
+                };
+                // batches of independent 16-byte loads in flight per thread (memory-level parallelism)
+                if (!pair) {
+                    constexpr int UE = 4;
+                    for (; i0 + (UE - 1) * stride < g.nvec; i0 += UE * stride) {
+                        float4 r[UE], lq[UE], zo[UE];
+#pragma unroll
+                        for (int k = 0; k < UE; ++k) {
+                            const long long i = i0 + k * stride;
+                            r[k] = R[i];
+                            lq[k] = LQ[i];
+                            zo[k] = g.flex ? Zo[i] : lq[k];
+                        }
+#pragma unroll
+                        for (int k = 0; k < UE; ++k) rbody(i0 + k * stride, r[k], lq[k], zo[k]);
+                    }
+                } else {
+                    constexpr int UO = 2;
+                    for (; i0 + (UO - 1) * stride < g.nvec; i0 += UO * stride) {
+                        float4 r[UO], lq[UO], zo[UO], qp[UO], qc[UO];
+                        DF u[UO];
+#pragma unroll
+                        for (int k = 0; k < UO; ++k) {
+                            const long long i = i0 + k * stride;
+                            r[k] = R[i];
+                            lq[k] = LQ[i];
+                            zo[k] = g.flex ? Zo[i] : lq[k];
+                            u[k] = DF{U.ph[i], U.pl[i]};
+                            qp[k] = Qp4[i];
+                            qc[k] = Q[i];
+                        }
+#pragma unroll
+                        for (int k = 0; k < UO; ++k) {
+                            const long long i = i0 + k * stride;
+                            df_axpy2(u[k], qp[k], ap, qc[k], alpha);
+                            U.ph[i] = u[k].h;
+                            U.pl[i] = u[k].l;
+                            rbody(i, r[k], lq[k], zo[k]);
+                        }
+                    }
+                }
+                for (; i0 < g.nvec; i0 += stride) {
+                    float4 r = R[i0];
+                    const float4 lq = LQ[i0];
+                    const float4 zo = g.flex ? Zo[i0] : lq;
+                    if (pair) {
+                        DF u{U.ph[i0], U.pl[i0]};
+                        df_axpy2(u, Qp4[i0], ap, Q[i0], alpha);
+                        U.ph[i0] = u.h;
+                        U.pl[i0] = u.l;
+                    }
+                    rbody(i0, r, lq, zo);
+                }
+            }
+        }
+        if (!lazy) {
         using UV = typename UVec<T, MIXED>::Val;
         auto body = [&](long long i, UV u, V r, const V& qv, const V& lq, const V& zo) {
             U.axpy_store(i, u, qv, alpha);
@@ -227,6 +310,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
             for (int k = 0; k < UNR; ++k) body(i0 + k * stride, u[k], r[k], qv[k], lq[k], zo[k]);
         }
         for (; i0 < g.nvec; i0 += stride) body(i0, U.load(i0), R[i0], Q[i0], LQ[i0], g.flex ? Zo[i0] : Q[i0]);
+        }
         const double rr = (double)rrt, rzo = (double)rzt;
         const double s1 = block_sum<UPD_THREADS>(rr, sh);
         const double s2 = block_sum<UPD_THREADS>(rzo, sh);
@@ -248,7 +332,8 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdArgs g) {
                     const int it = sc->iters + 1;
                     sc->iters = it;
                     sc->rr = rrs;
-                    sc->rzo = rzs;
+                    if (g.flex) sc->rzo = rzs;   // else set by the apply kernel
+                    if (lazy) sc->alpha_pend = pair ? 0.0 : (double)alpha;
                     if (ROP == 2) sc->rscale = rs;
                     int act = 1;
                     if (!isfinite(rrs)) {
@@ -309,6 +394,7 @@ __global__ void k_init(InitArgs g) {
             s->rz = 1.0;
             s->rzo = 0.0;
             s->rscale = (rr > 0.0 && isfinite(rr)) ? FP16_RMS * sqrt(g.count / rr) : 1.0;
+            s->alpha_pend = 0.0;
             s->status = isfinite(rr) ? 0 : DEV_ERR_NONFINITE;
             s->active = (rr > s->tol2 && isfinite(rr)) ? 1 : 0;
         }
@@ -432,13 +518,18 @@ __global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const d
         row[j] /= product ? li * mu[j] : li + mu[j];
 }
 
-// U64 += hi + lo at the end of an inner solve of the mixed form (the pair is
-// cleared before the next inner solve starts).  16-byte vectors: n % 4 == 0.
-__global__ void k_fold_df(double* U, long long bs, const float* hi, const float* lo, long long n) {
+// U64 += hi + lo (+ alpha_pend Q_pend, the last even iteration's term when the
+// correction is accumulated lazily) at the end of an inner solve of the mixed
+// form; the pair is cleared before the next inner solve starts.  16-byte
+// vectors: n % 4 == 0.  The pending product is exact in FP64.
+__global__ void k_fold_df(double* U, long long bs, const float* hi, const float* lo, long long n,
+                          const PcgScalars* sc, const float* Qpend) {
     const int inst = blockIdx.y;
+    const double ap = sc ? sc[inst].alpha_pend : 0.0;
     double2* U2 = reinterpret_cast<double2*>(U + (size_t)inst * bs);
     const float4* h4 = reinterpret_cast<const float4*>(hi + (size_t)inst * bs);
     const float4* l4 = reinterpret_cast<const float4*>(lo + (size_t)inst * bs);
+    const float4* q4 = reinterpret_cast<const float4*>(Qpend + (size_t)inst * bs);
     const long long nv = n / 4;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
         const float4 h = h4[i], l = l4[i];
@@ -447,6 +538,13 @@ __global__ void k_fold_df(double* U, long long bs, const float* hi, const float*
         a.y += (double)h.y + (double)l.y;
         b.x += (double)h.z + (double)l.z;
         b.y += (double)h.w + (double)l.w;
+        if (ap != 0.0) {
+            const float4 q = q4[i];
+            a.x += ap * (double)q.x;
+            a.y += ap * (double)q.y;
+            b.x += ap * (double)q.z;
+            b.y += ap * (double)q.w;
+        }
         U2[2 * i] = a;
         U2[2 * i + 1] = b;
     }
@@ -473,9 +571,13 @@ __global__ void k_scale_copy64(const double* src, long long s_bs, int s_ld, doub
 // ---------------------------------------------------------------------------
 mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo, void* R, const void* Q,
                                const void* LQ, const void* Zold, void* Rop, int rop_kind, int flex, int max_iter,
-                               bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st, bool use_scalars) {
+                               bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st, bool use_scalars,
+                               const void* Qprev, int lazy_phase) {
     UpdArgs g;
     g.U = U; g.Ulo = Ulo; g.R = R; g.Q = Q; g.LQ = LQ; g.Zold = Zold; g.Rop = Rop;
+    g.Qprev = Qprev;
+    g.lazy = (!fp64 && Qprev) ? 1 : 0;
+    g.lazy_phase = lazy_phase;
     g.bs = (long long)c->q * c->ld;
     g.nvec = g.bs / (fp64 ? 2 : 4);
     g.rr_part = c->part.rr; g.rzo_part = c->part.rzo; g.n_upd = c->part.n_upd;
@@ -585,10 +687,11 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
     return MOFEM_OK;
 }
 
-mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, cudaStream_t st) {
+mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, const PcgScalars* sc,
+                            const float* Qpend, cudaStream_t st) {
     if (bs % 4 != 0) return MOFEM_ERR_INVALID_ARG;   // internal layout: ld is a multiple of 64
     dim3 grid(592, batch);
-    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs);
+    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

@@ -255,7 +255,10 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, in
 // release an accumulator on the leader's barrier.  Each SM receives 32 KB per
 // 512 tensor cycles instead of 48 KB (the K-slice bytes per MMA are what bound
 // the 1-SM tiles).
-constexpr int ST2 = 6;
+#ifndef MOFEM_GEMM_STAGES
+#define MOFEM_GEMM_STAGES 6   // 32 KB stages in flight per CTA
+#endif
+constexpr int ST2 = MOFEM_GEMM_STAGES;
 constexpr int A2_BYTES = 128 * 128, B2_BYTES = 128 * 128;
 constexpr int STAGE2_BYTES = A2_BYTES + B2_BYTES;
 

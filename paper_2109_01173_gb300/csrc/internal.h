@@ -29,6 +29,7 @@ struct PcgScalars {
     double rr;          // ||R||^2 after the last update
     double tol2;        // stop when rr <= tol2
     double rscale;      // scale applied to the FP16 operand copy of R (undone on the GEMM output)
+    double alpha_pend;  // mixed form: alpha of the last even iteration, not yet added to the correction
     int iters;          // iterations done in this (inner) solve
     int active;         // 1 while not converged
     int status;         // DEV_ERR_* bits
@@ -42,6 +43,7 @@ struct Partials {
     double* rr;     // ||R||^2 after update [batch][n_upd_ctas]
     double* rzo;    // <R_new, Z_old>       [batch][n_upd_ctas]
     double* rz;     // <R, Z_new>           [batch][n_rz_ctas]
+    double* lqz;    // <L(Q), Z>            [batch][n_apply_ctas] (packed apply: flexible beta without Z_old)
     int n_apply, n_upd, n_rz;
 };
 
@@ -155,6 +157,7 @@ struct ApplyPcgArgs {
     int q, ld; long long bs;
     void* Qnew; void* LQ;
     double* partial; unsigned* counter;
+    double* partial2;   // packed FP32 apply: per-CTA <L(Q), Z>, finalised into rzo = rz - alpha <L(Q), Z> (or null)
     PcgScalars* sc; int use_sc;
     int* status;
 };

@@ -31,8 +31,9 @@
 mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo, void* R, const void* Q,
                                const void* LQ, const void* Zold, void* Rop, int rop_kind, int flex, int max_iter,
                                bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st,
-                               bool use_scalars = true);
-mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, cudaStream_t st);
+                               bool use_scalars = true, const void* Qprev = nullptr, int lazy_phase = -1);
+mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, const PcgScalars* sc,
+                            const float* Qpend, cudaStream_t st);
 mofem_status launch_scale_copy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
                                  int rows, int cols, int batch, double scale, cudaStream_t st);
 mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
@@ -87,11 +88,12 @@ static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
     c->part.n_upd = (int)std::max(1LL, std::min(296LL, (nvec + 1023) / 1024));
     c->part.n_rz = tc_rz_ctas(c);
     const size_t n_total =
-        (size_t)B * (c->part.n_apply + e.n_res + c->part.n_upd * 2 + c->part.n_rz * 3) + B;
+        (size_t)B * (2 * c->part.n_apply + e.n_res + c->part.n_upd * 2 + c->part.n_rz * 3) + B;
     MOFEM_CUDA_TRY(cudaMalloc(&c->d_part, n_total * sizeof(double)));
     MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_part, 0, n_total * sizeof(double), st));
     double* p = c->d_part;
     c->part.qlq = p; p += (size_t)B * c->part.n_apply;
+    c->part.lqz = p; p += (size_t)B * c->part.n_apply;
     e.res_part = p; p += (size_t)B * e.n_res;
     c->part.rr = p; p += (size_t)B * c->part.n_upd;
     c->part.rzo = p; p += (size_t)B * c->part.n_upd;
@@ -313,13 +315,17 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     a.q = c->q; a.ld = c->ld; a.bs = bs;
     a.Qnew = Qn; a.LQ = LQ;
     a.partial = c->part.qlq; a.counter = c->d_ctr;
+    // the packed FP32 apply also forms <R_new, Z> for the flexible beta (no Z re-read in the update)
+    const bool packed = apply_pcg_packed(c->K, c->NT, fp64);
+    a.partial2 = packed ? c->part.lqz : nullptr;
     a.sc = c->d_sc; a.use_sc = 1;
     a.status = c->d_status;
     MOFEM_TRY(launch_apply_pcg(c->K, c->NT, fp64, *mZ, *mQp, fp64 ? nullptr : &e.mS32, a, c->batch, st));
-    // 2) U += alpha Q ; R -= alpha LQ ; convergence (last CTA) ; graph condition
+    // 2) R -= alpha LQ ; U += alpha Q (mixed: lazily, two iterations at a time) ; convergence
+    //    (last CTA) ; graph condition
     MOFEM_TRY(launch_pcg_update(c, fp64, U, Ulo, R, Qn, LQ, Z, fp64 ? nullptr : c->tc[which].Rop,
-                                fp64 ? 0 : (which == 1 ? 1 : (which == 2 ? 2 : 0)), fp64 ? 0 : 1, max_iter, fixed,
-                                cond, st, true));
+                                fp64 ? 0 : (which == 1 ? 1 : (which == 2 ? 2 : 0)), (fp64 || packed) ? 0 : 1,
+                                max_iter, fixed, cond, st, true, fp64 ? nullptr : Qp));
     // 3) Z = P^{-1}(R) ; rz and beta (last CTA)
     if (fp64) {
         MOFEM_TRY(precond64(c, (const double*)R, bs, c->ld, (double*)Z, bs, c->ld, st));
@@ -620,7 +626,8 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
                 MOFEM_TRY(tc_prepare(c, plan_of(pe), st));
                 continue;
             }
-            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, st));
+            // even iterations leave alpha Q_a pending (lazy correction): the fold adds it
+            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, c->d_sc, w32(c, W32_QA), st));
             int it = 0;
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
@@ -806,12 +813,13 @@ mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int re
             MOFEM_TRY(launch_apply_pcg(c->K, c->NT, false, e.mZ32, e.mQB32, &e.mS32, a, c->batch, st));
         return MOFEM_OK;
     }
-    if (kernel == 5) {
-        MOFEM_TRY(tc_prepare(c, 1, st));
+    if (kernel == 5 || kernel == 7) {   // residual update of an even (5) or odd (7) iteration, FP16 operand copy
+        MOFEM_TRY(tc_prepare(c, 2, st));
+        const bool packed = apply_pcg_packed(c->K, c->NT, false);
         for (int r = 0; r < reps; ++r)
             MOFEM_TRY(launch_pcg_update(c, false, w32(c, W32_U), w32(c, W32_ULO), w32(c, W32_R), w32(c, W32_QA),
-                                        w32(c, W32_LQ),
-                                        w32(c, W32_Z), c->tc[1].Rop, 1, 1, 1 << 30, true, nullptr, st, false));
+                                        w32(c, W32_LQ), w32(c, W32_Z), c->tc[2].Rop, 2, packed ? 0 : 1, 1 << 30, true,
+                                        nullptr, st, false, w32(c, W32_QB), kernel == 7 ? 1 : 0));
         return MOFEM_OK;
     }
     return MOFEM_ERR_INVALID_ARG;
