@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-heat", action="store_true", help="skip the differentiation workload (heat IMEX + adjoint)")
     ap.add_argument("--no-dib", action="store_true", help="skip the reaction-diffusion (DIB) workload")
+    ap.add_argument("--no-batching", action="store_true", help="skip the heterogeneous-batch workload")
+    ap.add_argument("--batching-full", action="store_true",
+                    help="heterogeneous batch of 256 problems with n up to 2049 (default: 64 problems, n <= 513)")
     ap.add_argument("--host-loop", action="store_true",
                     help="step the inner loop from the host instead of a conditional-node CUDA graph "
                          "(per-kernel profilers cannot see kernels inside conditional graphs)")
@@ -221,6 +224,42 @@ def measure_dib(steps=300):
             "inner_iterations_per_step": info.iterations / max(steps, 1),
             "last_increment": inc[-1] if inc else None,
             "check": "states vs the FP64 oracle at checkpoints: tests/test_gpu_dib.py"}
+
+
+def measure_batching(full=False):
+    """Heterogeneous batch (256 problems with n in {129..2049} when `full`, else 64 with
+    n in {129, 257, 513}; k in 1..4, gamma ~ U[0,10], tops 1 + a sin(2 pi b x), Fourier f):
+    groups of equal (k, n) solved concurrently, concurrency chosen by the autotuner; setup
+    and tuning reported apart from the timed solve (CUDA events, rtol 1e-10, FP16 GEMMs)."""
+    import torch
+    import paper_2109_01173_gb300.mofem as mf
+    from paper_2109_01173_gb300.inputs import hetero_instances
+    count, nch = (256, (129, 257, 513, 1025, 2049)) if full else (64, (129, 257, 513))
+    probs = hetero_instances(count, n_choices=nch, k_choices=(1, 2, 3, 4), seed=0)
+    t0 = time.perf_counter()
+    g = mf.Group(probs)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    F = [torch.tensor(p["F"], device="cuda") for p in probs]
+    U = [torch.zeros((p["n"] - 2, p["n"] - 2), dtype=torch.float64, device="cuda") for p in probs]
+    t0 = time.perf_counter()
+    chosen = g.autotune(F, U, rtol=1e-10)
+    t_tune = time.perf_counter() - t0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    infos, code = g.solve(F, U, rtol=1e-10, check=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    n_groups = mf.group_layout(probs)[0]
+    g.close()
+    return {"workload": f"{count} Dirichlet elliptic problems, n in {list(nch)} (k = 3: n adjusted), k in 1..4, "
+                        f"gamma ~ U[0,10], g2 = 1 + a sin(2 pi b x), Fourier f, rtol 1e-10",
+            "groups": n_groups, "concurrency_chosen": chosen, "status": code, "setup_s": t_setup,
+            "autotune_s": t_tune, "solve_ms": ms, "problems_per_s": count / (ms / 1e3),
+            "max_rel_residual": max(i.rel_residual for i in infos),
+            "check": "per-problem solutions vs the FP64 oracle: tests/test_gpu_group.py"}
 
 
 # ----------------------------------------------------------------------------------
@@ -454,6 +493,8 @@ def run_mofem(a):
         line["heat_adjoint"] = measure_heat()
     if not a.no_dib and rank == 0:
         line["reaction_diffusion"] = measure_dib()
+    if not a.no_batching and rank == 0:
+        line["heterogeneous_batch"] = measure_batching(a.batching_full)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

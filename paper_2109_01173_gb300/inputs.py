@@ -180,3 +180,22 @@ def dib_initial(n, eta_e, theta_e, seed=0, amplitude=1e-3):
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.stack([eta_e + rng.uniform(-amplitude, amplitude, (n, n)),
                      theta_e + rng.uniform(-amplitude, amplitude, (n, n))])
+
+
+def hetero_instances(count, n_choices=(129, 257, 513, 1025, 2049), k_choices=(1, 2, 3, 4), seed=0):
+    """Heterogeneous batch: per instance n ~ U(n_choices), k ~ U(k_choices) (n adjusted to
+    3 floor((n-1)/3) + 1 when k = 3 does not divide n - 1), gamma ~ U[0, 10],
+    g2 = 1 + a sin(2 pi b x) with a ~ U[0, 0.3], b ~ U{1, 2, 3}, Dirichlet, seeded
+    32-mode Fourier f."""
+    rng = np.random.Generator(np.random.PCG64(5000 + seed))
+    out = []
+    for i in range(count):
+        n = int(rng.choice(n_choices))
+        k = int(rng.choice(k_choices))
+        if (n - 1) % k:
+            n = k * ((n - 1) // k) + 1
+        gamma = float(rng.uniform(0.0, 10.0))
+        g2 = Profile(c0=1.0, sa=float(rng.uniform(0.0, 0.3)), sf=int(rng.integers(1, 4)))
+        out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet',
+                        F=fourier_f(ZERO, g2, n, seed * 100000 + i)))
+    return out

@@ -48,6 +48,11 @@ class MofemError(RuntimeError):
         self.code = code
 
 
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("g1", Profile), ("g2", Profile), ("k", ctypes.c_int), ("n_nodes", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("bc", ctypes.c_int)]
+
+
 class DibParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("alpha", "gamma", "A1", "A2", "B", "C", "D", "k2", "k3", "d_theta")]
 
@@ -77,6 +82,11 @@ def _load():
         "mofem_rds_step": [vp, c_double, vp, vp, vp, c_double, c_int, P(SolveInfo), vp],
         "mofem_dib_kinetics": [P(DibParams), c_double, vp, vp, vp, vp, ctypes.c_longlong, vp],
         "mofem_dib_equilibrium": [P(DibParams), P(c_double), P(c_double)],
+        "mofem_group_layout": [c_int, P(ProblemDesc), P(c_int), P(c_int)],
+        "mofem_group_setup": [c_int, P(ProblemDesc), P(Opts), P(vp)],
+        "mofem_group_solve": [vp, P(vp), P(vp), c_double, c_int, c_int, P(SolveInfo), vp],
+        "mofem_group_autotune": [vp, P(vp), P(vp), c_double, c_int, c_int, P(c_int)],
+        "mofem_group_destroy": [vp],
         "mofem_dib_run": [vp, P(DibParams), c_double, c_double, c_int, vp, c_double, c_int, P(c_double),
                           P(SolveInfo), vp],
         "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
@@ -101,7 +111,8 @@ LIB = _load()
 
 EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply", "mofem_rhs", "mofem_precond",
             "mofem_pcg_direction", "mofem_imex_step_tol", "mofem_imex_adjoint_step", "mofem_rds_step",
-            "mofem_dib_kinetics", "mofem_dib_run", "mofem_dib_equilibrium",
+            "mofem_dib_kinetics", "mofem_dib_run", "mofem_dib_equilibrium", "mofem_group_layout",
+            "mofem_group_setup", "mofem_group_solve", "mofem_group_autotune", "mofem_group_destroy",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
             "mofem_host_tables", "mofem_bench_kernel"]
 
@@ -298,3 +309,65 @@ def dib_equilibrium(params):
     e, t = ctypes.c_double(), ctypes.c_double()
     _check("mofem_dib_equilibrium", LIB.mofem_dib_equilibrium(ctypes.byref(p), ctypes.byref(e), ctypes.byref(t)))
     return e.value, t.value
+
+
+def _problem_array(problems):
+    """ctypes array of problem descriptors from dicts with g1, g2, k, n, gamma, bc ('dirichlet'/'neumann')."""
+    arr = (ProblemDesc * len(problems))()
+    keep = []
+    for i, d in enumerate(problems):
+        p1, k1 = make_profile(d["g1"])
+        p2, k2 = make_profile(d["g2"])
+        keep += [k1, k2]
+        bc = d.get("bc", DIRICHLET)
+        bc = {"dirichlet": DIRICHLET, "neumann": NEUMANN}.get(bc, bc)
+        arr[i] = ProblemDesc(p1, p2, int(d["k"]), int(d["n"]), float(d["gamma"]), int(bc))
+    return arr, keep
+
+
+def group_layout(problems):
+    """(number of groups, group index of each problem), computed on the host."""
+    arr, keep = _problem_array(problems)
+    ng = ctypes.c_int()
+    of = (ctypes.c_int * len(problems))()
+    _check("mofem_group_layout", LIB.mofem_group_layout(len(problems), arr, ctypes.byref(ng), of))
+    return ng.value, list(of)
+
+
+class Group:
+    """Heterogeneous batch of elliptic problems (see mofem_group_setup)."""
+
+    def __init__(self, problems, opts=None):
+        arr, keep = _problem_array(problems)
+        self.count = len(problems)
+        self.g = ctypes.c_void_p()
+        _check("mofem_group_setup", LIB.mofem_group_setup(self.count, arr, ctypes.byref(opts) if opts else None,
+                                                          ctypes.byref(self.g)))
+
+    def _ptrs(self, tensors):
+        return (ctypes.c_void_p * self.count)(*[_ptr(t) for t in tensors])
+
+    def solve(self, F, U, rtol=1e-10, max_iter=500, precision="fp16", check=True):
+        infos = (SolveInfo * self.count)()
+        code = LIB.mofem_group_solve(self.g, self._ptrs(F), self._ptrs(U), rtol, max_iter, PRECISIONS[precision],
+                                     infos, _stream())
+        if check:
+            _check("mofem_group_solve", code)
+        return list(infos), code
+
+    def autotune(self, F, U, rtol=1e-10, max_iter=500, precision="fp16"):
+        chosen = ctypes.c_int()
+        _check("mofem_group_autotune", LIB.mofem_group_autotune(self.g, self._ptrs(F), self._ptrs(U), rtol, max_iter,
+                                                                PRECISIONS[precision], ctypes.byref(chosen)))
+        return chosen.value
+
+    def close(self):
+        if self.g:
+            LIB.mofem_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

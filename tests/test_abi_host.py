@@ -125,3 +125,15 @@ def test_dib_equilibrium_matches_oracle(mofem):
     # D = 3.2727 is printed to 4 decimals: g(0, 1/2) = 1.5e-5, so the zero moves by O(1e-5 / |J|)
     e, t = mofem.dib_equilibrium(dict(dib.CAP, C=4.0))
     assert abs(e) <= 1e-4 and abs(t - 0.5) <= 1e-4
+
+
+def test_group_layout_on_host(mofem):
+    """Problems of equal (k, n, bc) share a group; groups ordered by decreasing n^3 * size."""
+    P = lambda k, n, bc="dirichlet": dict(g1=ZERO, g2=SIN_TOP, k=k, n=n, gamma=1.0, bc=bc)
+    probs = [P(2, 33), P(1, 65), P(2, 33), P(2, 33, "neumann"), P(1, 65), P(4, 129), P(2, 33)]
+    ng, of = mofem.group_layout(probs)
+    assert ng == 4
+    assert of[0] == of[2] == of[6] and of[1] == of[4]
+    assert len({of[0], of[1], of[3], of[5]}) == 4
+    assert of[5] == 0                      # 129^3 x 1 is the most work
+    assert mofem.LIB.mofem_group_layout(0, None, None, None) == 1
