@@ -419,6 +419,8 @@ def run_mofem(a):
     t_apply = time_kernel(0, prec_k)
     t_upd_even, t_upd_odd = time_kernel(5, prec_k), time_kernel(7, prec_k)
     t_upd = 0.5 * (t_upd_even + t_upd_odd)   # one update of each parity per pair of iterations
+    t_res64 = time_kernel(6, prec_k)          # FP64 residual B - L(U) (first refinement step)
+    t_resdf = time_kernel(8, prec_k)          # double-float residual update R -= L(d) (later steps)
     flops_gemm = 2.0 * B * q ** 3
     gemm_tflops = [flops_gemm / t / 1e12 for t in t_gemm]
     tg = statistics.mean(t_gemm)
@@ -484,6 +486,9 @@ def run_mofem(a):
                             "achieved": upd_bytes / t_upd / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                             "frac": upd_bytes / t_upd / 1e9 / peaks["hbm_gbs"], "us": t_upd * 1e6,
                             "us_even_odd": [t_upd_even * 1e6, t_upd_odd * 1e6]},
+        "refinement_residual": {"fp64_recompute_us": t_res64 * 1e6, "df_update_us": t_resdf * 1e6,
+                                "note": "per refinement step: B - L(U) in FP64 after the first step from zero, "
+                                        "R -= L(d) in double-float arithmetic after later steps"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * n * n * 8,
                 "d2h_bytes_per_step": B * q * q * 8, "max_abs_diff_vs_device_run": err_e2e},
         "fp64_form": fp64,

@@ -70,6 +70,8 @@ struct mofem_ctx {
     // banded tables, diagonal-major: tab[term][j][row] = S_term[row][row + j - K]
     double* S64 = nullptr;  float* S32 = nullptr;   // [batch][NT][P][q]
     float* S2dup = nullptr;   // [batch][q][2*SR2] FP32 S rows, each coefficient twice (packed apply)
+    float* Sdf = nullptr;     // plain S tables as double-float: hi plane then lo plane, each [batch][NT][P][q]
+    float* Tdf = nullptr;     // plain T tables as double-float: hi plane then lo plane, each [NT][P][q]
     int s2_row = 0;           // floats per S2dup row
     double* T64 = nullptr;  float* T32 = nullptr;   // [NT][P][q]
     double* Sr64 = nullptr; double* Tr64 = nullptr; // RHS mass factors: [batch][P][q], [P][q] (offset off)
@@ -163,6 +165,12 @@ struct ApplyPcgArgs {
 };
 mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const double* beta, const double* rz,
                            void* Q, void* LQ, int ld, double* alpha, bool fp64, cudaStream_t st);
+// R -= L(d) in double-float arithmetic, d = hi + lo + alpha_pend * Qpend - err per
+// instance (internal layout; err may be null), and per-CTA FP64 partials of ||R||^2
+// (nblk per instance).
+mofem_status launch_residual_update_df(const mofem_ctx* c, const float* hi, const float* lo, const float* Qpend,
+                                       const float* err, double* R, double* partial, int* nblk, cudaStream_t st);
+int residual_update_df_ctas(int K, int q);   // partials per instance of the above
 mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, const CUtensorMap& mQ,
                               const CUtensorMap* mS,
                               const ApplyPcgArgs& a, int batch, cudaStream_t st);

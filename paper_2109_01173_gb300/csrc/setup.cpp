@@ -360,6 +360,23 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
     Band& Mt = H.Mt;
     Band& Kt = H.Kt;
 
+    // --- double-float copies of the plain tables (residual updates, before the row-sum form)
+    {
+        auto split = [&](const std::vector<double>& h, float** d) -> mofem_status {
+            std::vector<float> two(2 * h.size());
+            for (size_t i = 0; i < h.size(); ++i) {
+                const float hi = (float)h[i];
+                two[i] = hi;
+                two[h.size() + i] = (float)(h[i] - (double)hi);
+            }
+            MOFEM_TRY(dev_alloc(d, two.size()));
+            MOFEM_CUDA_TRY(cudaMemcpy(*d, two.data(), two.size() * sizeof(float), cudaMemcpyHostToDevice));
+            return MOFEM_OK;
+        };
+        MOFEM_TRY(split(Sh, &c->Sdf));   // [hi | lo] planes of [batch][NT][P][q]
+        MOFEM_TRY(split(Th, &c->Tdf));   // [hi | lo] planes of [NT][P][q]
+    }
+
     // --- upload tables (difference form: row sum in the diagonal slot) -------------
     auto rowsum_one = [&](double* base) {
         for (int r = 0; r < q; ++r) {
@@ -504,7 +521,7 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
 }
 
 void mofem_free(mofem_ctx* c) {
-    void* ptrs[] = {c->U64m, c->S64, c->S32, c->S2dup, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
+    void* ptrs[] = {c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
                     c->lam32, c->mu32, c->w64, c->w32, c->Bm64, c->R64, c->d_part, c->d_sc, c->d_status,
                     c->d_red};
     for (void* p : ptrs) cudaFree(p);

@@ -18,7 +18,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_EIG, ERR_NONFINITE, ERR_BREAKDOWN, ERR_NOT_CO
 DIRICHLET, NEUMANN = 0, 1
 FP64, MIXED_TF32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
 PENCIL_AVERAGED, PENCIL_DOMINANT, PENCIL_PRODUCT = 0, 1, 2
-FLAG_HOST_LOOP, FLAG_FIXED_ITERS = 1, 2
+FLAG_HOST_LOOP, FLAG_FIXED_ITERS, FLAG_TRUE_RESIDUAL = 1, 2, 4
 
 PRECISIONS = {"fp64": FP64, "tf32": MIXED_TF32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
 

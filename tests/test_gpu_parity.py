@@ -358,6 +358,86 @@ def test_full_size_solve(mf, full):
     assert float(((U64 - U).norm() / U64.norm()).item()) <= 1e-8
 
 
+def _true_rel(h, F, U):
+    """||B - L(U)|| / ||B|| per instance with the library's FP64 (difference-form) apply."""
+    torch = torch_()
+    B = torch.zeros_like(U)
+    h.rhs(F, B)
+    Y = torch.zeros_like(U)
+    h.apply(U, Y, "fp64")
+    R = (B - Y).reshape(U.shape[0] if U.dim() == 3 else 1, -1)
+    return (R.norm(dim=1) / B.reshape(R.shape).norm(dim=1)).tolist()
+
+
+def _solve_both(mf, g1, g2, k, n, gam, bc, F, prec, rtol=1e-10):
+    """The same solve with the residual updated after the first step (default) and
+    recomputed in FP64 after every step (FLAG_TRUE_RESIDUAL)."""
+    torch = torch_()
+    B = len(g1)
+    out = []
+    for flags in (0, mf.FLAG_TRUE_RESIDUAL):
+        h = mf.Handle(g1, g2, k, n, gam, bc=bc, opts=mf.make_opts(flags=flags))
+        U = torch.zeros((B, h.q, h.q), dtype=torch.float64, device="cuda")
+        info, code = h.pcg_solve(F, U, rtol=rtol, max_iter=500, precision=prec)
+        assert code == 0 and info.outer_steps >= 2
+        out.append((U, info.rel_residual, _true_rel(h, F, U)))
+        h.close()
+    return out
+
+
+def test_residual_update_full_size(mf):
+    """Bench workload (P2, 2049 x 2049 nodes, 4 instances, rtol 1e-10).  Both runs
+    take the same steps, so the iterates are bitwise equal; the reported residuals
+    differ only by the evaluation noise of the FP64 recomputations that anchor
+    them (u q^2 / pi^2 = 4.7e-11 of ||B|| at q = 2047, the t-pass intermediate
+    rounded to FP64 and then second-differenced); the target holds on the
+    recomputed residual."""
+    torch = torch_()
+    insts = [metric_instance(n=2049, k=2, seed=s) for s in range(4)]
+    F = torch.tensor(np.stack([i["F"] for i in insts]), device="cuda")
+    (U0, rep0, rel0), (U1, rep1, rel1) = _solve_both(mf, [i["g1"] for i in insts], [i["g2"] for i in insts], 2,
+                                                     2049, [1.0] * 4, 0, F, "fp16")
+    assert torch.equal(U0, U1)
+    assert max(rel0) <= 1e-10
+    assert abs(max(rel1) - rep1) <= 1e-13, (rep1, rel1)
+    noise = 2.0 ** -53 * 2047 ** 2 / np.pi ** 2
+    assert abs(max(rel0) - rep0) <= 2 * noise, (rep0, rel0)
+
+
+@pytest.mark.parametrize("k,n,dname,bc,gamma", [(2, 257, "one", 0, 1.0), (1, 301, "two", 1, 2.0),
+                                                 (3, 193, "two", 0, 0.5), (0, 257, "one", 1, 1.0)])
+def test_residual_update_tracks_recomputed(mf, k, n, dname, bc, gamma):
+    """Where the FP64 evaluation noise is small (u q^2 / pi^2 < 1e-12), the updated
+    residual equals the recomputed one to 2e-12 of ||B||: an error of 1e-6 in the
+    double-float L(d) (or a missed rounding of the iterate) would show at 1e-11."""
+    torch = torch_()
+    g1, g2 = dom(dname)
+    F = torch.tensor(fourier_f(g1, g2, n, seed=n), device="cuda").unsqueeze(0)
+    (U0, rep0, rel0), (U1, rep1, rel1) = _solve_both(mf, [g1], [g2], k, n, [gamma], bc, F, "bf16")
+    assert torch.equal(U0, U1)
+    assert abs(rel0[0] - rep0) <= 2e-12, (rep0, rel0)
+    assert abs(rel1[0] - rep1) <= 1e-13, (rep1, rel1)
+
+
+def test_residual_update_nonzero_guess(mf):
+    """From a nonzero initial guess every step updates the residual (the first
+    residual is recomputed before the loop): result against the oracle."""
+    torch = torch_()
+    k, n = 2, 129
+    P = Problem(ZERO, SIN_TOP, k, n, 1.0)
+    F = fourier_f(ZERO, SIN_TOP, n, seed=5)
+    Uo, _ = pcg.solve(P, F, rtol=1e-13)
+    h = mf.Handle(ZERO, SIN_TOP, k, n, 1.0)
+    U = torch.tensor(Uo + 1e-3 * np.random.default_rng(2).standard_normal(Uo.shape), device="cuda")
+    Ft = torch.tensor(F, device="cuda")
+    info, code = h.pcg_solve(Ft, U, rtol=1e-10, max_iter=400, precision="bf16")
+    assert code == 0
+    assert np.linalg.norm(U.cpu().numpy() - Uo) <= 1e-8 * np.linalg.norm(Uo)
+    rel = _true_rel(h, Ft.unsqueeze(0), U.unsqueeze(0))
+    assert rel[0] <= 1e-10 and abs(rel[0] - info.rel_residual) <= 2e-12
+    h.close()
+
+
 def test_full_size_direction_batched(mf):
     """The PCG-form apply in the launch configuration of bench.py (P2, 2049 x 2049 nodes,
     four instances, FP32): new direction and L(Q) at sampled entries against the oracle's
