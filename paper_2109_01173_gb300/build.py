@@ -54,7 +54,7 @@ def build(verbose=False):
         return LIB
     cmd = [NVCC] + ARCH + ["-shared", "-o", LIB] + objs + [
         "-L", os.path.join(CUDA, "lib64"), "-lcublas", "-lcusolver",
-        "-Xlinker", "-rpath," + os.path.join(CUDA, "lib64")]
+        "-Xlinker", "-rpath," + os.path.join(CUDA, "lib64"), "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"libmofem link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

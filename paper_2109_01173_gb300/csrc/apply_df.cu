@@ -2,21 +2,27 @@
 //
 //     R64 <- R64 - L(d),   L(d) = sum_i S_i d T_i^T   (Sec. 5, operator L~)
 //
-// for the correction d = hi + lo + alpha_pend Q_pend - err of one refinement step
-// (the inner solve's double-float accumulator, its pending last term, and the exact
-// rounding error err of the FP64 iterate's update U <- fl(U + d), so that R tracks
-// B - L(U) of the stored iterate).  From the second refinement step on this
+// for the step d of one refinement step, given as a double-float pair (dh, dl):
+// the FP64 iterate's actual change fl(U + d') - U, which the fold of the inner
+// solve's correction d' leaves in the correction buffers, so that R tracks
+// B - L(U) of the stored iterate.  From the second refinement step on this
 // replaces the FP64 recomputation R = B - L(U): |d| is ~1e-5 |U| there, so an
-// evaluation of L(d) with ~2^-46 relative arithmetic (double-float: exact FMA
-// products, TwoSum accumulation) is accurate to ~1e-13 of ||B||, and it runs on
-// the FP32 pipes (FP64 throughput on this GPU is a small fraction of FP32).  Plain (not
-// difference) form: the coefficient tables are the plain banded factors split
-// into FP32 (hi, lo) pairs at setup.
+// evaluation of L(d) with ~2^-44 relative arithmetic is accurate to ~1e-13 of
+// ||B||, and it runs on the FP32 pipes (FP64 throughput on this GPU is a small
+// fraction of FP32).  Plain (not difference) form: the coefficient tables are the
+// plain banded factors split into FP32 (hi, lo) pairs at setup.
 //
-// Kernel: one CTA = 128 columns x TA rows, one column per thread; the correction
-// tile (with its K-halo) is formed in shared memory as (hi, lo) pairs, the t-pass
+// Arithmetic: each product (ah + al)(bh + bl) as ah*bh exactly (FMA residual) plus
+// the two cross terms; sums of a chain (2K+1 products, or the NT term results)
+// keep the running high part and collect every rounding error, exact by TwoSum,
+// in the low part, renormalised once at the end of the chain (error of the chain
+// ~ n^2 u^2 max|partial sum|, u = 2^-24).
+//
+// Kernel: one CTA = 128 columns x TA rows, one column per thread; the step's tile
+// (with its K-halo) is staged in shared memory as (hi, lo) pairs, the t-pass
 // values of all terms for each new row enter a register ring of the last 2K+1
-// rows, the s-pass reads the row's coefficients as shared-memory broadcasts.
+// rows (shifted by one per row), the s-pass reads the row's coefficients as
+// shared-memory broadcasts.
 // Output: R64 updated in place and one FP64 partial of ||R64||^2 per CTA.
 #include "internal.h"
 
@@ -27,16 +33,13 @@ constexpr int DTB = 128;
 template <int K>
 struct DGeo {
     static constexpr int P = 2 * K + 1;
-    static constexpr int MR = (32 + P - 1) / P;
-    static constexpr int TA = MR * P;
+    static constexpr int TA = 32;
     static constexpr int HR = TA + 2 * K;
     static constexpr int WC = DTB + 2 * K;
 };
 
 struct DfArgs {
-    const float* hi; const float* lo; const float* qp;   // correction parts, [batch][q][ld]
-    const float* err;                                    // rounding error of the fold (or null)
-    const PcgScalars* sc;                                // alpha_pend per instance
+    const float* dh; const float* dl;                    // the step, [batch][q][ld]
     const float* Sh; const float* Sl; long long s_bs;    // S tables, hi / lo planes, [batch][NT][P][q]
     const float* Th; const float* Tl;                    // T tables, hi / lo planes, [NT][P][q]
     double* R; long long bs; int ld, q;
@@ -47,8 +50,7 @@ struct dfl {
     float h, l;
 };
 
-// s += (ah + al)(bh + bl): high product exact by FMA, cross terms in FP32,
-// TwoSum of the high parts, renormalised.
+// s += (ah + al)(bh + bl); s.l collects the rounding errors (not renormalised).
 __device__ __forceinline__ void acc_prod(dfl& s, float ah, float al, float bh, float bl) {
     const float p = ah * bh;
     float e = fmaf(ah, bh, -p);
@@ -56,16 +58,38 @@ __device__ __forceinline__ void acc_prod(dfl& s, float ah, float al, float bh, f
     e = fmaf(al, bh, e);
     const float t = s.h + p;
     const float v = t - s.h;
-    e += (s.h - (t - v)) + (p - v);
-    e += s.l;
-    s.h = t + e;
-    s.l = e - (s.h - t);
+    const float r = (s.h - (t - v)) + (p - v);   // TwoSum: s.h + p = t + r exactly
+    s.h = t;
+    s.l += r + e;
+}
+
+// (ah + al)(bh + bl) as a new chain: high product and its collected error
+__device__ __forceinline__ dfl first_prod(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    return dfl{p, e};
+}
+
+// s += x for a double-float x (its low part joins the error collection)
+__device__ __forceinline__ void acc_df(dfl& s, dfl x) {
+    const float t = s.h + x.h;
+    const float v = t - s.h;
+    const float r = (s.h - (t - v)) + (x.h - v);
+    s.h = t;
+    s.l += r + x.l;
+}
+
+__device__ __forceinline__ dfl renorm(dfl s) {
+    const float h = s.h + s.l;
+    return dfl{h, s.l - (h - s.h)};
 }
 
 template <int K, int NT>
-__global__ void __launch_bounds__(DTB) k_resid_df(DfArgs a) {
+__global__ void __launch_bounds__(DTB, NT * (2 * K + 1) <= 25 ? 4 : 3) k_resid_df(DfArgs a) {
     using G = DGeo<K>;
-    constexpr int P = G::P, TA = G::TA, MR = G::MR, HR = G::HR, WC = G::WC, NTP = NT * P;
+    constexpr int P = G::P, TA = G::TA, HR = G::HR, WC = G::WC, NTP = NT * P;
     extern __shared__ __align__(16) float dsm[];
     float* xh = dsm;                     // [HR][WC]
     float* xl = xh + HR * WC;            // [HR][WC]
@@ -75,32 +99,26 @@ __global__ void __launch_bounds__(DTB) k_resid_df(DfArgs a) {
     const int tid = threadIdx.x, inst = blockIdx.z;
     const int a0 = blockIdx.y * TA, b0 = blockIdx.x * DTB;
     const int q = a.q;
-    const double apd = a.sc ? a.sc[inst].alpha_pend : 0.0;
-    const float aph = (float)apd, apl = (float)(apd - (double)aph);   // alpha_pend as a double-float
-    const float* hi = a.hi + (size_t)inst * a.bs;
-    const float* lo = a.lo + (size_t)inst * a.bs;
-    const float* qp = a.qp + (size_t)inst * a.bs;
-    const float* er = a.err ? a.err + (size_t)inst * a.bs : nullptr;
-    // correction tile with halo: d = (hi, lo) + ap * qp - err (exact products, TwoSum), zero outside
+    const float* dh = a.dh + (size_t)inst * a.bs;
+    const float* dl = a.dl + (size_t)inst * a.bs;
+    // step tile with halo, zero outside the domain
     for (int r = tid / 32; r < HR; r += DTB / 32) {
         const int gr = a0 - K + r;
         const bool rok = gr >= 0 && gr < q;
         for (int cc = tid & 31; cc < WC; cc += 32) {
             const int gc = b0 - K + cc;
-            dfl x{0.f, 0.f};
+            float vh = 0.f, vl = 0.f;
             if (rok && gc >= 0 && gc < q) {
                 const size_t o = (size_t)gr * a.ld + gc;
-                x.h = hi[o];
-                x.l = lo[o];
-                if (aph != 0.f) acc_prod(x, aph, apl, qp[o], 0.f);
-                if (er) acc_prod(x, er[o], 0.f, -1.f, 0.f);
+                vh = dh[o];
+                vl = dl[o];
             }
-            xh[r * WC + cc] = x.h;
-            xl[r * WC + cc] = x.l;
+            xh[r * WC + cc] = vh;
+            xl[r * WC + cc] = vl;
         }
     }
-    for (int idx = tid; idx < TA * NTP; idx += DTB) {
-        const int r = idx / NTP, e = idx - r * NTP;
+    for (int idx = tid; idx < TA * NTP; idx += DTB) {   // consecutive rows per thread group: coalesced
+        const int e = idx / TA, r = idx - e * TA;
         const int gr = a0 + r;
         float vh = 0.f, vl = 0.f;
         if (gr < q) {
@@ -108,8 +126,8 @@ __global__ void __launch_bounds__(DTB) k_resid_df(DfArgs a) {
             vh = a.Sh[o];
             vl = a.Sl[o];
         }
-        s_h[idx] = vh;
-        s_l[idx] = vl;
+        s_h[r * NTP + e] = vh;
+        s_l[r * NTP + e] = vl;
     }
     const int b = b0 + tid;
     float th[NT][P], tl[NT][P];
@@ -122,52 +140,54 @@ __global__ void __launch_bounds__(DTB) k_resid_df(DfArgs a) {
             tl[i][l] = b < q ? a.Tl[o] : 0.f;
         }
     __syncthreads();
+    // ring[i][j] = t-pass value of term i for input row al + j of the current output row al
+    // (a register shift per row keeps the loop body one row long: small code)
     dfl ring[NT][P];
     auto tpass = [&](int lr, int slot) {
         const float* rh = xh + lr * WC + tid;   // staged column of input b + l - K is tid + l
         const float* rl = xl + lr * WC + tid;
 #pragma unroll
         for (int i = 0; i < NT; ++i) {
-            dfl w{0.f, 0.f};
+            dfl w = first_prod(th[i][0], tl[i][0], rh[0], rl[0]);
 #pragma unroll
-            for (int l = 0; l < P; ++l) acc_prod(w, th[i][l], tl[i][l], rh[l], rl[l]);
-            ring[i][slot] = w;
+            for (int l = 1; l < P; ++l) acc_prod(w, th[i][l], tl[i][l], rh[l], rl[l]);
+            ring[i][slot] = renorm(w);
         }
     };
 #pragma unroll
-    for (int r = 0; r < 2 * K; ++r) tpass(r, r);
+    for (int r = 0; r < 2 * K; ++r) tpass(r, r + 1);
     float rs = 0.f;
     double* Rg = a.R + (size_t)inst * a.bs;
 #pragma unroll 1
-    for (int m = 0; m < MR; ++m) {
+    for (int al = 0; al < TA; ++al) {
+        // the row's old R is loaded before the row's arithmetic (latency hidden behind it)
+        const int gr = a0 + al;
+        const bool out = gr < q && b < q;
+        const size_t o = (size_t)gr * a.ld + b;
+        const double rold = out ? Rg[o] : 0.0;
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int al = m * P + u;
-            tpass(al + 2 * K, (u + P - 1) % P);
-            const float* ch = s_h + al * NTP;
-            const float* cl = s_l + al * NTP;
-            // one accumulation chain per term (independent chains hide the FP32 latency)
-            dfl ys[NT];
+        for (int i = 0; i < NT; ++i)
 #pragma unroll
-            for (int i = 0; i < NT; ++i) ys[i] = dfl{0.f, 0.f};
+            for (int j = 0; j + 1 < P; ++j) ring[i][j] = ring[i][j + 1];
+        tpass(al + 2 * K, P - 1);
+        const float* ch = s_h + al * NTP;
+        const float* cl = s_l + al * NTP;
+        // one accumulation chain per term (independent chains hide the FP32 latency)
+        dfl ys[NT];
 #pragma unroll
-            for (int j = 0; j < P; ++j)
+        for (int i = 0; i < NT; ++i) ys[i] = first_prod(ch[i * P], cl[i * P], ring[i][0].h, ring[i][0].l);
 #pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    const dfl& w = ring[i][(u + j) % P];
-                    acc_prod(ys[i], ch[i * P + j], cl[i * P + j], w.h, w.l);
-                }
-            dfl y = ys[0];
+        for (int j = 1; j < P; ++j)
 #pragma unroll
-            for (int i = 1; i < NT; ++i) acc_prod(y, ys[i].h, ys[i].l, 1.f, 0.f);
-            const int gr = a0 + al;
-            if (gr < q && b < q) {
-                const size_t o = (size_t)gr * a.ld + b;
-                const double r = Rg[o] - ((double)y.h + (double)y.l);
-                Rg[o] = r;
-                const float rf = (float)r;
-                rs = fmaf(rf, rf, rs);
-            }
+            for (int i = 0; i < NT; ++i) acc_prod(ys[i], ch[i * P + j], cl[i * P + j], ring[i][j].h, ring[i][j].l);
+        dfl y = ys[0];
+#pragma unroll
+        for (int i = 1; i < NT; ++i) acc_df(y, ys[i]);
+        if (out) {
+            const double r = rold - ((double)y.h + (double)y.l);
+            Rg[o] = r;
+            const float rf = (float)r;
+            rs = fmaf(rf, rf, rs);
         }
     }
     double v = (double)rs;
@@ -182,9 +202,6 @@ __global__ void __launch_bounds__(DTB) k_resid_df(DfArgs a) {
         a.partial[(size_t)inst * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
 }
-
-template <int K>
-constexpr int df_rows() { return DGeo<K>::TA; }
 
 template <int K, int NT>
 mofem_status launch_df_t(const DfArgs& a, int batch, int* nblk, cudaStream_t st) {
@@ -214,19 +231,17 @@ mofem_status df_nt(int nt, const DfArgs& a, int batch, int* nblk, cudaStream_t s
 
 int residual_update_df_ctas(int K, int q) {
     if (K < 1 || K > 3) return 0;
-    const int ta = K == 1 ? df_rows<1>() : K == 2 ? df_rows<2>() : df_rows<3>();
-    return ((q + DTB - 1) / DTB) * ((q + ta - 1) / ta);
+    return ((q + DTB - 1) / DTB) * ((q + DGeo<1>::TA - 1) / DGeo<1>::TA);
 }
 
 // Forms served: the ring and the T coefficients in registers (NT * (2K+1) <= 40,
 // as the packed FP32 apply); others return MOFEM_ERR_UNSUPPORTED and the caller
 // recomputes the residual in FP64.
-mofem_status launch_residual_update_df(const mofem_ctx* c, const float* hi, const float* lo, const float* Qpend,
-                                       const float* err, double* R, double* partial, int* nblk, cudaStream_t st) {
+mofem_status launch_residual_update_df(const mofem_ctx* c, const float* dh, const float* dl, double* R,
+                                       double* partial, int* nblk, cudaStream_t st) {
     if (c->NT * (2 * c->K + 1) > 40 || !c->Sdf || !c->Tdf) return MOFEM_ERR_UNSUPPORTED;
     DfArgs a{};
-    a.hi = hi; a.lo = lo; a.qp = Qpend; a.err = err;
-    a.sc = c->d_sc;
+    a.dh = dh; a.dl = dl;
     const long long sp = (long long)c->batch * c->NT * c->P * c->q;   // S plane size
     const long long tp = (long long)c->NT * c->P * c->q;              // T plane size
     a.Sh = c->Sdf; a.Sl = c->Sdf + sp; a.s_bs = (long long)c->NT * c->P * c->q;

@@ -521,42 +521,46 @@ __global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const d
 // U64 += d with d = hi + lo (+ alpha_pend Q_pend, the last even iteration's term
 // when the correction is accumulated lazily) at the end of an inner solve of the
 // mixed form; the pair is cleared before the next inner solve starts.  d is formed
-// in FP64 and added with one rounding; with `err` non-null the rounding error
-// (U + d) - fl(U + d), exact by TwoSum, is written as FP32 (|err| <= ulp(U) / 2)
-// so that a residual update can account for it.  16-byte vectors: n % 4 == 0.
-__device__ __forceinline__ double fold_one(double u, float h, float l, double ap, float q, float* e) {
+// in FP64 and added with one rounding.  With `write_d` the pair is overwritten by
+// the step actually taken, d - err with err = (U + d) - fl(U + d) exact by TwoSum,
+// as a double-float (hi, lo): a residual update R -= L(hi + lo) then tracks
+// B - L(U) of the stored iterate.  16-byte vectors: n % 4 == 0.
+__device__ __forceinline__ double fold_one(double u, float& h, float& l, double ap, float q, bool write_d) {
     double d = (double)h + (double)l;
     if (ap != 0.0) d = fma(ap, (double)q, d);
     const double s = u + d;
-    if (e) {
+    if (write_d) {
         const double v = s - u;
-        *e = (float)((u - (s - v)) + (d - v));
+        const double taken = d - ((u - (s - v)) + (d - v));   // = s - u exactly, up to one rounding of d's size
+        h = (float)taken;
+        l = (float)(taken - (double)h);
     }
     return s;
 }
 
-__global__ void k_fold_df(double* U, long long bs, const float* hi, const float* lo, long long n,
-                          const PcgScalars* sc, const float* Qpend, float* err) {
+__global__ void k_fold_df(double* U, long long bs, float* hi, float* lo, long long n, const PcgScalars* sc,
+                          const float* Qpend, int write_d) {
     const int inst = blockIdx.y;
     const double ap = sc ? sc[inst].alpha_pend : 0.0;
     double2* U2 = reinterpret_cast<double2*>(U + (size_t)inst * bs);
-    const float4* h4 = reinterpret_cast<const float4*>(hi + (size_t)inst * bs);
-    const float4* l4 = reinterpret_cast<const float4*>(lo + (size_t)inst * bs);
+    float4* h4 = reinterpret_cast<float4*>(hi + (size_t)inst * bs);
+    float4* l4 = reinterpret_cast<float4*>(lo + (size_t)inst * bs);
     const float4* q4 = reinterpret_cast<const float4*>(Qpend + (size_t)inst * bs);
-    float4* e4 = err ? reinterpret_cast<float4*>(err + (size_t)inst * bs) : nullptr;
     const long long nv = n / 4;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
-        const float4 h = h4[i], l = l4[i];
+        float4 h = h4[i], l = l4[i];
         const float4 q = ap != 0.0 ? q4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         double2 a = U2[2 * i], b = U2[2 * i + 1];
-        float4 ev;
-        a.x = fold_one(a.x, h.x, l.x, ap, q.x, e4 ? &ev.x : nullptr);
-        a.y = fold_one(a.y, h.y, l.y, ap, q.y, e4 ? &ev.y : nullptr);
-        b.x = fold_one(b.x, h.z, l.z, ap, q.z, e4 ? &ev.z : nullptr);
-        b.y = fold_one(b.y, h.w, l.w, ap, q.w, e4 ? &ev.w : nullptr);
+        a.x = fold_one(a.x, h.x, l.x, ap, q.x, write_d);
+        a.y = fold_one(a.y, h.y, l.y, ap, q.y, write_d);
+        b.x = fold_one(b.x, h.z, l.z, ap, q.z, write_d);
+        b.y = fold_one(b.y, h.w, l.w, ap, q.w, write_d);
         U2[2 * i] = a;
         U2[2 * i + 1] = b;
-        if (e4) e4[i] = ev;
+        if (write_d) {
+            h4[i] = h;
+            l4[i] = l;
+        }
     }
 }
 
@@ -698,10 +702,10 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
 }
 
 mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, const PcgScalars* sc,
-                            const float* Qpend, float* err, cudaStream_t st) {
+                            const float* Qpend, bool write_d, cudaStream_t st) {
     if (bs % 4 != 0) return MOFEM_ERR_INVALID_ARG;   // internal layout: ld is a multiple of 64
     dim3 grid(592, batch);
-    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend, err);
+    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend, write_d ? 1 : 0);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

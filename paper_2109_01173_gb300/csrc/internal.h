@@ -165,11 +165,10 @@ struct ApplyPcgArgs {
 };
 mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const double* beta, const double* rz,
                            void* Q, void* LQ, int ld, double* alpha, bool fp64, cudaStream_t st);
-// R -= L(d) in double-float arithmetic, d = hi + lo + alpha_pend * Qpend - err per
-// instance (internal layout; err may be null), and per-CTA FP64 partials of ||R||^2
-// (nblk per instance).
-mofem_status launch_residual_update_df(const mofem_ctx* c, const float* hi, const float* lo, const float* Qpend,
-                                       const float* err, double* R, double* partial, int* nblk, cudaStream_t st);
+// R -= L(d) in double-float arithmetic, d = dh + dl per instance (internal layout),
+// and per-CTA FP64 partials of ||R||^2 (nblk per instance).
+mofem_status launch_residual_update_df(const mofem_ctx* c, const float* dh, const float* dl, double* R,
+                                       double* partial, int* nblk, cudaStream_t st);
 int residual_update_df_ctas(int K, int q);   // partials per instance of the above
 mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, const CUtensorMap& mQ,
                               const CUtensorMap* mS,

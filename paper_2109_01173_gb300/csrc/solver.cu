@@ -33,7 +33,7 @@ mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo
                                bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st,
                                bool use_scalars = true, const void* Qprev = nullptr, int lazy_phase = -1);
 mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, const PcgScalars* sc,
-                            const float* Qpend, float* err, cudaStream_t st);
+                            const float* Qpend, bool write_d, cudaStream_t st);
 mofem_status launch_scale_copy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
                                  int rows, int cols, int batch, double scale, cudaStream_t st);
 mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
@@ -641,11 +641,10 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             }
             // R after this step: recomputed in FP64 after a first step from zero (cancellation
             // against B), else updated R -= L(d - err) in double-float arithmetic, err the
-            // fold's rounding of U + d (the R32 slot is free once the inner solve ended)
+            // fold's rounding of U + d (the fold leaves d - err in the correction pair)
             const bool upd = df_update && (outer >= 1 || !zero_guess);
-            float* err = upd ? w32(c, W32_R) : nullptr;
             // even iterations leave alpha Q_a pending (lazy correction): the fold adds it
-            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, c->d_sc, w32(c, W32_QA), err, st));
+            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, c->d_sc, w32(c, W32_QA), upd, st));
             int it = 0;
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
@@ -654,8 +653,7 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             int nblk = 0;
             mofem_status du = MOFEM_ERR_UNSUPPORTED;
             if (upd)
-                du = launch_residual_update_df(c, w32(c, W32_U), w32(c, W32_ULO), w32(c, W32_QA), err, c->R64,
-                                               e.res_part, &nblk, st);
+                du = launch_residual_update_df(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, e.res_part, &nblk, st);
             if (du == MOFEM_OK) {
                 MOFEM_TRY(sum_partials(e.res_part, nblk, B, rr, st));
             } else {
@@ -853,8 +851,8 @@ mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int re
     if (kernel == 8) {   // double-float residual update of a refinement step
         int nblk = 0;
         for (int r = 0; r < reps; ++r)
-            MOFEM_TRY(launch_residual_update_df(c, w32(c, W32_U), w32(c, W32_ULO), w32(c, W32_QA), w32(c, W32_R),
-                                                c->R64, extras()[c].res_part, &nblk, st));
+            MOFEM_TRY(launch_residual_update_df(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, extras()[c].res_part,
+                                                &nblk, st));
         return MOFEM_OK;
     }
     return MOFEM_ERR_INVALID_ARG;
