@@ -530,8 +530,12 @@ __device__ __forceinline__ double fold_one(double u, float& h, float& l, double 
     if (ap != 0.0) d = fma(ap, (double)q, d);
     const double s = u + d;
     if (write_d) {
-        const double v = s - u;
-        const double taken = d - ((u - (s - v)) + (d - v));   // = s - u exactly, up to one rounding of d's size
+        // the step taken, s - u: exact when |d| <= |u| (Fast2Sum), else d minus the TwoSum error
+        double taken = s - u;
+        if (!(fabs(d) <= fabs(u))) {
+            const double v = s - u;
+            taken = d - ((u - (s - v)) + (d - v));
+        }
         h = (float)taken;
         l = (float)(taken - (double)h);
     }

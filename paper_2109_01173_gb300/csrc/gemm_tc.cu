@@ -26,6 +26,8 @@
 // times out as well).
 #include "internal.h"
 
+#include <type_traits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cstdio>
@@ -51,6 +53,8 @@ struct GemmArgs {
     int div_product;       // EPI_DIV divisor lambda_i * mu_j (product preconditioner) instead of lambda_i + mu_j
     const PcgScalars* scl; // FP16 operands: the G4 output is divided by scl[inst].rscale
     int* status;
+    int pad_ok;            // the output's row padding (columns N .. round_up(N, 32) - 1 <= out_ld) may be
+                           // written with zeros: the ragged last chunk then takes 16-byte stores
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -75,24 +79,6 @@ __device__ __forceinline__ unsigned long long gtimer() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait for the phase of the given parity; false on timeout.
-__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-    if (mbar_try(a, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try(a, parity)) {
-        if (gtimer() - t0 > WAIT_LIMIT_NS) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
-                                            int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
 // Shared-memory matrix descriptor: K-major tile written by TMA with 128-byte
 // swizzle (8-row x 128-byte atoms, 1024 bytes apart), tcgen05 descriptor version 1.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
@@ -155,78 +141,88 @@ __device__ __forceinline__ bool pwait(uint32_t a, uint32_t parity, volatile int*
     return true;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-// Epilogue of one 32-column chunk held by this thread (row m): divide, store
-// (16-byte vectors when aligned), and the <R, Z> accumulation of G4.
+// Epilogue of one 32-column chunk held by this thread (row m): divide (G2), unscale
+// and <R, Z> accumulation (G4), store (16-byte vectors when aligned).  Specialised
+// at compile time on the epilogue kind and the output type (OUTK 0 FP32, 1 BF16,
+// 2 FP16): one small code path per GEMM (a generic epilogue with every path inlined
+// cost 10-20% of the GEMM's time).
+template <int EPI, int OUTK>
 __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, int nb, float (&v)[32], float mu_m,
-                                          double& acc) {
+                                          float inv_scale, double& acc) {
     const size_t obase = (size_t)inst * g.out_bs + (size_t)m * g.out_ld;
-    const bool vec_ok = (g.out_ld % 8) == 0;
-    if (g.epi == EPI_DIV) {
-        const float* lam = g.lam + (size_t)inst * g.lam_bs + nb;
+    if constexpr (EPI == EPI_DIV) {
+        // lambda of the chunk's 32 columns: 16-byte read-only loads (the rows of lam are
+        // ld-strided, ld a multiple of 64, and nb a multiple of 32: 128-byte aligned)
+        const float4* lam4 = reinterpret_cast<const float4*>(g.lam + (size_t)inst * g.lam_bs + nb);
+        float lam[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 t = __ldg(lam4 + j);
+            lam[4 * j] = t.x; lam[4 * j + 1] = t.y; lam[4 * j + 2] = t.z; lam[4 * j + 3] = t.w;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], g.div_product ? lam[j] * mu_m : lam[j] + mu_m);
     }
-    if (g.epi == EPI_Z && g.scl) {
-        const float inv = (float)(1.0 / g.scl[inst].rscale);
+    if constexpr (EPI == EPI_Z) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] *= inv;
+        for (int j = 0; j < 32; ++j) v[j] *= inv_scale;
     }
-    const bool full = vec_ok && nb + 32 <= g.N;
-    if (g.out_bf16 == 2) {
-        // FP16 intermediates: saturate instead of overflowing to inf
+    // ragged last chunk: zero the columns >= N and store whole vectors where the padding
+    // may be written (scalar sub-word stores into one sector serialise: 10-15% of a GEMM)
+    const bool fits = nb + 32 <= g.N;
+    const bool padw = !fits && g.pad_ok && nb + 32 <= g.out_ld;
+    if (padw) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = fminf(fmaxf(v[j], -65504.f), 65504.f);
-        __half* o = reinterpret_cast<__half*>(g.out) + obase + nb;
-        if (full) {
+        for (int j = 0; j < 32; ++j)
+            if (nb + j >= g.N) v[j] = 0.f;
+    }
+    if constexpr (OUTK != 0) {
+        const bool full = (g.out_ld % 8) == 0 && (fits || padw);
+        if constexpr (OUTK == 2) {   // FP16 intermediates: saturate instead of overflowing to inf
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-                uint4 pk;
-                __half2 p0 = __floats2half2_rn(v[j], v[j + 1]);
-                __half2 p1 = __floats2half2_rn(v[j + 2], v[j + 3]);
-                __half2 p2 = __floats2half2_rn(v[j + 4], v[j + 5]);
-                __half2 p3 = __floats2half2_rn(v[j + 6], v[j + 7]);
-                pk.x = *reinterpret_cast<uint32_t*>(&p0);
-                pk.y = *reinterpret_cast<uint32_t*>(&p1);
-                pk.z = *reinterpret_cast<uint32_t*>(&p2);
-                pk.w = *reinterpret_cast<uint32_t*>(&p3);
-                *reinterpret_cast<uint4*>(o + j) = pk;
-            }
-        } else {
-            for (int j = 0; j < 32 && nb + j < g.N; ++j) o[j] = __float2half_rn(v[j]);
+            for (int j = 0; j < 32; ++j) v[j] = fminf(fmaxf(v[j], -65504.f), 65504.f);
         }
-    } else if (g.out_bf16) {
-        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(g.out) + obase + nb;
+        using OT = typename std::conditional<OUTK == 2, __half, __nv_bfloat16>::type;
+        OT* o = reinterpret_cast<OT*>(g.out) + obase + nb;
         if (full) {
 #pragma unroll
             for (int j = 0; j < 32; j += 8) {
-                uint4 pk;
-                __nv_bfloat162 p0 = __floats2bfloat162_rn(v[j], v[j + 1]);
-                __nv_bfloat162 p1 = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
-                __nv_bfloat162 p2 = __floats2bfloat162_rn(v[j + 4], v[j + 5]);
-                __nv_bfloat162 p3 = __floats2bfloat162_rn(v[j + 6], v[j + 7]);
-                pk.x = *reinterpret_cast<uint32_t*>(&p0);
-                pk.y = *reinterpret_cast<uint32_t*>(&p1);
-                pk.z = *reinterpret_cast<uint32_t*>(&p2);
-                pk.w = *reinterpret_cast<uint32_t*>(&p3);
-                *reinterpret_cast<uint4*>(o + j) = pk;
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if constexpr (OUTK == 2) {
+                        __half2 t = __floats2half2_rn(v[j + 2 * e], v[j + 2 * e + 1]);
+                        w[e] = *reinterpret_cast<uint32_t*>(&t);
+                    } else {
+                        __nv_bfloat162 t = __floats2bfloat162_rn(v[j + 2 * e], v[j + 2 * e + 1]);
+                        w[e] = *reinterpret_cast<uint32_t*>(&t);
+                    }
+                }
+                *reinterpret_cast<uint4*>(o + j) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         } else {
-            for (int j = 0; j < 32 && nb + j < g.N; ++j) o[j] = __float2bfloat16_rn(v[j]);
+            for (int j = 0; j < 32 && nb + j < g.N; ++j) {
+                if constexpr (OUTK == 2) o[j] = __float2half_rn(v[j]);
+                else o[j] = __float2bfloat16_rn(v[j]);
+            }
         }
     } else {
         float* o = reinterpret_cast<float*>(g.out) + obase + nb;
-        const float* r = (g.epi == EPI_Z && g.R) ? g.R + (size_t)inst * g.r_bs + (size_t)m * g.r_ld + nb : nullptr;
+        const float* r = (EPI == EPI_Z && g.R) ? g.R + (size_t)inst * g.r_bs + (size_t)m * g.r_ld + nb : nullptr;
         float a32 = 0.f;   // FP32 within the 32-column chunk, FP64 across chunks
+        const bool full = (g.out_ld % 4) == 0 && (fits || (padw && (!r || nb + 32 <= g.r_ld)));
         if (full && (!r || (g.r_ld % 4) == 0)) {
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
                 *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                if (r) {
-                    const float4 rv = *reinterpret_cast<const float4*>(r + j);
+                if (EPI == EPI_Z && r) {
+                    float4 rv = *reinterpret_cast<const float4*>(r + j);
+                    if (!fits) {   // padding of R contributes nothing, whatever it holds
+                        if (nb + j >= g.N) rv.x = 0.f;
+                        if (nb + j + 1 >= g.N) rv.y = 0.f;
+                        if (nb + j + 2 >= g.N) rv.z = 0.f;
+                        if (nb + j + 3 >= g.N) rv.w = 0.f;
+                    }
                     a32 = fmaf(v[j], rv.x, a32);
                     a32 = fmaf(v[j + 1], rv.y, a32);
                     a32 = fmaf(v[j + 2], rv.z, a32);
@@ -236,10 +232,10 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, in
         } else {
             for (int j = 0; j < 32 && nb + j < g.N; ++j) {
                 o[j] = v[j];
-                if (r) a32 = fmaf(v[j], r[j], a32);
+                if (EPI == EPI_Z && r) a32 = fmaf(v[j], r[j], a32);
             }
         }
-        acc += (double)a32;
+        if constexpr (EPI == EPI_Z) acc += (double)a32;
     }
 }
 
@@ -311,9 +307,10 @@ __device__ __forceinline__ void commit2_mc(uint32_t mbar, uint16_t mask) {
         : "memory");
 }
 
-template <int KIND>
+template <int KIND, int EPI>
 __global__ void __launch_bounds__(P_THREADS, 1)
     k_gemm_2sm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
+    constexpr int OUTK = EPI == EPI_Z ? 0 : KIND;   // output type: FP32 (TF32 plans and Z), BF16, FP16
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     PBars2* pb = reinterpret_cast<PBars2*>(smem + ST2 * STAGE2_BYTES);
@@ -423,19 +420,20 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             const int m = m0 + warp * 32 + lane;
             const bool m_ok = m < g.M;
             float mu_m = 0.f;
-            if (g.epi == EPI_DIV && m_ok) mu_m = g.mu[m];
+            if (EPI == EPI_DIV && m_ok) mu_m = g.mu[m];
+            const float inv_scale = (EPI == EPI_Z && g.scl) ? (float)(1.0 / g.scl[inst].rscale) : 1.f;
             double acc = 0.0;
 #pragma unroll 1
             for (int c = 0; c < 256 / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256 + c * 32), v);
                 const int nb = n0 + c * 32;
-                if (m_ok && nb < g.N) epi_chunk(g, inst, m, nb, v, mu_m, acc);
+                if (m_ok && nb < g.N) epi_chunk<EPI, OUTK>(g, inst, m, nb, v, mu_m, inv_scale, acc);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(mapa_shared(bar_addr(&pb->tempty[b]), 0));
-            if (g.epi == EPI_Z && g.rz_part) {
+            if (EPI == EPI_Z && g.rz_part) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (lane == 0) pb->red[tl & 1][warp] = acc;
@@ -567,10 +565,11 @@ int num_sms() {
 
 constexpr int GEMM_CM = 2;   // CTAs per cluster: one tcgen05 CTA pair
 
-template <int KIND>
-mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g0, int batch, cudaStream_t st) {
+template <int KIND, int EPI>
+mofem_status launch_gemm_e(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g0, int batch,
+                           cudaStream_t st) {
     constexpr int CM = GEMM_CM;
-    auto kern = k_gemm_2sm<KIND>;
+    auto kern = k_gemm_2sm<KIND, EPI>;
     static int max_pairs = 0;
     const int smem = ST2 * STAGE2_BYTES + 1024 + (int)sizeof(PBars2) + 64;
     cudaLaunchConfig_t cfg = {};
@@ -602,6 +601,15 @@ mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const Gem
     cfg.gridDim = dim3(CM * pairs);
     MOFEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, mA, mB, g));
     return MOFEM_OK;
+}
+
+// Output type follows the operand kind (FP32 for TF32, BF16, FP16), except G4's FP32 Z.
+template <int KIND>
+mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch, cudaStream_t st) {
+    if (g.out_bf16 != (g.epi == EPI_Z ? 0 : KIND)) return MOFEM_ERR_INVALID_ARG;
+    if (g.epi == EPI_DIV) return launch_gemm_e<KIND, EPI_DIV>(mA, mB, g, batch, st);
+    if (g.epi == EPI_Z) return launch_gemm_e<KIND, EPI_Z>(mA, mB, g, batch, st);
+    return launch_gemm_e<KIND, EPI_STORE>(mA, mB, g, batch, st);
 }
 
 }  // namespace
@@ -680,6 +688,7 @@ mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaS
     g.status = c->d_status;
     g.lam = c->lam32; g.lam_bs = ld; g.mu = c->mu32; g.div_product = c->div_product;
     g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = which;
+    g.pad_ok = 1;   // internal buffers, zero padding
     void* outs[4] = {p.X1T, p.WT, p.Y, Z};
     const int epis[4] = {EPI_STORE, EPI_DIV, EPI_STORE, EPI_Z};
     g.out = outs[idx]; g.epi = epis[idx];
@@ -691,7 +700,7 @@ mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaS
 // Z = P^{-1}(R) with R already in p.Rop (rounded operand).  R32 (FP32, same
 // layout as Z) feeds the fused <R, Z> partials when rz_partial != nullptr.
 mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z, int z_ld,
-                        long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st) {
+                        long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st, bool z_internal) {
     const TcPlan& p = c->tc[which];
     const int q = c->q, ld = c->ld;
     const int bk = which == 0 ? 32 : 64;
@@ -709,6 +718,7 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
     g.out_ld = ld;
     g.out_bf16 = which;
     g.scl = which == 2 ? c->d_sc : nullptr;
+    g.pad_ok = 1;   // G1..G3 write internal intermediates
     auto run = [&](int i) -> mofem_status { return launch_gemm_kind(which, p.mA[i], p.mB[i], g, c->batch, st); };
     // G1: X1T = (R Q2)^T
     g.out = p.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
@@ -721,6 +731,7 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
     MOFEM_TRY(run(2));
     // G4: Z = Y Q2^T (+ <R, Z> partials)
     g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 0; g.b_shared = 1;
+    g.pad_ok = z_internal ? 1 : 0;   // a caller's Z keeps its padding untouched
     g.R = R32; g.r_bs = r_bs; g.r_ld = r_ld; g.rz_part = rz_partial;
     g.counter = c->d_ctr + 2 * c->batch;
     g.flex = 1;
@@ -749,6 +760,7 @@ mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z
     g.status = c->d_status;
     g.lam = c->lam32; g.lam_bs = c->ld; g.mu = c->mu32; g.div_product = c->div_product;
     g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = 1;
+    g.pad_ok = 1;   // the library's own scratch array
     g.out = b.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
     MOFEM_TRY(launch_gemm<1>(mA[0], mB[0], g, B, st));
     g.out = b.WT; g.epi = EPI_DIV; g.a_shared = 0; g.b_shared = 0;
@@ -756,5 +768,6 @@ mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z
     g.out = b.Y; g.epi = EPI_STORE;
     MOFEM_TRY(launch_gemm<1>(mA[2], mB[2], g, B, st));
     g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 0; g.b_shared = 1;
+    g.pad_ok = 0;   // the caller's Z
     return launch_gemm<1>(mA[3], mB[3], g, B, st);
 }

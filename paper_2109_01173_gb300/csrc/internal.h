@@ -207,8 +207,10 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
 // Four GEMMs of the reduced-approach preconditioner on the operand already in
 // plan.Rop; writes Z (FP32) and, if rz_partial, the <R, Z> partials (R32 = R in FP32).
 mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st);
+// z_internal: Z is a library buffer whose row padding may be written (with zeros)
 mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z,
-                        int z_ld, long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st);
+                        int z_ld, long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st,
+                        bool z_internal = false);
 int tc_rz_ctas(const mofem_ctx* c);
 mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaStream_t st);
 struct TcBuffers {   // caller-provided BF16 buffers of the preconditioner GEMMs

@@ -336,7 +336,8 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     } else {
         if (which == 0)   // TF32 GEMMs read their own FP32 operand copy of R
             MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[0].Rop, 0, bs, c->ld, c->q, c->q, c->batch, st));
-        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st));
+        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st,
+                             true));
     }
     return MOFEM_OK;
 }
@@ -456,7 +457,8 @@ static mofem_status run_inner(mofem_ctx* c, mofem_precision prec, int max_iter, 
         else
             MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[which].Rop, conv_kind_of_plan(which), bs, c->ld, c->q,
                                      c->q, c->batch, st));
-        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st));
+        MOFEM_TRY(tc_precond(c, which, (const float*)R, bs, c->ld, (float*)Z, c->ld, bs, e.rz_slots[0], c->d_sc, st,
+                             true));
     }
     const int pi = (int)prec;
     bool stepped = (c->opts.flags & MOFEM_FLAG_HOST_LOOP) || c->host_stepped[pi];
