@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MO-PCG solves/s and ms/iter, P2 N=2049 (mixed vs FP64 GPU form, rel.err<=1e-8)"
 # DRAM bytes per preconditioner-GEMM launch at P2 2049 x 4 (ncu capture of the current kernel;
 # set to None whenever k_gemm_2sm changes until it is captured again)
-GEMM_DRAM_BYTES = 59.9e6
+GEMM_DRAM_BYTES = 60.0e6
 UNIT = "solves/s"
 
 
