@@ -24,6 +24,12 @@
 // rows (shifted by one per row), the s-pass reads the row's coefficients as
 // shared-memory broadcasts.
 // Output: R64 updated in place and one FP64 partial of ||R64||^2 per CTA.
+//
+// The same kernel in its second mode evaluates the right-hand side B = M_s F M_t^T
+// (Sec. 5, operator R~; one mass term, FP64 nodal F with an index offset from the
+// trimmed rows to the node rows) from FP64 input split to double-float on load: the
+// mass products have no cancellation, so B comes out to ~2^-46 of each entry
+// without the FP64 pipe.
 #include "internal.h"
 
 namespace {
@@ -38,8 +44,13 @@ struct DGeo {
     static constexpr int WC = DTB + 2 * K;
 };
 
+enum { DF_RESID = 0, DF_APPLY64 = 1 };
+
 struct DfArgs {
-    const float* dh; const float* dl;                    // the step, [batch][q][ld]
+    const float* dh; const float* dl;                    // the step, [batch][q][ld] (DF_RESID)
+    const double* X; long long x_bs; int x_ld;           // FP64 input (DF_APPLY64)
+    int rows_in, cols_in, off;                           // input extent; input index = output index + off
+    double* Y; long long y_bs; int y_ld;                 // output (DF_APPLY64)
     const float* Sh; const float* Sl; long long s_bs;    // S tables, hi / lo planes, [batch][NT][P][q]
     const float* Th; const float* Tl;                    // T tables, hi / lo planes, [NT][P][q]
     double* R; long long bs; int ld, q;
@@ -86,7 +97,7 @@ __device__ __forceinline__ dfl renorm(dfl s) {
     return dfl{h, s.l - (h - s.h)};
 }
 
-template <int K, int NT>
+template <int K, int NT, int MODE>
 __global__ void __launch_bounds__(DTB, NT * (2 * K + 1) <= 25 ? 4 : 3) k_resid_df(DfArgs a) {
     using G = DGeo<K>;
     constexpr int P = G::P, TA = G::TA, HR = G::HR, WC = G::WC, NTP = NT * P;
@@ -99,22 +110,41 @@ __global__ void __launch_bounds__(DTB, NT * (2 * K + 1) <= 25 ? 4 : 3) k_resid_d
     const int tid = threadIdx.x, inst = blockIdx.z;
     const int a0 = blockIdx.y * TA, b0 = blockIdx.x * DTB;
     const int q = a.q;
-    const float* dh = a.dh + (size_t)inst * a.bs;
-    const float* dl = a.dl + (size_t)inst * a.bs;
-    // step tile with halo, zero outside the domain
-    for (int r = tid / 32; r < HR; r += DTB / 32) {
-        const int gr = a0 - K + r;
-        const bool rok = gr >= 0 && gr < q;
-        for (int cc = tid & 31; cc < WC; cc += 32) {
-            const int gc = b0 - K + cc;
-            float vh = 0.f, vl = 0.f;
-            if (rok && gc >= 0 && gc < q) {
-                const size_t o = (size_t)gr * a.ld + gc;
-                vh = dh[o];
-                vl = dl[o];
+    // input tile with halo (double-float), zero outside the input
+    if constexpr (MODE == DF_RESID) {
+        const float* dh = a.dh + (size_t)inst * a.bs;
+        const float* dl = a.dl + (size_t)inst * a.bs;
+        for (int r = tid / 32; r < HR; r += DTB / 32) {
+            const int gr = a0 - K + r;
+            const bool rok = gr >= 0 && gr < q;
+            for (int cc = tid & 31; cc < WC; cc += 32) {
+                const int gc = b0 - K + cc;
+                float vh = 0.f, vl = 0.f;
+                if (rok && gc >= 0 && gc < q) {
+                    const size_t o = (size_t)gr * a.ld + gc;
+                    vh = dh[o];
+                    vl = dl[o];
+                }
+                xh[r * WC + cc] = vh;
+                xl[r * WC + cc] = vl;
             }
-            xh[r * WC + cc] = vh;
-            xl[r * WC + cc] = vl;
+        }
+    } else {
+        const double* X = a.X + (size_t)inst * a.x_bs;
+        for (int r = tid / 32; r < HR; r += DTB / 32) {
+            const int gr = a0 - K + r + a.off;
+            const bool rok = gr >= 0 && gr < a.rows_in;
+            for (int cc = tid & 31; cc < WC; cc += 32) {
+                const int gc = b0 - K + cc + a.off;
+                float vh = 0.f, vl = 0.f;
+                if (rok && gc >= 0 && gc < a.cols_in) {
+                    const double x = X[(size_t)gr * a.x_ld + gc];
+                    vh = (float)x;
+                    vl = (float)(x - (double)vh);
+                }
+                xh[r * WC + cc] = vh;
+                xl[r * WC + cc] = vl;
+            }
         }
     }
     for (int idx = tid; idx < TA * NTP; idx += DTB) {   // consecutive rows per thread group: coalesced
@@ -157,14 +187,15 @@ __global__ void __launch_bounds__(DTB, NT * (2 * K + 1) <= 25 ? 4 : 3) k_resid_d
 #pragma unroll
     for (int r = 0; r < 2 * K; ++r) tpass(r, r + 1);
     float rs = 0.f;
-    double* Rg = a.R + (size_t)inst * a.bs;
+    double* Rg = MODE == DF_RESID ? a.R + (size_t)inst * a.bs : a.Y + (size_t)inst * a.y_bs;
+    const int rld = MODE == DF_RESID ? a.ld : a.y_ld;
 #pragma unroll 1
     for (int al = 0; al < TA; ++al) {
         // the row's old R is loaded before the row's arithmetic (latency hidden behind it)
         const int gr = a0 + al;
         const bool out = gr < q && b < q;
-        const size_t o = (size_t)gr * a.ld + b;
-        const double rold = out ? Rg[o] : 0.0;
+        const size_t o = (size_t)gr * rld + b;
+        const double rold = (MODE == DF_RESID && out) ? Rg[o] : 0.0;
 #pragma unroll
         for (int i = 0; i < NT; ++i)
 #pragma unroll
@@ -184,12 +215,17 @@ __global__ void __launch_bounds__(DTB, NT * (2 * K + 1) <= 25 ? 4 : 3) k_resid_d
 #pragma unroll
         for (int i = 1; i < NT; ++i) acc_df(y, ys[i]);
         if (out) {
-            const double r = rold - ((double)y.h + (double)y.l);
-            Rg[o] = r;
-            const float rf = (float)r;
-            rs = fmaf(rf, rf, rs);
+            if constexpr (MODE == DF_RESID) {
+                const double r = rold - ((double)y.h + (double)y.l);
+                Rg[o] = r;
+                const float rf = (float)r;
+                rs = fmaf(rf, rf, rs);
+            } else {
+                Rg[o] = (double)y.h + (double)y.l;
+            }
         }
     }
+    if constexpr (MODE != DF_RESID) return;
     double v = (double)rs;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -203,18 +239,19 @@ __global__ void __launch_bounds__(DTB, NT * (2 * K + 1) <= 25 ? 4 : 3) k_resid_d
     }
 }
 
-template <int K, int NT>
+template <int K, int NT, int MODE = DF_RESID>
 mofem_status launch_df_t(const DfArgs& a, int batch, int* nblk, cudaStream_t st) {
     using G = DGeo<K>;
     const size_t smem = sizeof(float) * (2 * (size_t)G::HR * G::WC + 2 * (size_t)G::TA * NT * G::P);
     static bool attr = false;
     if (!attr) {
-        MOFEM_CUDA_TRY(cudaFuncSetAttribute(k_resid_df<K, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MOFEM_CUDA_TRY(
+            cudaFuncSetAttribute(k_resid_df<K, NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     dim3 grid((a.q + DTB - 1) / DTB, (a.q + G::TA - 1) / G::TA, batch);
-    *nblk = grid.x * grid.y;
-    k_resid_df<K, NT><<<grid, DTB, smem, st>>>(a);
+    if (nblk) *nblk = grid.x * grid.y;
+    k_resid_df<K, NT, MODE><<<grid, DTB, smem, st>>>(a);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }
@@ -253,5 +290,23 @@ mofem_status launch_residual_update_df(const mofem_ctx* c, const float* dh, cons
         case 2: return df_nt<2>(c->NT, a, c->batch, nblk, st);
         case 3: return df_nt<3>(c->NT, a, c->batch, nblk, st);
         default: return MOFEM_ERR_UNSUPPORTED;
+    }
+}
+
+mofem_status launch_rhs_df(const mofem_ctx* c, const double* F, double* B, long long b_bs, int b_ld, cudaStream_t st) {
+    if (!c->Srdf || !c->Trdf || c->K < 1 || c->K > 4) return MOFEM_ERR_UNSUPPORTED;
+    DfArgs a{};
+    a.X = F; a.x_bs = (long long)c->n * c->n; a.x_ld = c->n;
+    a.rows_in = a.cols_in = c->n; a.off = c->off;
+    a.Y = B; a.y_bs = b_bs; a.y_ld = b_ld;
+    const long long sp = (long long)c->batch * c->P * c->q, tp = (long long)c->P * c->q;
+    a.Sh = c->Srdf; a.Sl = c->Srdf + sp; a.s_bs = (long long)c->P * c->q;
+    a.Th = c->Trdf; a.Tl = c->Trdf + tp;
+    a.q = c->q;
+    switch (c->K) {
+        case 1: return launch_df_t<1, 1, DF_APPLY64>(a, c->batch, nullptr, st);
+        case 2: return launch_df_t<2, 1, DF_APPLY64>(a, c->batch, nullptr, st);
+        case 3: return launch_df_t<3, 1, DF_APPLY64>(a, c->batch, nullptr, st);
+        default: return launch_df_t<4, 1, DF_APPLY64>(a, c->batch, nullptr, st);
     }
 }

@@ -72,6 +72,8 @@ struct mofem_ctx {
     float* S2dup = nullptr;   // [batch][q][2*SR2] FP32 S rows, each coefficient twice (packed apply)
     float* Sdf = nullptr;     // plain S tables as double-float: hi plane then lo plane, each [batch][NT][P][q]
     float* Tdf = nullptr;     // plain T tables as double-float: hi plane then lo plane, each [NT][P][q]
+    float* Srdf = nullptr;    // right-hand-side mass factors as double-float: [hi | lo] of [batch][P][q]
+    float* Trdf = nullptr;    // and [hi | lo] of [P][q]
     int s2_row = 0;           // floats per S2dup row
     double* T64 = nullptr;  float* T32 = nullptr;   // [NT][P][q]
     double* Sr64 = nullptr; double* Tr64 = nullptr; // RHS mass factors: [batch][P][q], [P][q] (offset off)
@@ -170,6 +172,9 @@ mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const do
 mofem_status launch_residual_update_df(const mofem_ctx* c, const float* dh, const float* dl, double* R,
                                        double* partial, int* nblk, cudaStream_t st);
 int residual_update_df_ctas(int K, int q);   // partials per instance of the above
+// B = M_s F M_t^T (right-hand side; F n x n nodal, ld n, FP64; B q x q, b_ld) in double-float
+// arithmetic; MOFEM_ERR_UNSUPPORTED where the tables are missing.
+mofem_status launch_rhs_df(const mofem_ctx* c, const double* F, double* B, long long b_bs, int b_ld, cudaStream_t st);
 mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, const CUtensorMap& mQ,
                               const CUtensorMap* mS,
                               const ApplyPcgArgs& a, int batch, cudaStream_t st);

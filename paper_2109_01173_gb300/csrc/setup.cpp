@@ -375,6 +375,8 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
         };
         MOFEM_TRY(split(Sh, &c->Sdf));   // [hi | lo] planes of [batch][NT][P][q]
         MOFEM_TRY(split(Th, &c->Tdf));   // [hi | lo] planes of [NT][P][q]
+        MOFEM_TRY(split(Srh, &c->Srdf)); // [hi | lo] planes of [batch][P][q] (right-hand side)
+        MOFEM_TRY(split(Trh, &c->Trdf)); // [hi | lo] planes of [P][q]
     }
 
     // --- upload tables (difference form: row sum in the diagonal slot) -------------
@@ -521,7 +523,7 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
 }
 
 void mofem_free(mofem_ctx* c) {
-    void* ptrs[] = {c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
+    void* ptrs[] = {c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->Srdf, c->Trdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
                     c->lam32, c->mu32, c->w64, c->w32, c->Bm64, c->R64, c->d_part, c->d_sc, c->d_status,
                     c->d_red};
     for (void* p : ptrs) cudaFree(p);

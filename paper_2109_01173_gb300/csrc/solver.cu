@@ -201,6 +201,9 @@ mofem_status op_apply(mofem_ctx* c, bool fp64, const void* X, long long x_bs, in
 }
 
 mofem_status op_rhs(mofem_ctx* c, const double* F, double* Bout, long long b_bs, int b_ld, cudaStream_t st) {
+    // double-float evaluation (HBM-bound; the FP64 pipe of this GPU is slow), FP64 otherwise
+    const mofem_status sd = launch_rhs_df(c, F, Bout, b_bs, b_ld, st);
+    if (sd != MOFEM_ERR_UNSUPPORTED) return sd;
     ApplyArgs a{};
     a.X = F; a.x_bs = (long long)c->n * c->n; a.x_ld = c->n;
     a.Y = Bout; a.y_bs = b_bs; a.y_ld = b_ld;
