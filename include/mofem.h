@@ -214,10 +214,13 @@ mofem_status mofem_imex_step_tol(mofem_handle h, double d_u, double tau, const d
  *   dd_u[i] = -tau <Y, A~ U_np1>_F   (this step's contribution to dJ/dd_u).
  * For a loss J(U_N) start from Lam_N = dJ/dU_N and go n = N-1 .. 0 with U_np1 the
  * forward state after step n; Lam_0 = dJ/dU_0.  Lam_np1, U_np1, Lam_n: q x q per
- * instance (ld q), FP64, device; Lam_n must not alias Lam_np1.  dd_u: host array
- * of `batch` doubles.  The handle must have gamma = 1/(d_u tau).  Synchronises. */
+ * instance (ld q), FP64, device; Lam_n must not alias Lam_np1.  Y: q x q per
+ * instance (ld q), FP64, device, in: initial guess of the solve, out: S^{-1} Lam_np1;
+ * NULL starts from zero in a library buffer.  Passing the previous step's Y warm-
+ * starts the solve (successive adjoint solutions differ by O(d_u tau)).  dd_u: host
+ * array of `batch` doubles.  The handle must have gamma = 1/(d_u tau).  Synchronises. */
 mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, const double* Lam_np1,
-                                     const double* U_np1, double* Lam_n, double* dd_u, double rtol,
+                                     const double* U_np1, double* Lam_n, double* Y, double* dd_u, double rtol,
                                      mofem_precision prec, mofem_solve_info* info, cudaStream_t stream);
 
 /* One IMEX Euler step of a batch of reaction-diffusion species (Sec. 6 applied

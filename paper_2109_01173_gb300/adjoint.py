@@ -49,10 +49,11 @@ class HeatSetup:
         h.imex_step_tol(float(d_u), self.tau, U, self.F0, out, self.rtol, self.precision)
         return out
 
-    def adjoint_step(self, h, d_u, lam, U1):
-        """(M~ S^{-1} lam, this step's dJ/dd_u) with U1 the state after the step."""
+    def adjoint_step(self, h, d_u, lam, U1, Y=None):
+        """(M~ S^{-1} lam, this step's dJ/dd_u) with U1 the state after the step; Y (in/out)
+        warm-starts the solve from the previous step's S^{-1} lam."""
         out = torch.empty_like(lam)
-        dd, _, _ = h.imex_adjoint_step(float(d_u), self.tau, lam, U1, out, self.rtol, self.precision)
+        dd, _, _ = h.imex_adjoint_step(float(d_u), self.tau, lam, U1, out, self.rtol, self.precision, Y=Y)
         return out, float(sum(dd))
 
     def close(self):
@@ -87,6 +88,7 @@ class HeatIMEX(torch.autograd.Function):
         setup, N, M, du = ctx.setup, ctx.n_steps, ctx.every, ctx.du
         h = setup.handle(du)
         lam = gU.detach().to(torch.float64).contiguous()
+        Y = torch.zeros_like(lam)   # S^{-1} lam of the previous step: the next solve's initial guess
         g_du = 0.0
         for s in range(len(ctx.ckpt) - 1, -1, -1):
             start, stop = s * M, min(s * M + M, N)
@@ -94,7 +96,7 @@ class HeatIMEX(torch.autograd.Function):
             for _ in range(start, stop):
                 states.append(setup.step(h, du, states[-1]))
             for n in range(stop - 1, start - 1, -1):
-                lam, dd = setup.adjoint_step(h, du, lam, states[n + 1 - start])
+                lam, dd = setup.adjoint_step(h, du, lam, states[n + 1 - start], Y)
                 g_du += dd
         ctx.ckpt = None
         gu0 = lam if ctx.needs_input_grad[0] else None

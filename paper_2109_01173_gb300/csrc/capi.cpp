@@ -159,13 +159,14 @@ mofem_status mofem_imex_step_tol(mofem_handle h, double d_u, double tau, const d
 }
 
 mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, const double* Lam_np1,
-                                     const double* U_np1, double* Lam_n, double* dd_u, double rtol,
+                                     const double* U_np1, double* Lam_n, double* Y, double* dd_u, double rtol,
                                      mofem_precision prec, mofem_solve_info* info, cudaStream_t stream) {
     if (!h || !Lam_np1 || !U_np1 || !Lam_n || !dd_u || !(d_u > 0.0) || !(tau > 0.0) || !(rtol > 0.0) ||
         !valid_precision(prec) || Lam_n == Lam_np1)
         return MOFEM_ERR_INVALID_ARG;
+    if (Y && (Y == Lam_np1 || Y == Lam_n || Y == U_np1)) return MOFEM_ERR_INVALID_ARG;
     if (!imex_gamma_ok(h, d_u, tau)) return MOFEM_ERR_INVALID_ARG;
-    return solve_imex_adjoint(h, d_u, tau, Lam_np1, U_np1, Lam_n, dd_u, rtol, prec, info, stream);
+    return solve_imex_adjoint(h, d_u, tau, Lam_np1, U_np1, Lam_n, Y, dd_u, rtol, prec, info, stream);
 }
 
 mofem_status mofem_rds_step(mofem_handle h, double tau, const double* U_n, const double* F_n, double* U_np1,

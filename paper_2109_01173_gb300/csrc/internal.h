@@ -245,6 +245,6 @@ mofem_status dib_equilibrium(const mofem_dib_params& p, double* eta, double* the
 mofem_status launch_dib_kinetics(const mofem_dib_params& p, double rho, const double* eta, const double* theta,
                                  double* f, double* g, long long n, cudaStream_t st);
 mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const double* Lam1, const double* U1,
-                                double* Lam0, double* dd, double rtol, mofem_precision prec, mofem_solve_info* info,
+                                double* Lam0, double* Y, double* dd, double rtol, mofem_precision prec, mofem_solve_info* info,
                                 cudaStream_t st);
 void mofem_free_extra(mofem_ctx* c);

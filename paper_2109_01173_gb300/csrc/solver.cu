@@ -727,18 +727,18 @@ mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, 
 // S = M~ + d_u tau A~ = d_u tau L with L the handle's operator (gamma = 1/(d_u tau)),
 //   Y = S^{-1} Lam_np1,  Lam_n = M~ Y,  dd[i] = -tau <Y, A~ U_np1> = -tau (<Y, L U> - gamma <Y, M~ U>).
 mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const double* Lam1, const double* U1,
-                                double* Lam0, double* dd, double rtol, mofem_precision prec, mofem_solve_info* info,
-                                cudaStream_t st) {
+                                double* Lam0, double* Y_io, double* dd, double rtol, mofem_precision prec,
+                                mofem_solve_info* info, cudaStream_t st) {
     MOFEM_TRY(ensure_common(c, st));
     Extra& e = extras()[c];
     const int q = c->q, B = c->batch;
     const long long qq = (long long)q * q;
     double* buf = nullptr;
     MOFEM_CUDA_TRY(cudaMallocAsync((void**)&buf, sizeof(double) * (size_t)qq * B * 3, st));
-    double *Y = buf, *LU = buf + qq * B, *MU = buf + 2 * qq * B;
+    double *Y = Y_io ? Y_io : buf, *LU = buf + qq * B, *MU = buf + 2 * qq * B;
     mofem_status s = launch_scale_copy64(Lam1, qq, q, c->Bm64, (long long)per(c), c->ld, q, q, B, 1.0 / (d_u * tau), st);
-    if (s == MOFEM_OK) s = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)qq * B, st) == cudaSuccess ? MOFEM_OK
-                                                                                                    : MOFEM_ERR_CUDA;
+    if (s == MOFEM_OK && !Y_io)   // no guess: start from zero
+        s = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)qq * B, st) == cudaSuccess ? MOFEM_OK : MOFEM_ERR_CUDA;
     mofem_status solve = MOFEM_OK;
     if (s == MOFEM_OK) {
         solve = solve_core(c, Y, qq, q, rtol, 100000, prec, 0, info, st);

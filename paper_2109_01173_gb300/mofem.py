@@ -89,7 +89,7 @@ def _load():
         "mofem_group_destroy": [vp],
         "mofem_dib_run": [vp, P(DibParams), c_double, c_double, c_int, vp, c_double, c_int, P(c_double),
                           P(SolveInfo), vp],
-        "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
+        "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
                                     vp],
         "mofem_destroy": [vp],
         "mofem_bench_kernel": [vp, c_int, c_int, c_int, vp],
@@ -251,11 +251,13 @@ class Handle:
             _check("mofem_imex_step_tol", code)
         return info, code
 
-    def imex_adjoint_step(self, d_u, tau, Lam1, U1, Lam0, rtol, precision="fp16", check=True):
-        """Lam0 = M~ S^{-1} Lam1; returns (dJ/dd_u contributions per instance, info, code)."""
+    def imex_adjoint_step(self, d_u, tau, Lam1, U1, Lam0, rtol, precision="fp16", check=True, Y=None):
+        """Lam0 = M~ S^{-1} Lam1; returns (dJ/dd_u contributions per instance, info, code).
+        Y (optional, in/out): initial guess of S^{-1} Lam1, overwritten by it."""
         dd = (ctypes.c_double * self.batch)()
         info = SolveInfo()
-        code = LIB.mofem_imex_adjoint_step(self.h, d_u, tau, _ptr(Lam1), _ptr(U1), _ptr(Lam0), dd, rtol,
+        code = LIB.mofem_imex_adjoint_step(self.h, d_u, tau, _ptr(Lam1), _ptr(U1), _ptr(Lam0),
+                                           _ptr(Y) if Y is not None else None, dd, rtol,
                                            PRECISIONS[precision], ctypes.byref(info), _stream())
         if check:
             _check("mofem_imex_adjoint_step", code)

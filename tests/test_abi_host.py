@@ -66,7 +66,7 @@ def test_invalid_arguments_rejected_without_gpu(mofem):
     assert L.mofem_pcg_solve(None, None, None, 1e-10, 10, 0, None, None) == 1
     assert L.mofem_imex_step(None, 1.0, 1.0, None, None, None, 0, None, None) == 1
     assert L.mofem_imex_step_tol(None, 1.0, 1.0, None, None, None, 1e-10, 0, None, None) == 1
-    assert L.mofem_imex_adjoint_step(None, 1.0, 1.0, None, None, None, None, 1e-10, 0, None, None) == 1
+    assert L.mofem_imex_adjoint_step(None, 1.0, 1.0, None, None, None, None, None, 1e-10, 0, None, None) == 1
     assert L.mofem_rds_step(None, 1.0, None, None, None, 0.0, 0, None, None) == 1
     assert L.mofem_dib_kinetics(None, 1.0, None, None, None, None, 0, None) == 1
     assert L.mofem_dib_run(None, None, 1.0, 1.0, 1, None, 0.0, 0, None, None, None) == 1
