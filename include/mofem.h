@@ -50,7 +50,7 @@ typedef enum {
     MOFEM_ERR_NOT_CONVERGED = 6, /* max_iter reached; the iterate is kept */
     MOFEM_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
     MOFEM_ERR_OOM = 8,           /* device allocation failed */
-    MOFEM_ERR_UNSUPPORTED = 9    /* valid request this build does not implement */
+    MOFEM_ERR_UNSUPPORTED = 9    /* valid request the library does not implement */
 } mofem_status;
 
 typedef enum { MOFEM_BC_DIRICHLET = 0, MOFEM_BC_NEUMANN = 1 } mofem_bc;
