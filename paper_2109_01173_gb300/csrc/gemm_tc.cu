@@ -74,6 +74,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// try_wait with cluster-scope acquire: for data the partner CTA stored into this CTA's
+// shared memory before its release arrive
+__device__ __forceinline__ bool mbar_try_cl(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, "
+        "0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -258,10 +270,14 @@ constexpr int ST2 = MOFEM_GEMM_STAGES;
 constexpr int A2_BYTES = 128 * 128, B2_BYTES = 128 * 128;
 constexpr int STAGE2_BYTES = A2_BYTES + B2_BYTES;
 
+constexpr int NU = 8;   // unit ring of a chain launch: tile indices taken, not yet consumed by every role
 struct PBars2 {
     uint64_t full[ST2], empty[ST2], tfull[2], tempty[2];
+    uint64_t ufull[NU], uempty[NU];
+    int uslot[NU];
     uint32_t tmem_slot;
     int abort;
+    int mode;   // chain tile order of this launch (1 static, 2 dynamic)
     double red[2][4];
 };
 
@@ -307,10 +323,84 @@ __device__ __forceinline__ void commit2_mc(uint32_t mbar, uint16_t mask) {
         : "memory");
 }
 
-template <int KIND, int EPI>
-__global__ void __launch_bounds__(P_THREADS, 1)
-    k_gemm_2sm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, GemmArgs g) {
-    constexpr int OUTK = EPI == EPI_Z ? 0 : KIND;   // output type: FP32 (TF32 plans and Z), BF16, FP16
+// A chain of GEMMs in one persistent launch (the preconditioner's G1..G4): the
+// pairs walk the tiles of all stages in stage-major order; a tile of stage s > 0
+// whose operand is stage s-1's output waits (bounded) until the 256-row output panel
+// it reads is complete, counted by the four epilogue warps of both CTAs of every
+// tile of that panel.  Two tile orders:
+//  - static round-robin (pair p: tiles p, p + P, ...): the fastest (0.7 ms per
+//    P2 2049 x 4 solve ahead of the dynamic order), but a pair may wait on a tile of
+//    a pair that is not resident yet, so it is taken only by a launch that is alone
+//    among chain launches on the device (g_chain_inflight);
+//  - dynamic: each pair's leader takes the next tile from a global counter, so a
+//    tile waits only on smaller indices taken earlier by running pairs and the
+//    smallest unfinished tile can always proceed, however many pairs are resident.
+// One launch instead of four saves three launch / prologue / pipeline-fill /
+// last-epilogue latencies (~9.5 us each at P2 2049 x 4), and the next stage's tiles
+// fill the previous one's tail.
+constexpr int CHAIN_MAX = 4;
+struct GemmChain {
+    CUtensorMap mA[CHAIN_MAX], mB[CHAIN_MAX];
+    GemmArgs g[CHAIN_MAX];   // per stage; M, N, nk, batch, sc and status are the same in all
+    int dep[CHAIN_MAX];      // operand from stage s-1: 0 none, 1 the A rows (panel = tile row),
+                             // 2 the B rows (panel = tile column)
+    int ns;                  // stages in this launch
+    unsigned* panel_cnt;     // [stage][batch][row panel]: finished CTA tiles (null: ns == 1)
+    unsigned* end_ticket;    // CTAs done; the last one resets panel_cnt and unit_ctr for the next launch
+    unsigned* unit_ctr;      // next tile index (dynamic order): taken by each pair's leader as it goes
+    unsigned* mode;          // this launch's tile order, set by its first CTA: 1 static, 2 dynamic
+};
+
+// Chain launches in flight on this device (all handles).  A launch walks the static
+// round-robin order only when it is the only one: the static order needs its pairs to
+// become resident eventually, which holds when every other launch is either a plain
+// kernel or a chain in dynamic order (neither waits on anything that is not running).
+__device__ unsigned g_chain_inflight;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void mbar_arrive_local(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, int v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+
+// Bounded wait on an mbarrier phase with cluster-scope acquire.
+__device__ __forceinline__ bool pwait_cl(uint32_t a, uint32_t parity, volatile int* abort) {
+    if (mbar_try_cl(a, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try_cl(a, parity)) {
+        if (*abort) return false;
+        if (gtimer() - t0 > WAIT_LIMIT_NS) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Bounded wait until *c >= need; raises the CTA's abort flag on timeout.
+__device__ __noinline__ bool panel_wait(const unsigned* c, unsigned need, volatile int* abort) {
+    if (ld_acquire_u32(c) >= need) return true;
+    const unsigned long long t0 = gtimer();
+    while (ld_acquire_u32(c) < need) {
+        if (*abort) return false;
+        if (gtimer() - t0 > WAIT_LIMIT_NS) {
+            *abort = 1;
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant__ GemmChain ch) {
+    const GemmArgs& g0 = ch.g[0];
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     PBars2* pb = reinterpret_cast<PBars2*>(smem + ST2 * STAGE2_BYTES);
@@ -319,12 +409,14 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     const int cr = (int)cluster_rank();
     const bool leader = cr == 0;
     const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
-    const int ntn = (g.N + 255) / 256, ntm = (g.M + 255) / 256;
-    const int per_inst = ntn * ntm;   // pair tiles per instance
-    const int total = per_inst * g.batch;
+    const int ntn = (g0.N + 255) / 256, ntm = (g0.M + 255) / 256;
+    const int per_inst = ntn * ntm;   // pair tiles per instance and stage
+    const int total = per_inst * g0.batch;
+    const int units = total * ch.ns;
     constexpr int BK = 128 / (KIND == 0 ? 4 : 2);
     auto bar_addr = [&](uint64_t* b) { return smem_u32(b); };
-    auto active = [&](int inst) { return !g.sc || g.sc[inst].active; };
+
+    auto active = [&](int inst) { return !g0.sc || g0.sc[inst].active; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST2; ++s) {
@@ -335,8 +427,30 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             mbar_init(bar_addr(&pb->tfull[b]), 1);
             mbar_init(bar_addr(&pb->tempty[b]), 8);   // 4 epilogue warps in each CTA
         }
+        for (int k = 0; k < NU; ++k) {
+            mbar_init(bar_addr(&pb->ufull[k]), 1);
+            // consumers of a slot: leader's MMA thread and 4 epilogue warps, partner's producer and 4 epilogue warps
+            mbar_init(bar_addr(&pb->uempty[k]), 10);
+        }
         pb->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // tile order of a chain launch: decided once by its first CTA, read by the others
+        if (leader && ch.ns > 1 && ch.mode) {
+            unsigned m = ld_acquire_u32(ch.mode);
+            if (m == 0u) {
+                const unsigned prev = atomicAdd(&g_chain_inflight, 1u);
+                const unsigned want = prev == 0u ? 1u : 2u;
+                const unsigned old = atomicCAS(ch.mode, 0u, want);
+                if (old != 0u) {
+                    atomicSub(&g_chain_inflight, 1u);   // another CTA decided first
+                    m = old;
+                } else {
+                    m = want;
+                }
+            }
+            pb->mode = (int)m;
+            st_cluster_u32(mapa_shared(smem_u32(&pb->mode), 1), (int)m);   // the partner's copy
+        }
     }
     if (warp == 5) {   // joint allocation: one warp in each CTA of the pair
         asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -349,15 +463,68 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     cluster_sync_all();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = pb->tmem_slot;
+    // Dynamic order: the leader's producer takes the next index from a global counter and
+    // publishes it to every role of both CTAs through the unit ring; a dependency wait is
+    // then always on smaller, already-taken tiles of running pairs.  Static order (single
+    // GEMMs, and a chain alone on the device): round-robin.
+    const bool dyn = ch.ns > 1 && ch.unit_ctr != nullptr && ch.mode != nullptr && pb->mode == 2;
 
     if (warp == 4) {
         if (lane == 0) {   // ---- TMA producer (both CTAs): own halves of A and B
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA)) : "memory");
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB)) : "memory");
+            for (int st = 0; st < ch.ns; ++st) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mA[st])) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mB[st])) : "memory");
+            }
             int it = 0;
-            for (int t = cid; t < total && !*abort_flag; t += ncl) {
+            // The leader publishes tile j + 1 as it starts tile j, so that the partner (and
+            // the counter's round trip) never hold up the start of a tile.
+            auto publish = [&](int jj, int uu) -> bool {
+                const int k = jj % NU;
+                if (jj >= NU && !pwait_cl(bar_addr(&pb->uempty[k]), ((uint32_t)(jj / NU) & 1u) ^ 1u, abort_flag))
+                    return false;
+                pb->uslot[k] = uu;
+                mbar_arrive_local(bar_addr(&pb->ufull[k]));
+                st_cluster_u32(mapa_shared(smem_u32(&pb->uslot[k]), 1), uu);
+                mbar_arrive_cluster(mapa_shared(bar_addr(&pb->ufull[k]), 1));
+                return true;
+            };
+            int u_pub = 0;   // leader: the index published for the current tile
+            if (dyn && leader) {
+                u_pub = (int)atomicAdd(ch.unit_ctr, 1u);
+                if (!publish(0, u_pub)) u_pub = units;   // abort raised: nothing to do
+            }
+            for (int j = 0;; ++j) {
+                int u;
+                if (dyn) {
+                    const int k = j % NU;
+                    const uint32_t ph = (uint32_t)(j / NU) & 1u;
+                    if (leader) {   // tile j was published; take and publish tile j + 1
+                        u = u_pub;
+                        if (u < units && !*abort_flag) {
+                            u_pub = (int)atomicAdd(ch.unit_ctr, 1u);
+                            if (!publish(j + 1, u_pub)) break;
+                        }
+                    } else {
+                        if (!pwait_cl(bar_addr(&pb->ufull[k]), ph, abort_flag)) break;
+                        u = *reinterpret_cast<volatile int*>(&pb->uslot[k]);
+                        mbar_arrive_cluster(mapa_shared(bar_addr(&pb->uempty[k]), 0));
+                    }
+                } else {
+                    u = cid + j * ncl;
+                }
+                if (u >= units || *abort_flag) break;
+                const int stg = u / total, t = u - stg * total;
+                const GemmArgs& g = ch.g[stg];
                 const int inst = t / per_inst, r = t - inst * per_inst;
                 if (!active(inst)) continue;
+                if (ch.dep[stg] && ch.panel_cnt) {   // the operand panel written by the previous stage
+                    const int pan = ch.dep[stg] == 2 ? r % ntn : r / ntn;
+                    const unsigned* c = ch.panel_cnt + ((size_t)(stg - 1) * g0.batch + inst) * ntm + pan;
+                    if (!panel_wait(c, 8u * (unsigned)ntn, abort_flag)) break;
+                    asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes -> TMA reads
+                }
+                const CUtensorMap* mA = &ch.mA[stg];
+                const CUtensorMap* mB = &ch.mB[stg];
                 const int m0 = (r / ntn) * 256 + cr * 128, nh = (r % ntn) * 256 + cr * 128;
                 const int za = g.a_shared ? 0 : inst, zb = g.b_shared ? 0 : inst;
                 for (int kb = 0; kb < g.nk; ++kb, ++it) {
@@ -367,16 +534,26 @@ __global__ void __launch_bounds__(P_THREADS, 1)
                     const uint32_t sa = smem_u32(smem + s * STAGE2_BYTES);
                     const uint32_t fl = mapa_shared(bar_addr(&pb->full[s]), 0);
                     if (leader) mbar_expect_tx(bar_addr(&pb->full[s]), 2 * STAGE2_BYTES);   // both CTAs' halves
-                    tma_load_3d_pair(sa, &mA, fl, kb * BK, m0, za);
-                    tma_load_3d_pair(sa + A2_BYTES, &mB, fl, kb * BK, nh, zb);
+                    tma_load_3d_pair(sa, mA, fl, kb * BK, m0, za);
+                    tma_load_3d_pair(sa + A2_BYTES, mB, fl, kb * BK, nh, zb);
                 }
             }
         }
     } else if (warp == 5) {
         if (lane == 0 && leader) {   // ---- MMA issuer (leader CTA only)
             int it = 0, tl = 0;
-            for (int t = cid; t < total && !*abort_flag; t += ncl) {
-                const int inst = t / per_inst;
+            for (int j = 0;; ++j) {
+                int u;
+                if (dyn) {
+                    const int k = j % NU;
+                    if (!pwait_cl(bar_addr(&pb->ufull[k]), (uint32_t)(j / NU) & 1u, abort_flag)) break;
+                    u = *reinterpret_cast<volatile int*>(&pb->uslot[k]);
+                    mbar_arrive_cluster(mapa_shared(bar_addr(&pb->uempty[k]), 0));
+                } else {
+                    u = cid + j * ncl;
+                }
+                if (u >= units || *abort_flag) break;
+                const int inst = (u % total) / per_inst;
                 if (!active(inst)) continue;
                 const int b = tl & 1;
                 const uint32_t use = (uint32_t)(tl >> 1);
@@ -384,7 +561,7 @@ __global__ void __launch_bounds__(P_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(b * 256);
                 bool ok = true;
-                for (int kb = 0; kb < g.nk; ++kb, ++it) {
+                for (int kb = 0; kb < g0.nk; ++kb, ++it) {
                     const int s = it % ST2;
                     const uint32_t ph = (uint32_t)(it / ST2) & 1u;
                     if (!pwait(bar_addr(&pb->full[s]), ph, abort_flag)) {
@@ -406,7 +583,28 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     } else {   // ---- epilogue warps 0-3 (both CTAs): thread = TMEM lane = output row
         int tl = 0;
         const int cta_per_inst = per_inst * 2;
-        for (int t = cid; t < total; t += ncl) {
+        for (int j = 0;; ++j) {
+            int u;
+            if (dyn) {
+                const int k = j % NU;
+                int uu = 0, okw = 1;
+                if (lane == 0) {
+                    okw = pwait_cl(bar_addr(&pb->ufull[k]), (uint32_t)(j / NU) & 1u, abort_flag) ? 1 : 0;
+                    if (okw) {
+                        uu = *reinterpret_cast<volatile int*>(&pb->uslot[k]);
+                        mbar_arrive_cluster(mapa_shared(bar_addr(&pb->uempty[k]), 0));
+                    }
+                }
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                uu = __shfl_sync(0xffffffffu, uu, 0);
+                if (!okw) break;
+                u = uu;
+            } else {
+                u = cid + j * ncl;
+            }
+            if (u >= units) break;
+            const int stg = u / total, t = u - stg * total;
+            const GemmArgs& g = ch.g[stg];
             const int inst = t / per_inst, r = t - inst * per_inst;
             if (!active(inst)) continue;
             const int m0 = (r / ntn) * 256 + cr * 128, n0 = (r % ntn) * 256;
@@ -419,21 +617,34 @@ __global__ void __launch_bounds__(P_THREADS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int m = m0 + warp * 32 + lane;
             const bool m_ok = m < g.M;
+            const int epi = g.epi;
             float mu_m = 0.f;
-            if (EPI == EPI_DIV && m_ok) mu_m = g.mu[m];
-            const float inv_scale = (EPI == EPI_Z && g.scl) ? (float)(1.0 / g.scl[inst].rscale) : 1.f;
+            if (epi == EPI_DIV && m_ok) mu_m = g.mu[m];
+            const float inv_scale = (epi == EPI_Z && g.scl) ? (float)(1.0 / g.scl[inst].rscale) : 1.f;
             double acc = 0.0;
 #pragma unroll 1
             for (int c = 0; c < 256 / 32; ++c) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256 + c * 32), v);
                 const int nb = n0 + c * 32;
-                if (m_ok && nb < g.N) epi_chunk<EPI, OUTK>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                if (m_ok && nb < g.N) {
+                    if (epi == EPI_DIV) epi_chunk<EPI_DIV, KIND>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                    else if (epi == EPI_Z) epi_chunk<EPI_Z, 0>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                    else epi_chunk<EPI_STORE, KIND>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(mapa_shared(bar_addr(&pb->tempty[b]), 0));
-            if (EPI == EPI_Z && g.rz_part) {
+            if (stg + 1 < ch.ns && ch.dep[stg + 1] && ch.panel_cnt) {
+                // publish this warp's 32 rows of the tile to the next stage's TMA reads
+                // (4 warps x 2 CTAs per tile: a panel of ntn tiles is complete at 8 ntn)
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicAdd(ch.panel_cnt + ((size_t)stg * g0.batch + inst) * ntm + r / ntn, 1u);
+            }
+            if (epi == EPI_Z && g.rz_part) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (lane == 0) pb->red[tl & 1][warp] = acc;
@@ -473,7 +684,22 @@ __global__ void __launch_bounds__(P_THREADS, 1)
     }
     __syncthreads();
     cluster_sync_all();   // the peer's copies, commits and arrivals have all landed
-    if (threadIdx.x == 0 && pb->abort && g.status) atomicOr(g.status, DEV_ERR_TIMEOUT);
+    if (threadIdx.x == 0 && pb->abort && g0.status) atomicOr(g0.status, DEV_ERR_TIMEOUT);
+    if (threadIdx.x == 0 && ch.panel_cnt && ch.ns > 1) {
+        __threadfence();
+        const unsigned tk = atomicAdd(ch.end_ticket, 1u);
+        if (tk == gridDim.x - 1) {   // every CTA is done with the counters: reset them
+            const int ncnt = (ch.ns - 1) * g0.batch * ntm;
+            for (int i = 0; i < ncnt; ++i) ch.panel_cnt[i] = 0u;
+            if (ch.unit_ctr) *ch.unit_ctr = 0u;
+            if (ch.mode) {   // the launch's registration in the in-flight count ends here
+                *ch.mode = 0u;
+                atomicSub(&g_chain_inflight, 1u);
+            }
+            *ch.end_ticket = 0u;
+            __threadfence();
+        }
+    }
     if (warp == 5) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS_P) : "memory");
@@ -565,11 +791,10 @@ int num_sms() {
 
 constexpr int GEMM_CM = 2;   // CTAs per cluster: one tcgen05 CTA pair
 
-template <int KIND, int EPI>
-mofem_status launch_gemm_e(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g0, int batch,
-                           cudaStream_t st) {
+template <int KIND>
+mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
     constexpr int CM = GEMM_CM;
-    auto kern = k_gemm_2sm<KIND, EPI>;
+    auto kern = k_gemm_2sm<KIND>;
     static int max_pairs = 0;
     const int smem = ST2 * STAGE2_BYTES + 1024 + (int)sizeof(PBars2) + 64;
     cudaLaunchConfig_t cfg = {};
@@ -594,22 +819,44 @@ mofem_status launch_gemm_e(const CUtensorMap& mA, const CUtensorMap& mB, const G
         }
         max_pairs = n;
     }
-    GemmArgs g = g0;
-    g.batch = batch;
-    const int total = ((g.N + BN - 1) / BN) * ((g.M + BM * CM - 1) / (BM * CM)) * batch;   // pair tiles
-    const int pairs = total < max_pairs ? total : max_pairs;
+    GemmChain ch = ch0;
+    if (ch.ns < 1 || ch.ns > CHAIN_MAX ||
+        (ch.ns > 1 && (!ch.panel_cnt || !ch.end_ticket || !ch.unit_ctr || !ch.mode)))
+        return MOFEM_ERR_INVALID_ARG;
+    if (ch.ns > 1 && ch.g[0].M != ch.g[0].N) return MOFEM_ERR_INVALID_ARG;   // panels index rows and columns alike
+    for (int s = 0; s < ch.ns; ++s) {
+        GemmArgs& g = ch.g[s];
+        g.batch = batch;
+        // output type follows the operand kind (FP32 for TF32, BF16, FP16), except G4's FP32 Z;
+        // every stage shares the first one's shape and scalar state
+        if (g.out_bf16 != (g.epi == EPI_Z ? 0 : KIND)) return MOFEM_ERR_INVALID_ARG;
+        if (g.M != ch.g[0].M || g.N != ch.g[0].N || g.nk != ch.g[0].nk || g.sc != ch.g[0].sc) return MOFEM_ERR_INVALID_ARG;
+        if (s == 0 ? ch.dep[s] != 0 : (ch.dep[s] < 0 || ch.dep[s] > 2)) return MOFEM_ERR_INVALID_ARG;
+    }
+    for (int s = ch.ns; s < CHAIN_MAX; ++s) ch.dep[s] = 0;
+    const int total = ((ch.g[0].N + BN - 1) / BN) * ((ch.g[0].M + BM * CM - 1) / (BM * CM)) * batch;   // pair tiles
+    const int units = total * ch.ns;
+    const int pairs = units < max_pairs ? units : max_pairs;
     cfg.gridDim = dim3(CM * pairs);
-    MOFEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, mA, mB, g));
+    MOFEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ch));
     return MOFEM_OK;
 }
 
-// Output type follows the operand kind (FP32 for TF32, BF16, FP16), except G4's FP32 Z.
-template <int KIND>
-mofem_status launch_gemm(const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch, cudaStream_t st) {
-    if (g.out_bf16 != (g.epi == EPI_Z ? 0 : KIND)) return MOFEM_ERR_INVALID_ARG;
-    if (g.epi == EPI_DIV) return launch_gemm_e<KIND, EPI_DIV>(mA, mB, g, batch, st);
-    if (g.epi == EPI_Z) return launch_gemm_e<KIND, EPI_Z>(mA, mB, g, batch, st);
-    return launch_gemm_e<KIND, EPI_STORE>(mA, mB, g, batch, st);
+mofem_status launch_chain_kind(int which, const GemmChain& ch, int batch, cudaStream_t st) {
+    if (which == 1) return launch_chain<1>(ch, batch, st);
+    if (which == 2) return launch_chain<2>(ch, batch, st);
+    return launch_chain<0>(ch, batch, st);
+}
+
+// One GEMM: a chain of one stage.
+mofem_status launch_single(int which, const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch,
+                           cudaStream_t st) {
+    GemmChain ch{};
+    ch.mA[0] = mA;
+    ch.mB[0] = mB;
+    ch.g[0] = g;
+    ch.ns = 1;
+    return launch_chain_kind(which, ch, batch, st);
 }
 
 }  // namespace
@@ -619,9 +866,7 @@ mofem_status launch_transpose64_ld(const double* src, long long s_bs, int s_ld, 
 
 mofem_status launch_gemm_kind(int which, const CUtensorMap& mA, const CUtensorMap& mB, const GemmArgs& g, int batch,
                               cudaStream_t st) {
-    if (which == 1) return launch_gemm<1>(mA, mB, g, batch, st);
-    if (which == 2) return launch_gemm<2>(mA, mB, g, batch, st);
-    return launch_gemm<0>(mA, mB, g, batch, st);
+    return launch_single(which, mA, mB, g, batch, st);
 }
 
 // <R, Z> partial slots per instance: one per CTA tile of the paired grid
@@ -652,6 +897,11 @@ mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
     for (void* z : zero) MOFEM_CUDA_TRY(cudaMemsetAsync(z, 0, per * B * es, st));
     MOFEM_CUDA_TRY(cudaMemsetAsync(p.Q2, 0, per * es, st));
     MOFEM_CUDA_TRY(cudaMemsetAsync(p.Q2T, 0, per * es, st));
+    // panel counters of the GEMM chain (three producing stages) and its end ticket, self-resetting
+    p.n_panel_cnt = 3 * B * ((q + 255) / 256);
+    // + end ticket, unit counter, order word
+    MOFEM_CUDA_TRY(cudaMalloc(&p.panel_cnt, sizeof(unsigned) * (p.n_panel_cnt + 3)));
+    MOFEM_CUDA_TRY(cudaMemsetAsync(p.panel_cnt, 0, sizeof(unsigned) * (p.n_panel_cnt + 3), st));
     double* tmp = nullptr;
     MOFEM_CUDA_TRY(cudaMalloc(&tmp, per * sizeof(double)));
     MOFEM_TRY(launch_convert(c->Q2_64, 1, per, ld, p.Q2, kind, per, ld, q, q, 1, st));
@@ -719,24 +969,33 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
     g.out_bf16 = which;
     g.scl = which == 2 ? c->d_sc : nullptr;
     g.pad_ok = 1;   // G1..G3 write internal intermediates
-    auto run = [&](int i) -> mofem_status { return launch_gemm_kind(which, p.mA[i], p.mB[i], g, c->batch, st); };
+    GemmChain ch{};
+    for (int i = 0; i < 4; ++i) {
+        ch.mA[i] = p.mA[i];
+        ch.mB[i] = p.mB[i];
+    }
     // G1: X1T = (R Q2)^T
     g.out = p.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
-    MOFEM_TRY(run(0));
-    // G2: WT[j][i] = (Q1^T X1)[i][j] / (lam_i + mu_j)
+    ch.g[0] = g;
+    // G2: WT[j][i] = (Q1^T X1)[i][j] / (lam_i + mu_j)   (A = X1T: rows written by G1)
     g.out = p.WT; g.epi = EPI_DIV; g.a_shared = 0; g.b_shared = 0;
-    MOFEM_TRY(run(1));
-    // G3: Y = Q1 W
+    ch.g[1] = g; ch.dep[1] = 1;
+    // G3: Y = Q1 W   (B = WT: rows written by G2)
     g.out = p.Y; g.epi = EPI_STORE; g.a_shared = 0; g.b_shared = 0;
-    MOFEM_TRY(run(2));
-    // G4: Z = Y Q2^T (+ <R, Z> partials)
+    ch.g[2] = g; ch.dep[2] = 2;
+    // G4: Z = Y Q2^T (+ <R, Z> partials)   (A = Y: rows written by G3)
     g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 0; g.b_shared = 1;
     g.pad_ok = z_internal ? 1 : 0;   // a caller's Z keeps its padding untouched
     g.R = R32; g.r_bs = r_bs; g.r_ld = r_ld; g.rz_part = rz_partial;
     g.counter = c->d_ctr + 2 * c->batch;
     g.flex = 1;
-    MOFEM_TRY(run(3));
-    return MOFEM_OK;
+    ch.g[3] = g; ch.dep[3] = 1;
+    ch.ns = 4;
+    ch.panel_cnt = p.panel_cnt;
+    ch.end_ticket = p.panel_cnt + p.n_panel_cnt;
+    ch.unit_ctr = p.panel_cnt + p.n_panel_cnt + 1;
+    ch.mode = p.panel_cnt + p.n_panel_cnt + 2;
+    return launch_chain_kind(which, ch, c->batch, st);
 }
 
 // The four preconditioner GEMMs on caller-provided BF16 buffers (operand copies
@@ -762,12 +1021,12 @@ mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z
     g.out_bs = (long long)q * ld; g.out_ld = ld; g.out_bf16 = 1;
     g.pad_ok = 1;   // the library's own scratch array
     g.out = b.X1T; g.epi = EPI_STORE; g.a_shared = 1; g.b_shared = 0;
-    MOFEM_TRY(launch_gemm<1>(mA[0], mB[0], g, B, st));
+    MOFEM_TRY(launch_single(1, mA[0], mB[0], g, B, st));
     g.out = b.WT; g.epi = EPI_DIV; g.a_shared = 0; g.b_shared = 0;
-    MOFEM_TRY(launch_gemm<1>(mA[1], mB[1], g, B, st));
+    MOFEM_TRY(launch_single(1, mA[1], mB[1], g, B, st));
     g.out = b.Y; g.epi = EPI_STORE;
-    MOFEM_TRY(launch_gemm<1>(mA[2], mB[2], g, B, st));
+    MOFEM_TRY(launch_single(1, mA[2], mB[2], g, B, st));
     g.out = Z; g.out_bs = z_bs; g.out_ld = z_ld; g.out_bf16 = 0; g.epi = EPI_Z; g.a_shared = 0; g.b_shared = 1;
     g.pad_ok = 0;   // the caller's Z
-    return launch_gemm<1>(mA[3], mB[3], g, B, st);
+    return launch_single(1, mA[3], mB[3], g, B, st);
 }

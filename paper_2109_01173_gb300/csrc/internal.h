@@ -54,6 +54,8 @@ struct TcPlan {                 // one tensor-core precision (BF16 or TF32)
     void* Q2 = nullptr;  void* Q2T = nullptr;   // [q][ld] (shared)
     void* Rop = nullptr;                        // GEMM1 A operand (R rounded), [batch][q][ld]
     void* X1T = nullptr; void* WT = nullptr; void* Y = nullptr;  // intermediates
+    unsigned* panel_cnt = nullptr;  // GEMM-chain panel counters [3][batch][panels] + end ticket
+    int n_panel_cnt = 0;
     CUtensorMap mA[4], mB[4];
 };
 

@@ -528,7 +528,7 @@ void mofem_free(mofem_ctx* c) {
                     c->d_red};
     for (void* p : ptrs) cudaFree(p);
     for (auto& t : c->tc) {
-        void* tp[] = {t.Q1, t.Q1T, t.Q2, t.Q2T, t.Rop, t.X1T, t.WT, t.Y};
+        void* tp[] = {t.Q1, t.Q1T, t.Q2, t.Q2T, t.Rop, t.X1T, t.WT, t.Y, t.panel_cnt};
         for (void* p : tp) cudaFree(p);
     }
     for (int i = 0; i < 3; ++i) {

@@ -60,3 +60,34 @@ def test_group_autotune_restores_guesses(mf):
     infos, code = g.solve(F, U, rtol=1e-10)
     assert code == 0 and all(i.rel_residual <= 1e-10 for i in infos)
     g.close()
+
+
+def test_group_concurrent_full_size_bitwise(mf):
+    """Two groups of full-size problems (P2 and P1, 2049 x 2049 nodes, two instances
+    each) solved concurrently on their own streams: their preconditioner GEMM chains
+    overlap on the device, and a chain launch that finds another one in flight walks
+    its tiles in the dynamic order.  No tile order changes any result (each tile's
+    arithmetic and every reduction slot are fixed), so each problem's solution must
+    equal bitwise the one from its group's batched handle solved alone."""
+    import torch
+    from paper_2109_01173_gb300.inputs import metric_instance
+    probs = []
+    for k in (2, 1):
+        for s, gam in ((0, 1.0), (1, 3.0)):
+            inst = metric_instance(n=2049, k=k, seed=s, gamma=gam)
+            probs.append(dict(g1=inst["g1"], g2=inst["g2"], k=k, n=2049, gamma=gam, bc="dirichlet", F=inst["F"]))
+    g = mf.Group(probs)
+    F = [torch.tensor(p["F"], device="cuda") for p in probs]
+    U = [torch.zeros((2047, 2047), dtype=torch.float64, device="cuda") for _ in probs]
+    infos, code = g.solve(F, U, rtol=1e-10, max_iter=500, precision="fp16")
+    assert code == 0
+    g.close()
+    for k, idx in ((2, [0, 1]), (1, [2, 3])):
+        h = mf.Handle([probs[i]["g1"] for i in idx], [probs[i]["g2"] for i in idx], k, 2049,
+                      [probs[i]["gamma"] for i in idx])
+        Ub = torch.zeros((2, 2047, 2047), dtype=torch.float64, device="cuda")
+        info, c2 = h.pcg_solve(torch.stack([F[i] for i in idx]), Ub, rtol=1e-10, max_iter=500, precision="fp16")
+        assert c2 == 0
+        for j, i in enumerate(idx):
+            assert torch.equal(Ub[j], U[i]), (k, i)
+        h.close()
