@@ -314,7 +314,9 @@ mofem_status mofem_group_destroy(mofem_group g);
  *   7 = FP32 PCG update of an odd iteration (R, FP16 copy, and the correction
  *       U += alpha_prev Q_prev + alpha Q in double-float),
  *   8 = double-float residual update R64 -= L(d) of a refinement step
- *       (MOFEM_ERR_UNSUPPORTED for forms it does not serve).
+ *       (MOFEM_ERR_UNSUPPORTED for forms it does not serve),
+ *   9 = the preconditioner's four GEMMs as the solver runs them, one chained
+ *       launch (prec MIXED_TF32, MIXED_BF16 or MIXED_FP16).
  * The buffers' contents are whatever the last solve left (timing only). */
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps,
                                 cudaStream_t stream);

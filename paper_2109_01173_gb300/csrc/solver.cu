@@ -853,6 +853,13 @@ mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int re
                                         nullptr, st, false, w32(c, W32_QB), kernel == 7 ? 1 : 0));
         return MOFEM_OK;
     }
+    if (kernel == 9) {   // the preconditioner's four GEMMs as one chained launch (<R, Z> partials, no beta)
+        MOFEM_TRY(tc_prepare(c, which, st));
+        for (int r = 0; r < reps; ++r)
+            MOFEM_TRY(tc_precond(c, which, w32(c, W32_R), bs, c->ld, w32(c, W32_Z), c->ld, bs, extras()[c].rz_slots[0],
+                                 nullptr, st, true));
+        return MOFEM_OK;
+    }
     if (kernel == 8) {   // double-float residual update of a refinement step
         int nblk = 0;
         for (int r = 0; r < reps; ++r)
