@@ -243,12 +243,8 @@ template <int K, int NT, int MODE = DF_RESID>
 mofem_status launch_df_t(const DfArgs& a, int batch, int* nblk, cudaStream_t st) {
     using G = DGeo<K>;
     const size_t smem = sizeof(float) * (2 * (size_t)G::HR * G::WC + 2 * (size_t)G::TA * NT * G::P);
-    static bool attr = false;
-    if (!attr) {
-        MOFEM_CUDA_TRY(
-            cudaFuncSetAttribute(k_resid_df<K, NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<bool> attr[MOFEM_MAX_DEV];
+    MOFEM_CUDA_TRY(smem_attr_once(k_resid_df<K, NT, MODE>, (int)smem, attr));
     dim3 grid((a.q + DTB - 1) / DTB, (a.q + G::TA - 1) / G::TA, batch);
     if (nblk) *nblk = grid.x * grid.y;
     k_resid_df<K, NT, MODE><<<grid, DTB, smem, st>>>(a);

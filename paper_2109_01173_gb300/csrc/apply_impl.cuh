@@ -431,11 +431,8 @@ template <typename T, int K, int NT, int MODE, bool TSMEM>
 mofem_status launch_t(const KArgs& a, int batch, cudaStream_t st) {
     const size_t sm = smem_generic<T, K, NT, TSMEM>();
     auto kern = k_apply<T, K, NT, MODE, TSMEM>;
-    static bool attr_done = false;   // per instantiation
-    if (!attr_done) {
-        MOFEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_done = true;
-    }
+    static std::atomic<bool> attr_done[MOFEM_MAX_DEV];   // per instantiation and device
+    MOFEM_CUDA_TRY(smem_attr_once(kern, (int)sm, attr_done));
     dim3 grid((a.cols_out + TB - 1) / TB, (a.rows_out + Geo<K>::TA_G - 1) / Geo<K>::TA_G, batch);
     kern<<<grid, TB, sm, st>>>(a);
     MOFEM_CUDA_TRY(cudaGetLastError());
@@ -447,11 +444,8 @@ mofem_status launch_pcg_t(const CUtensorMap& mZ, const CUtensorMap& mQ, const Ap
                           cudaStream_t st) {
     const size_t sm = smem_pcg<T, K, NT, TSMEM>();
     auto kern = k_apply_pcg<T, K, NT, TSMEM>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        MOFEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_done = true;
-    }
+    static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
+    MOFEM_CUDA_TRY(smem_attr_once(kern, (int)sm, attr_done));
     dim3 grid((a.q + TB - 1) / TB, (a.q + Geo<K>::TA_T - 1) / Geo<K>::TA_T, batch);
     kern<<<grid, TB, sm, st>>>(mZ, mQ, a);
     MOFEM_CUDA_TRY(cudaGetLastError());

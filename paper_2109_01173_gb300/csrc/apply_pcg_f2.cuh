@@ -286,11 +286,8 @@ mofem_status launch_pcg2_t(const CUtensorMap& mZ, const CUtensorMap& mQ, const C
                            const ApplyPcgArgs& a, int batch, cudaStream_t st) {
     using G = Geo2<K, NT>;
     auto kern = k_apply_pcg2<K, NT>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        MOFEM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM));
-        attr_done = true;
-    }
+    static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
+    MOFEM_CUDA_TRY(smem_attr_once(kern, (int)G::SMEM, attr_done));
     dim3 grid((a.q + TB - 1) / TB, (a.q + G::TA - 1) / G::TA, batch);
     kern<<<grid, G::NTH, G::SMEM, st>>>(mZ, mQ, mS, a);
     MOFEM_CUDA_TRY(cudaGetLastError());

@@ -711,15 +711,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {   // thread-safe one-time lookup
         void* p = nullptr;
         cudaDriverEntryPointQueryResult qr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
                 cudaSuccess &&
             qr == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+            return reinterpret_cast<EncodeTiledFn>(p);
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -779,12 +779,15 @@ mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols,
 namespace {
 
 int num_sms() {
-    static int n = 0;
+    static std::atomic<int> cache[MOFEM_MAX_DEV];
+    const int slot = dev_slot();
+    int n = cache[slot].load(std::memory_order_relaxed);
     if (!n) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 148;
+        cache[slot].store(n, std::memory_order_relaxed);
     }
     return n;
 }
@@ -795,7 +798,9 @@ template <int KIND>
 mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
     constexpr int CM = GEMM_CM;
     auto kern = k_gemm_2sm<KIND>;
-    static int max_pairs = 0;
+    static std::atomic<int> max_pairs_dev[MOFEM_MAX_DEV];   // per device: co-resident pairs
+    std::atomic<int>& max_pairs_slot = max_pairs_dev[dev_slot()];
+    int max_pairs = max_pairs_slot.load(std::memory_order_acquire);
     const int smem = ST2 * STAGE2_BYTES + 1024 + (int)sizeof(PBars2) + 64;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -818,6 +823,7 @@ mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
             return MOFEM_ERR_UNSUPPORTED;
         }
         max_pairs = n;
+        max_pairs_slot.store(n, std::memory_order_release);
     }
     GemmChain ch = ch0;
     if (ch.ns < 1 || ch.ns > CHAIN_MAX ||

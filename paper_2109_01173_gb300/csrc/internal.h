@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cublas_v2.h>
+#include <atomic>
 #include <cstdint>
 #include <vector>
 
@@ -174,6 +175,25 @@ mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const do
 mofem_status launch_residual_update_df(const mofem_ctx* c, const float* dh, const float* dl, double* R,
                                        double* partial, int* nblk, cudaStream_t st);
 int residual_update_df_ctas(int K, int q);   // partials per instance of the above
+
+// One-time launch set-up (function attributes, occupancy queries) is kept per device:
+// a process may drive several GPUs, and the heterogeneous-batch runtime launches from
+// several host threads.
+constexpr int MOFEM_MAX_DEV = 64;
+inline int dev_slot() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MOFEM_MAX_DEV) d = 0;
+    return d;
+}
+// Set the kernel's dynamic shared-memory limit once per device.
+template <typename F>
+inline cudaError_t smem_attr_once(F* kern, int bytes, std::atomic<bool> (&done)[MOFEM_MAX_DEV]) {
+    std::atomic<bool>& d = done[dev_slot()];
+    if (d.load(std::memory_order_acquire)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) d.store(true, std::memory_order_release);
+    return e;
+}
 // B = M_s F M_t^T (right-hand side; F n x n nodal, ld n, FP64; B q x q, b_ld) in double-float
 // arithmetic; MOFEM_ERR_UNSUPPORTED where the tables are missing.
 mofem_status launch_rhs_df(const mofem_ctx* c, const double* F, double* B, long long b_bs, int b_ld, cudaStream_t st);

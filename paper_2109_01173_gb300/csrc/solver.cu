@@ -69,12 +69,29 @@ struct Extra {   // per-handle scratch not in the public struct
 
 }  // namespace
 
-// Extra scratch lives in a side table keyed by handle (keeps mofem_ctx POD-like).
+// Extra scratch lives in a side table keyed by handle (keeps mofem_ctx POD-like).  The
+// table is shared by all handles, which threads may create, use and destroy
+// concurrently: lookups and changes take a lock; an element stays where it is until
+// its handle is freed, so the reference returned is used without it.
 #include <map>
-static std::map<const mofem_ctx*, Extra>& extras() {
+#include <mutex>
+namespace {
+std::mutex& extras_lock() {
+    static std::mutex m;
+    return m;
+}
+std::map<const mofem_ctx*, Extra>& extras_map() {
     static std::map<const mofem_ctx*, Extra> m;
     return m;
 }
+struct ExtrasRef {   // extras()[c]: the handle's entry, created on first use
+    Extra& operator[](const mofem_ctx* c) const {
+        std::lock_guard<std::mutex> g(extras_lock());
+        return extras_map()[c];
+    }
+};
+}  // namespace
+static ExtrasRef extras() { return ExtrasRef{}; }
 
 static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
     Extra& e = extras()[c];
@@ -172,12 +189,17 @@ static mofem_status ensure_apply_maps(mofem_ctx* c, bool fp64) {
 }
 
 void mofem_free_extra(mofem_ctx* c) {
-    auto it = extras().find(c);
-    if (it == extras().end()) return;
-    cudaFree(it->second.cublas_ws);
-    cudaFree(it->second.dir_sc);
-    if (it->second.cap) cudaStreamDestroy(it->second.cap);
-    extras().erase(it);
+    Extra e;
+    {
+        std::lock_guard<std::mutex> g(extras_lock());
+        auto it = extras_map().find(c);
+        if (it == extras_map().end()) return;
+        e = it->second;
+        extras_map().erase(it);
+    }
+    cudaFree(e.cublas_ws);
+    cudaFree(e.dir_sc);
+    if (e.cap) cudaStreamDestroy(e.cap);
 }
 
 // ---- single operations ---------------------------------------------------------
