@@ -55,7 +55,7 @@ double* w64(const mofem_ctx* c, int i) { return c->w64 + per(c) * c->batch * i; 
 
 struct Extra {   // per-handle scratch not in the public struct
     double* res_part = nullptr;   // [batch][n_apply] residual partials
-    double* bb_part = nullptr;    // [batch][n_rz] partials for ||B||^2
+    double* bb_part = nullptr;    // [2][batch][n_rz] partials for ||B||^2 and ||U||^2
     double* ref2 = nullptr;       // [batch] reference norm^2 of the stop test
     double* rz_slots[2] = {nullptr, nullptr};
     void* cublas_ws = nullptr;
@@ -107,7 +107,7 @@ static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
     c->part.n_upd = (int)std::max(1LL, std::min(296LL, (nvec + 1023) / 1024));
     c->part.n_rz = tc_rz_ctas(c);
     const size_t n_total =
-        (size_t)B * (2 * c->part.n_apply + e.n_res_alloc + c->part.n_upd * 2 + c->part.n_rz * 3) + B;
+        (size_t)B * (2 * c->part.n_apply + e.n_res_alloc + c->part.n_upd * 2 + c->part.n_rz * 4) + B;
     MOFEM_CUDA_TRY(cudaMalloc(&c->d_part, n_total * sizeof(double)));
     MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_part, 0, n_total * sizeof(double), st));
     double* p = c->d_part;
@@ -118,7 +118,7 @@ static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
     c->part.rzo = p; p += (size_t)B * c->part.n_upd;
     e.rz_slots[0] = p; p += (size_t)B * c->part.n_rz;
     e.rz_slots[1] = p; p += (size_t)B * c->part.n_rz;
-    e.bb_part = p; p += (size_t)B * c->part.n_rz;
+    e.bb_part = p; p += (size_t)B * c->part.n_rz * 2;   // ||B||^2 and ||U||^2 partials side by side
     e.ref2 = p;
     c->part.rz = e.rz_slots[0];
     MOFEM_CUDA_TRY(cudaMalloc(&c->d_ctr, sizeof(unsigned) * (4 * B + 1)));
@@ -536,16 +536,15 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
     const bool fixed = (c->opts.flags & MOFEM_FLAG_FIXED_ITERS) != 0;
     MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
     MOFEM_CUDA_TRY(cudaEventRecord(c->ev0, st));
-    // reference norms
-    std::vector<double> bb, rr;
+    // reference norm ||B||^2 and ||U||^2 (a zero initial guess needs no FP64 apply: R0 = B),
+    // both read back with one synchronisation
+    std::vector<double> bb, rr, uu, both;
     MOFEM_TRY(launch_dot_partials(c->Bm64, c->Bm64, true, bs, bs, B, e.bb_part, c->part.n_rz, st));
-    MOFEM_TRY(sum_partials(e.bb_part, c->part.n_rz, B, bb, st));
-    // initial residual; a zero initial guess needs no FP64 apply (R0 = B)
-    std::vector<double> uu;
-    MOFEM_TRY(launch_dot_partials(U, U, true, u_bs, (long long)q * q, B, e.bb_part + (size_t)B * c->part.n_rz / 2,
-                                  c->part.n_rz / 2 > 0 ? c->part.n_rz / 2 : 1, st));
-    MOFEM_TRY(sum_partials(e.bb_part + (size_t)B * c->part.n_rz / 2, c->part.n_rz / 2 > 0 ? c->part.n_rz / 2 : 1, B,
-                           uu, st));
+    MOFEM_TRY(launch_dot_partials(U, U, true, u_bs, (long long)q * q, B, e.bb_part + (size_t)B * c->part.n_rz,
+                                  c->part.n_rz, st));
+    MOFEM_TRY(sum_partials(e.bb_part, c->part.n_rz, 2 * B, both, st));
+    bb.assign(both.begin(), both.begin() + B);
+    uu.assign(both.begin() + B, both.end());
     bool zero_guess = true;
     for (int i = 0; i < B; ++i) zero_guess = zero_guess && uu[i] == 0.0;
     if (zero_guess) {
@@ -698,12 +697,14 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
         MOFEM_TRY(launch_convert(c->U64m, 1, bs, ld, U, 1, u_bs, u_ld, q, q, B, st));
     }
     MOFEM_CUDA_TRY(cudaEventRecord(c->ev1, st));
-    MOFEM_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    // status word and scalar state, read back with one synchronisation
+    int dev_status = 0;
+    sc.resize(B);
+    MOFEM_CUDA_TRY(cudaMemcpyAsync(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MOFEM_CUDA_TRY(cudaMemcpyAsync(sc.data(), c->d_sc, sizeof(PcgScalars) * B, cudaMemcpyDeviceToHost, st));
+    MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-    int dev_status = 0;
-    MOFEM_CUDA_TRY(cudaMemcpy(&dev_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-    MOFEM_TRY(read_scalars(c, sc, st));
     int sc_status = 0;
     for (auto& s : sc) sc_status |= s.status;
     dev_status |= sc_status;
@@ -770,10 +771,14 @@ mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const doub
     if (s == MOFEM_OK) s = op_apply(c, true, U1, qq, q, LU, qq, q, nullptr, st);
     if (s == MOFEM_OK) s = op_mass(c, U1, qq, q, MU, qq, q, st);
     std::vector<double> yl, ym;
+    std::vector<double> both;   // <Y, L U> and <Y, M~ U>, read back with one synchronisation
     if (s == MOFEM_OK) s = launch_dot_partials(Y, LU, true, qq, qq, B, e.bb_part, c->part.n_rz, st);
-    if (s == MOFEM_OK) s = sum_partials(e.bb_part, c->part.n_rz, B, yl, st);
-    if (s == MOFEM_OK) s = launch_dot_partials(Y, MU, true, qq, qq, B, e.bb_part, c->part.n_rz, st);
-    if (s == MOFEM_OK) s = sum_partials(e.bb_part, c->part.n_rz, B, ym, st);
+    if (s == MOFEM_OK) s = launch_dot_partials(Y, MU, true, qq, qq, B, e.bb_part + (size_t)B * c->part.n_rz, c->part.n_rz, st);
+    if (s == MOFEM_OK) s = sum_partials(e.bb_part, c->part.n_rz, 2 * B, both, st);
+    if (s == MOFEM_OK) {
+        yl.assign(both.begin(), both.begin() + B);
+        ym.assign(both.begin() + B, both.end());
+    }
     cudaFreeAsync(buf, st);
     MOFEM_TRY(s);
     for (int i = 0; i < B; ++i) dd[i] = -tau * (yl[i] - c->gamma[i] * ym[i]);
