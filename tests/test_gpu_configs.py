@@ -7,14 +7,16 @@
   manufactured u (P1 at h = 1/64: O(h^2) nodal error).
 * Precision form at full size: P2 at n = 1025 and P4 at n = 2049, seeded 32-mode
   Fourier f.  The oracle cannot solve these in seconds, so: sampled operator
-  outputs against the oracle entry by entry, the mixed forms (BF16, TF32, FP16
-  GEMM operands) against the FP64 GPU form (relative difference <= 1e-8), and each
-  solution's residual recomputed with the library's FP64 apply.
+  outputs and every right-hand-side entry against the oracle, the mixed forms
+  (BF16, TF32, FP16 GEMM operands) against the FP64 GPU form (relative difference
+  <= 1e-8), and each solution's residual recomputed with the library's FP64 apply.
+* The bench workload's batched right-hand side (P2 2049, 4 instances) against the
+  oracle, every entry.
 """
 import numpy as np
 import pytest
 
-from oracle.operator import Problem, apply_entry
+from oracle.operator import Problem, apply_entry, rhs
 from oracle import pcg
 from paper_2109_01173_gb300.inputs import config_p1_65, metric_instance
 
@@ -83,8 +85,13 @@ def test_precision_form_full_size(mf, k, n):
     scale = np.abs(Y).max()
     for a, b in pts:
         assert abs(Y[a, b] - apply_entry(terms, X, a, b)) <= 1e-13 * scale, (a, b)
-    # FP64 GPU form, then the mixed forms against it
+    # the right-hand side (double-float on the GPU) against the oracle, every entry
     F = torch.tensor(inst["F"], device="cuda")
+    Bt = torch.zeros((q, q), dtype=torch.float64, device="cuda")
+    h.rhs(F, Bt)
+    Bo = rhs(P, inst["F"])
+    assert np.abs(Bt.cpu().numpy() - Bo).max() <= 1e-13 * np.abs(Bo).max()
+    # FP64 GPU form, then the mixed forms against it
     U64 = torch.zeros((q, q), dtype=torch.float64, device="cuda")
     info64, code64 = h.pcg_solve(F, U64, rtol=1e-10, max_iter=1000, precision="fp64")
     assert code64 == 0
@@ -95,4 +102,20 @@ def test_precision_form_full_size(mf, k, n):
         assert code == 0, prec
         assert float(((U - U64).norm() / U64.norm()).item()) <= 1e-8, prec
         assert _true_rel(h, F, U) <= 1.5e-10, prec
+    h.close()
+
+
+def test_rhs_bench_workload(mf):
+    """The right-hand side of the bench workload (P2, 2049 x 2049 nodes, 4 instances of
+    different seeds, one batched launch) against the oracle, every entry: the double-float
+    evaluation is accurate to ~2^-46 of each entry (mass weights only, no cancellation)."""
+    import torch
+    insts = [metric_instance(n=2049, k=2, seed=s) for s in range(4)]
+    h = mf.Handle([i["g1"] for i in insts], [i["g2"] for i in insts], 2, 2049, [1.0] * 4)
+    F = torch.tensor(np.stack([i["F"] for i in insts]), device="cuda")
+    Bt = torch.zeros((4, h.q, h.q), dtype=torch.float64, device="cuda")
+    h.rhs(F, Bt)
+    for i, inst in enumerate(insts):
+        Bo = rhs(Problem(inst["g1"], inst["g2"], 2, 2049, 1.0), inst["F"])
+        assert np.abs(Bt[i].cpu().numpy() - Bo).max() <= 1e-13 * np.abs(Bo).max(), i
     h.close()
