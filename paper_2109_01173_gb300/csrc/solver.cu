@@ -65,6 +65,7 @@ struct Extra {   // per-handle scratch not in the public struct
     bool maps32 = false, maps64 = false;
     CUtensorMap mZ32, mQA32, mQB32, mS32, mZ64, mQA64, mQB64;   // apply staging maps (PCG form)
     PcgScalars* dir_sc = nullptr;  // [batch] scalars of mofem_pcg_direction (apart from the solver's)
+    int body_kernels[4] = {0, 0, 0, 0};   // kernel nodes of the captured two-iteration body, per precision
 };
 
 }  // namespace
@@ -367,6 +368,20 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     return MOFEM_OK;
 }
 
+// Kernel nodes of a captured graph (its memset nodes not counted).
+static int count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> v(n);
+    if (n && cudaGraphGetNodes(g, v.data(), &n) != cudaSuccess) return 0;
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(v[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 // Build (once per precision) the graph: WHILE(cond) { iteration(0); iteration(1) }.
 static mofem_status build_loop_graph(mofem_ctx* c, mofem_precision prec, int max_iter, bool fixed) {
     Extra& e = extras()[c];
@@ -398,6 +413,7 @@ static mofem_status build_loop_graph(mofem_ctx* c, mofem_precision prec, int max
         return s1;
     }
     MOFEM_CUDA_TRY(ce);
+    e.body_kernels[pi] = count_kernel_nodes(body);
     cudaGraphExec_t ex;
     MOFEM_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
     cudaGraphDestroy(g);
@@ -426,6 +442,7 @@ static mofem_status build_step_graph(mofem_ctx* c, mofem_precision prec, int max
         return s1;
     }
     MOFEM_CUDA_TRY(ce);
+    e.body_kernels[pi] = count_kernel_nodes(g);
     cudaGraphExec_t ex;
     MOFEM_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
     cudaGraphDestroy(g);
@@ -558,14 +575,20 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
     std::vector<double> ref2(B);
     for (int i = 0; i < B; ++i) ref2[i] = ref_is_r0 ? rr[i] : bb[i];
     int total_it = 0, outer = 0;
-    long long launches = 3;   // dot(B,B), residual, (rhs counted by the caller)
-    // kernels per inner solve: init sequence + WHILE bodies of two iterations
-    // (libmofem kernels only; the FP64 form's DGEMMs are cuBLAS kernels and not counted)
-    auto inner_launches = [&](int it, bool fp64) -> long long {
-        const long long per_it = fp64 ? 2 + 2 : (prec == MOFEM_MIXED_TF32 ? 2 + 1 + 4 : 2 + 4);
+    // ||B||^2 and ||U||^2 dots, the FP64 residual of a nonzero guess, the copy of U into
+    // the iterate's layout (the right-hand side is counted by the caller)
+    long long launches = 2 + (zero_guess ? 0 : 1) + 1;
+    // kernels per inner solve: init sequence (dot, init, then the first preconditioner:
+    // operand conversion + GEMM chain, or Hadamard division + dot) + WHILE bodies of two
+    // iterations.  libmofem kernels only: a mixed body is counted from its captured graph
+    // (apply, update, [TF32 operand copy,] GEMM chain per iteration); the FP64 body's
+    // DGEMMs are cuBLAS kernels, so its count is apply, update, division, dot.
+    auto inner_launches = [&](int it, mofem_precision pr) -> long long {
+        const bool fp64 = pr == MOFEM_FP64;
+        const int pb = extras()[c].body_kernels[(int)pr];
+        const long long per_body = fp64 ? 2 * 4 : (pb > 0 ? pb : 2 * (pr == MOFEM_MIXED_TF32 ? 4 : 3));
         const long long bodies = std::max(1, (it + 1) / 2);
-        const long long init = fp64 ? 2 + 2 : 2 + 1 + 4;
-        return init + bodies * 2 * per_it;
+        return 4 + bodies * per_body;
     };
     mofem_status code = MOFEM_OK;
     std::vector<PcgScalars> sc;
@@ -605,7 +628,7 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
             ++outer;
-            launches += inner_launches(it, true) + 2;
+            launches += inner_launches(it, MOFEM_FP64) + 2;
             MOFEM_TRY(launch_convert(w64(c, W64_U), 1, bs, ld, U, 1, u_bs, u_ld, q, q, B, st));
             MOFEM_TRY(op_residual64(c, U, u_bs, u_ld, c->R64, e.res_part, st));
             MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, rr, st));
@@ -661,6 +684,9 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             if (bad && pe == MOFEM_MIXED_FP16) {
                 // FP16 operand range exceeded: redo this step with TF32 operands
                 if (trace) fprintf(stderr, "[mofem] FP16 inner solve non-finite; repeating the step in TF32\n");
+                int it_bad = 0;
+                for (auto& s : sc) it_bad = std::max(it_bad, s.iters);
+                launches += inner_launches(it_bad, pe) + 1;   // + convert R
                 pe = MOFEM_MIXED_TF32;
                 MOFEM_TRY(tc_prepare(c, plan_of(pe), st));
                 continue;
@@ -675,7 +701,7 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
             ++outer;
-            launches += inner_launches(it, false) + 3;   // + convert R, fold, residual
+            launches += inner_launches(it, pe) + 3;   // + convert R, fold, residual
             int nblk = 0;
             mofem_status du = MOFEM_ERR_UNSUPPORTED;
             if (upd)
@@ -712,7 +738,8 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
     else if ((dev_status & DEV_ERR_NONFINITE) || !std::isfinite(rel)) code = MOFEM_ERR_NONFINITE;
     else if (dev_status & DEV_ERR_BREAKDOWN && !(rel <= rtol)) code = MOFEM_ERR_BREAKDOWN;
     else if (!(rel <= rtol) && !fixed && !(stalled && ref_is_r0)) code = MOFEM_ERR_NOT_CONVERGED;
-    return finish_info(c, info, code, total_it, outer, rel, ms, launches + 1);
+    // + the mixed forms' copy of the iterate back into U
+    return finish_info(c, info, code, total_it, outer, rel, ms, launches + (prec == MOFEM_FP64 ? 0 : 1));
 }
 
 mofem_status solver_init(mofem_ctx* c, cudaStream_t st) { return ensure_common(c, st); }
@@ -721,7 +748,9 @@ mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rto
                             mofem_solve_info* info, cudaStream_t st) {
     MOFEM_TRY(ensure_common(c, st));
     MOFEM_TRY(op_rhs(c, F, c->Bm64, (long long)per(c), c->ld, st));
-    return solve_core(c, U, (long long)c->q * c->q, c->q, rtol, max_iter, prec, 0, info, st);
+    const mofem_status r = solve_core(c, U, (long long)c->q * c->q, c->q, rtol, max_iter, prec, 0, info, st);
+    if (info) info->kernel_launches += 1;   // the right-hand side
+    return r;
 }
 
 mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
@@ -742,8 +771,10 @@ mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, 
     if (Unp1 != Un)
         MOFEM_CUDA_TRY(cudaMemcpyAsync(Unp1, Un, sizeof(double) * qq * c->batch, cudaMemcpyDeviceToDevice, st));
     // rtol > 0: ||B - S U||_F <= rtol ||B||_F; else the paper's ||R_s|| <= tau ||R_0|| (Sec. 6)
-    if (rtol > 0) return solve_core(c, Unp1, qq, c->q, rtol, 100000, prec, 0, info, st);
-    return solve_core(c, Unp1, qq, c->q, tau, 100000, prec, 1, info, st);
+    const mofem_status r = rtol > 0 ? solve_core(c, Unp1, qq, c->q, rtol, 100000, prec, 0, info, st)
+                                    : solve_core(c, Unp1, qq, c->q, tau, 100000, prec, 1, info, st);
+    if (info) info->kernel_launches += c->batch + 1;   // the nodal load per instance and the right-hand side
+    return r;
 }
 
 // One backward step of IMEX Euler with f = 0 (discrete adjoint of solve_imex):
