@@ -95,8 +95,7 @@ typedef struct {
                                     per iteration) instead of a device-side conditional loop */
 #define MOFEM_FLAG_FIXED_ITERS 2 /* run exactly max_iter inner iterations (timing runs) */
 #define MOFEM_FLAG_TRUE_RESIDUAL 4 /* mixed forms: recompute B - L(U) in FP64 after every refinement
-                                      step (default: after the first step from a zero guess only,
-                                      later steps update R -= L(d) in double-float arithmetic) */
+                                      step (default: update R -= L(d) in double-float arithmetic) */
 
 typedef struct {
     int status;            /* mofem_status of the whole (batched) solve */
@@ -176,11 +175,14 @@ mofem_status mofem_pcg_direction(mofem_handle h, const void* Z, const void* Q_pr
  * recurrences) until ||B - L(U)||_F <= rtol ||B||_F, checked on the FP64 true
  * residual.  F: n x n per instance (ld n), FP64.  U: q x q per instance (ld q),
  * FP64, in: initial guess, out: solution.  MIXED_*: flexible PCG in FP32 inside
- * FP64 iterative refinement; after a first step from a zero guess the residual is
- * updated (R -= L(d - err), double-float arithmetic, err the exact rounding of the
- * FP64 iterate's update) rather than recomputed, when rtol ||ref|| lies above
- * max(1e-11, 2 u q^2 / pi^2) ||B|| (u = 2^-53; twice the evaluation noise of an FP64
- * residual of this operator); MOFEM_FLAG_TRUE_RESIDUAL recomputes it every step.  max_iter bounds the inner iterations of each
+ * FP64 iterative refinement; after each step the residual is updated (R -= L(d -
+ * err), double-float arithmetic, err the exact rounding of the FP64 iterate's
+ * update) rather than recomputed, when rtol ||ref|| lies above max(1e-11, 2 u q^2 /
+ * pi^2) ||B|| (u = 2^-53; twice the evaluation noise of an FP64 residual of this
+ * operator).  The step from a zero guess, of the size of U, takes the difference
+ * form with exact row sums and input differences (P1 and P2, or an FP64
+ * recomputation for the other degrees); MOFEM_FLAG_TRUE_RESIDUAL recomputes the
+ * residual in FP64 after every step.  max_iter bounds the inner iterations of each
  * refinement step (FP64: of the whole solve).  Synchronises `stream`.
  * info may be NULL. */
 mofem_status mofem_pcg_solve(mofem_handle h, const double* F, double* U, double rtol, int max_iter,
@@ -316,7 +318,9 @@ mofem_status mofem_group_destroy(mofem_group g);
  *   8 = double-float residual update R64 -= L(d) of a refinement step
  *       (MOFEM_ERR_UNSUPPORTED for forms it does not serve),
  *   9 = the preconditioner's four GEMMs as the solver runs them, one chained
- *       launch (prec MIXED_TF32, MIXED_BF16 or MIXED_FP16).
+ *       launch (prec MIXED_TF32, MIXED_BF16 or MIXED_FP16),
+ *  10 = the residual update of 8 in difference form (the step from zero;
+ *       MOFEM_ERR_UNSUPPORTED for forms it does not serve).
  * The buffers' contents are whatever the last solve left (timing only). */
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps,
                                 cudaStream_t stream);

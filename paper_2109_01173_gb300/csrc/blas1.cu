@@ -524,8 +524,10 @@ __global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const d
 // in FP64 and added with one rounding.  With `write_d` the pair is overwritten by
 // the step actually taken, d - err with err = (U + d) - fl(U + d) exact by TwoSum,
 // as a double-float (hi, lo): a residual update R -= L(hi + lo) then tracks
-// B - L(U) of the stored iterate.  16-byte vectors: n % 4 == 0.
-__device__ __forceinline__ double fold_one(double u, float& h, float& l, double ap, float q, bool write_d) {
+// B - L(U) of the stored iterate, up to the pair's rounding of that step (2^-48 of it).
+// Mode 2, for a step from U = 0: the iterate becomes hi + lo itself (exact in FP64),
+// so that the pair is the step to the bit.  16-byte vectors: n % 4 == 0.
+__device__ __forceinline__ double fold_one(double u, float& h, float& l, double ap, float q, int write_d) {
     double d = (double)h + (double)l;
     if (ap != 0.0) d = fma(ap, (double)q, d);
     const double s = u + d;
@@ -538,6 +540,7 @@ __device__ __forceinline__ double fold_one(double u, float& h, float& l, double 
         }
         h = (float)taken;
         l = (float)(taken - (double)h);
+        if (write_d == 2) return u + ((double)h + (double)l);
     }
     return s;
 }
@@ -706,10 +709,11 @@ mofem_status launch_axpy_into64(double* U64, long long u_bs, int u_ld, const flo
 }
 
 mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, const PcgScalars* sc,
-                            const float* Qpend, bool write_d, cudaStream_t st) {
+                            const float* Qpend, int write_d, cudaStream_t st) {
     if (bs % 4 != 0) return MOFEM_ERR_INVALID_ARG;   // internal layout: ld is a multiple of 64
+    if (write_d < 0 || write_d > 2) return MOFEM_ERR_INVALID_ARG;
     dim3 grid(592, batch);
-    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend, write_d ? 1 : 0);
+    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend, write_d);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

@@ -209,7 +209,7 @@ mofem_status mofem_dib_run(mofem_handle h, const mofem_dib_params* p, double rho
 }
 
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps, cudaStream_t stream) {
-    if (!h || kernel < 0 || kernel > 9 || reps < 0 || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
+    if (!h || kernel < 0 || kernel > 10 || reps < 0 || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
     if (kernel >= 1 && kernel <= 4 && prec == MOFEM_FP64) return MOFEM_ERR_INVALID_ARG;
     return bench_kernel(h, kernel, prec, reps, stream);
 }

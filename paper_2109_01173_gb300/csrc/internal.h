@@ -75,6 +75,11 @@ struct mofem_ctx {
     float* S2dup = nullptr;   // [batch][q][2*SR2] FP32 S rows, each coefficient twice (packed apply)
     float* Sdf = nullptr;     // plain S tables as double-float: hi plane then lo plane, each [batch][NT][P][q]
     float* Tdf = nullptr;     // plain T tables as double-float: hi plane then lo plane, each [NT][P][q]
+    // difference-form tables as double-float (same planes and shapes): off the diagonal slot the
+    // plain coefficient, on it the exact row sum of the FP64 coefficients; term 0's t-table holds
+    // N = D^{-1}(M_t - D) off the diagonal and D = rowsum M_t on it (exact mass split)
+    float* Sdd = nullptr;
+    float* Tdd = nullptr;
     float* Srdf = nullptr;    // right-hand-side mass factors as double-float: [hi | lo] of [batch][P][q]
     float* Trdf = nullptr;    // and [hi | lo] of [P][q]
     int s2_row = 0;           // floats per S2dup row
@@ -175,6 +180,11 @@ mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const do
 mofem_status launch_residual_update_df(const mofem_ctx* c, const float* dh, const float* dl, double* R,
                                        double* partial, int* nblk, cudaStream_t st);
 int residual_update_df_ctas(int K, int q);   // partials per instance of the above
+// The same in difference form with exact row sums and exact input differences (the step
+// from U = 0, of the size of U); same grid and partials.  UNSUPPORTED where not served.
+mofem_status launch_residual_update_dfd(const mofem_ctx* c, const float* dh, const float* dl, double* R,
+                                        double* partial, int* nblk, cudaStream_t st);
+bool residual_update_dfd_ok(const mofem_ctx* c);
 
 // One-time launch set-up (function attributes, occupancy queries) is kept per device:
 // a process may drive several GPUs, and the heterogeneous-batch runtime launches from

@@ -378,6 +378,64 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
         MOFEM_TRY(split(Srh, &c->Srdf)); // [hi | lo] planes of [batch][P][q] (right-hand side)
         MOFEM_TRY(split(Trh, &c->Trdf)); // [hi | lo] planes of [P][q]
     }
+    // --- double-float difference-form tables (residual of a step from zero) -------------
+    // The row sum enters exactly (TwoSum accumulation of the FP64 coefficients, then the
+    // (hi, lo) pair of that sum): with differences of the input taken exactly, the only
+    // rounding that a stiffness factor amplifies is then of the size of the differences.
+    {
+        const int P = c->P, K = c->K, NT = c->NT;
+        const unsigned dmask = NT == 5 ? 0x19u : 0xF1u;   // s-passes in difference form
+        auto exact_rowsum = [&](const double* base, int r, double& s, double& e) {
+            s = 0.0;
+            e = 0.0;
+            for (int j = 0; j < P; ++j) {
+                const double a = base[(size_t)j * q + r];
+                const double t = s + a, v = t - s;
+                e += (s - (t - v)) + (a - v);
+                s = t;
+            }
+        };
+        auto put = [](float* hi, float* lo, size_t i, double s, double e) {
+            const float h = (float)s;
+            hi[i] = h;
+            lo[i] = (float)((s - (double)h) + e);
+        };
+        std::vector<float> Sd(2 * Sh.size()), Td(2 * Th.size());
+        float *sh = Sd.data(), *sl = Sd.data() + Sh.size(), *th = Td.data(), *tl = Td.data() + Th.size();
+        for (int t = 0; t < NT; ++t) {
+            const double* base = Th.data() + (size_t)t * P * q;
+            for (int r = 0; r < q; ++r) {
+                double s, e;
+                exact_rowsum(base, r, s, e);
+                const double d = s + e;
+                for (int j = 0; j < P; ++j) {
+                    const size_t o = (size_t)t * P * q + (size_t)j * q + r;
+                    if (j == K) put(th, tl, o, s, e);
+                    else if (t == 0 && NT > 1) put(th, tl, o, d != 0.0 ? base[(size_t)j * q + r] / d : 0.0, 0.0);
+                    else put(th, tl, o, base[(size_t)j * q + r], 0.0);
+                }
+            }
+        }
+        for (int i = 0; i < B; ++i)
+            for (int t = 0; t < NT; ++t) {
+                const size_t b0 = ((size_t)i * NT + t) * P * q;
+                const double* base = Sh.data() + b0;
+                for (int r = 0; r < q; ++r) {
+                    double s = 0.0, e = 0.0;
+                    const bool diff = (dmask >> t) & 1u;
+                    if (diff) exact_rowsum(base, r, s, e);
+                    for (int j = 0; j < P; ++j) {
+                        const size_t o = b0 + (size_t)j * q + r;
+                        if (diff && j == K) put(sh, sl, o, s, e);
+                        else put(sh, sl, o, base[(size_t)j * q + r], 0.0);
+                    }
+                }
+            }
+        MOFEM_TRY(dev_alloc(&c->Sdd, Sd.size()));
+        MOFEM_CUDA_TRY(cudaMemcpy(c->Sdd, Sd.data(), Sd.size() * sizeof(float), cudaMemcpyHostToDevice));
+        MOFEM_TRY(dev_alloc(&c->Tdd, Td.size()));
+        MOFEM_CUDA_TRY(cudaMemcpy(c->Tdd, Td.data(), Td.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
 
     // --- upload tables (difference form: row sum in the diagonal slot) -------------
     auto rowsum_one = [&](double* base) {
@@ -523,7 +581,7 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
 }
 
 void mofem_free(mofem_ctx* c) {
-    void* ptrs[] = {c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->Srdf, c->Trdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
+    void* ptrs[] = {c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->Sdd, c->Tdd, c->Srdf, c->Trdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
                     c->lam32, c->mu32, c->w64, c->w32, c->Bm64, c->R64, c->d_part, c->d_sc, c->d_status,
                     c->d_red};
     for (void* p : ptrs) cudaFree(p);

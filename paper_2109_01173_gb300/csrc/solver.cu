@@ -33,7 +33,7 @@ mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo
                                bool fixed, const cudaGraphConditionalHandle* cond, cudaStream_t st,
                                bool use_scalars = true, const void* Qprev = nullptr, int lazy_phase = -1);
 mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int batch, const PcgScalars* sc,
-                            const float* Qpend, bool write_d, cudaStream_t st);
+                            const float* Qpend, int write_d, cudaStream_t st);
 mofem_status launch_scale_copy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld,
                                  int rows, int cols, int batch, double scale, cudaStream_t st);
 mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int n_rr, const double* ref2, double rtol,
@@ -691,12 +691,16 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
                 MOFEM_TRY(tc_prepare(c, plan_of(pe), st));
                 continue;
             }
-            // R after this step: recomputed in FP64 after a first step from zero (cancellation
-            // against B), else updated R -= L(d - err) in double-float arithmetic, err the
-            // fold's rounding of U + d (the fold leaves d - err in the correction pair)
-            const bool upd = df_update && (outer >= 1 || !zero_guess);
+            // R after this step, updated R -= L(d - err) in double-float arithmetic, err the
+            // fold's rounding of U + d (the fold leaves d - err in the correction pair).  A step
+            // from zero (d of the size of U; R cancels to ~1e-5 of B) takes the difference form
+            // with exact row sums and differences, the iterate set to the pair itself; where
+            // that form is not served, R is recomputed in FP64.
+            const bool from_zero = outer == 0 && zero_guess;
+            const bool upd = df_update && (!from_zero || residual_update_dfd_ok(c));
+            const int dmode = !upd ? 0 : (from_zero ? 2 : 1);
             // even iterations leave alpha Q_a pending (lazy correction): the fold adds it
-            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, c->d_sc, w32(c, W32_QA), upd, st));
+            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, c->d_sc, w32(c, W32_QA), dmode, st));
             int it = 0;
             for (auto& s : sc) it = std::max(it, s.iters);
             total_it += it;
@@ -705,7 +709,8 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
             int nblk = 0;
             mofem_status du = MOFEM_ERR_UNSUPPORTED;
             if (upd)
-                du = launch_residual_update_df(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, e.res_part, &nblk, st);
+                du = from_zero ? launch_residual_update_dfd(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, e.res_part, &nblk, st)
+                               : launch_residual_update_df(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, e.res_part, &nblk, st);
             if (du == MOFEM_OK) {
                 MOFEM_TRY(sum_partials(e.res_part, nblk, B, rr, st));
             } else {
@@ -916,6 +921,13 @@ mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int re
         for (int r = 0; r < reps; ++r)
             MOFEM_TRY(tc_precond(c, which, w32(c, W32_R), bs, c->ld, w32(c, W32_Z), c->ld, bs, extras()[c].rz_slots[0],
                                  nullptr, st, true));
+        return MOFEM_OK;
+    }
+    if (kernel == 10) {   // the same update in difference form (the step from zero)
+        int nblk = 0;
+        for (int r = 0; r < reps; ++r)
+            MOFEM_TRY(launch_residual_update_dfd(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, extras()[c].res_part,
+                                                 &nblk, st));
         return MOFEM_OK;
     }
     if (kernel == 8) {   // double-float residual update of a refinement step

@@ -386,18 +386,18 @@ def _solve_both(mf, g1, g2, k, n, gam, bc, F, prec, rtol=1e-10):
 
 
 def test_residual_update_full_size(mf):
-    """Bench workload (P2, 2049 x 2049 nodes, 4 instances, rtol 1e-10).  Both runs
-    take the same steps, so the iterates are bitwise equal; the reported residuals
-    differ only by the evaluation noise of the FP64 recomputations that anchor
-    them (u q^2 / pi^2 = 4.7e-11 of ||B|| at q = 2047, the t-pass intermediate
-    rounded to FP64 and then second-differenced); the target holds on the
-    recomputed residual."""
+    """Bench workload (P2, 2049 x 2049 nodes, 4 instances, rtol 1e-10).  The two runs
+    agree to 1e-8 (their first steps' residuals differ by the FP64 evaluation noise, so
+    the later inner solves start from slightly different right-hand sides); each reported
+    residual differs from an FP64 recomputation only by that recomputation's evaluation
+    noise (u q^2 / pi^2 = 4.7e-11 of ||B|| at q = 2047, the t-pass mass product rounded to
+    FP64 and then second-differenced); the target holds on the recomputed residual."""
     torch = torch_()
     insts = [metric_instance(n=2049, k=2, seed=s) for s in range(4)]
     F = torch.tensor(np.stack([i["F"] for i in insts]), device="cuda")
     (U0, rep0, rel0), (U1, rep1, rel1) = _solve_both(mf, [i["g1"] for i in insts], [i["g2"] for i in insts], 2,
                                                      2049, [1.0] * 4, 0, F, "fp16")
-    assert torch.equal(U0, U1)
+    assert float(((U0 - U1).norm() / U1.norm()).item()) <= 1e-8
     assert max(rel0) <= 1e-10
     assert abs(max(rel1) - rep1) <= 1e-13, (rep1, rel1)
     noise = 2.0 ** -53 * 2047 ** 2 / np.pi ** 2
@@ -414,9 +414,94 @@ def test_residual_update_tracks_recomputed(mf, k, n, dname, bc, gamma):
     g1, g2 = dom(dname)
     F = torch.tensor(fourier_f(g1, g2, n, seed=n), device="cuda").unsqueeze(0)
     (U0, rep0, rel0), (U1, rep1, rel1) = _solve_both(mf, [g1], [g2], k, n, [gamma], bc, F, "bf16")
-    assert torch.equal(U0, U1)
+    assert float(((U0 - U1).norm() / U1.norm()).item()) <= 1e-8
     assert abs(rel0[0] - rep0) <= 2e-12, (rep0, rel0)
     assert abs(rel1[0] - rep1) <= 1e-13, (rep1, rel1)
+
+
+def _two_prod(a, b):
+    """a * b = p + e exactly (Dekker's product with Veltkamp's split; no FMA needed)."""
+    def split(x):
+        c = 134217729.0 * x
+        hi = c - (c - x)
+        return hi, x - hi
+    p = a * b
+    ah, al = split(a)
+    bh, bl = split(b)
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def _two_sum(a, b):
+    s = a + b
+    v = s - a
+    return s, (a - (s - v)) + (b - v)
+
+
+def _shift(X, off, axis):
+    """Y[.., i] = X[.., i + off] along axis, zero outside."""
+    Y = np.zeros_like(X)
+    n = X.shape[axis]
+    src = [slice(None)] * 2
+    dst = [slice(None)] * 2
+    if off >= 0:
+        src[axis], dst[axis] = slice(off, n), slice(0, n - off)
+    else:
+        src[axis], dst[axis] = slice(0, n + off), slice(-off, n)
+    Y[tuple(dst)] = X[tuple(src)]
+    return Y
+
+
+def _residual_dd(S, T, K, B, U):
+    """B - sum_i S_i U T_i^T for band tables S, T [term][slot][row] (slot j of row r:
+    column r + j - K), in double-double arithmetic (products exact, sums with their
+    errors carried): accurate to far below the FP64 rounding of U's apply."""
+    P = 2 * K + 1
+    yh = np.zeros_like(U)
+    yl = np.zeros_like(U)
+    for i in range(S.shape[0]):
+        vh = np.zeros_like(U)
+        vl = np.zeros_like(U)
+        for l in range(P):
+            p, e = _two_prod(T[i][l][None, :], _shift(U, l - K, 1))
+            vh, t = _two_sum(vh, p)
+            vl = vl + (t + e)
+        vh, vl = _two_sum(vh, vl)
+        for j in range(P):
+            c = S[i][j][:, None]
+            p, e = _two_prod(c, _shift(vh, j - K, 0))
+            yh, t = _two_sum(yh, p)
+            yl = yl + (t + e + c * _shift(vl, j - K, 0))
+    r, t = _two_sum(B, -yh)
+    return r + (t - yl)
+
+
+@pytest.mark.parametrize("k,n", [(2, 2049), (1, 1025)])
+def test_first_step_residual_double_float(mf, k, n):
+    """One refinement step from zero: the residual B - L(U) that the solver carries
+    (double-float difference form with exact row sums and input differences) against
+    the same residual of the same iterate in double-double arithmetic on the library's
+    own FP64 coefficients.  The step cancels R to ~1e-5 of B; the carried norm agrees to
+    5e-12 of ||B|| (evaluation error ~2^-48 q), below the FP64 evaluation's own noise
+    (u q^2 / pi^2, 4.7e-11 at q = 2047), which the recomputed residual shows."""
+    torch = torch_()
+    inst = metric_instance(n=n, k=k, seed=1)
+    h = mf.Handle(inst["g1"], inst["g2"], k, n, 1.0, opts=mf.make_opts(max_outer=1))
+    q = h.q
+    F = torch.tensor(inst["F"], device="cuda")
+    U = torch.zeros((q, q), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(F, U, rtol=1e-10, max_iter=500, precision="fp16", check=False)
+    assert info.outer_steps == 1 and 1e-7 < info.rel_residual < 1e-3
+    Bt = torch.zeros_like(U)
+    h.rhs(F, Bt)
+    B = Bt.cpu().numpy()
+    tb = mf.host_tables(inst["g1"], inst["g2"], k, n, 1.0)
+    R = _residual_dd(tb["S"], tb["T"], tb["K"], B, U.cpu().numpy())
+    bn = np.linalg.norm(B)
+    ref = np.linalg.norm(R) / bn
+    assert abs(info.rel_residual - ref) <= 5e-12, (info.rel_residual, ref)
+    rel64 = _true_rel(h, F.unsqueeze(0), U.unsqueeze(0))[0]   # FP64 GPU recomputation
+    assert abs(rel64 - ref) <= 2 * 2.0 ** -53 * q * q / np.pi ** 2, (rel64, ref)
+    h.close()
 
 
 def test_residual_update_nonzero_guess(mf):
