@@ -525,8 +525,7 @@ __global__ void k_hadamard_div64(double* W, long long bs, int ld, int q, const d
 // the step actually taken, d - err with err = (U + d) - fl(U + d) exact by TwoSum,
 // as a double-float (hi, lo): a residual update R -= L(hi + lo) then tracks
 // B - L(U) of the stored iterate, up to the pair's rounding of that step (2^-48 of it).
-// Mode 2, for a step from U = 0: the iterate becomes hi + lo itself (exact in FP64),
-// so that the pair is the step to the bit.  16-byte vectors: n % 4 == 0.
+// 16-byte vectors: n % 4 == 0.  (Mode 2, a step from U = 0, is k_fold_zero.)
 __device__ __forceinline__ double fold_one(double u, float& h, float& l, double ap, float q, int write_d) {
     double d = (double)h + (double)l;
     if (ap != 0.0) d = fma(ap, (double)q, d);
@@ -540,7 +539,6 @@ __device__ __forceinline__ double fold_one(double u, float& h, float& l, double 
         }
         h = (float)taken;
         l = (float)(taken - (double)h);
-        if (write_d == 2) return u + ((double)h + (double)l);
     }
     return s;
 }
@@ -568,6 +566,65 @@ __global__ void k_fold_df(double* U, long long bs, float* hi, float* lo, long lo
             h4[i] = h;
             l4[i] = l;
         }
+    }
+}
+
+// The fold of a step from U = 0 (mode 2 of launch_fold_df): the step d = hi + lo
+// (+ alpha_pend Q_pend) formed in double-float arithmetic on the FP32 pipes, its low
+// part rounded onto the FP64 grid of its high part (multiples of 2^(e_hi - 52)), so that
+// hi + lo is exact in FP64.  The iterate becomes that sum and the pair is rewritten as
+// the step itself: one FP64 add and two conversions per element (this GPU's FP64 rate
+// is a small fraction of its FP32 rate).  |hi| < 2^-97 keeps hi alone.
+__device__ __forceinline__ double fold_zero_one(float& h, float& l, float aph, float apl, float q, bool pend) {
+    float s, lo;
+    {   // the accumulated pair may be unnormalised: TwoSum first
+        s = h + l;
+        const float v = s - h;
+        lo = (h - (s - v)) + (l - v);
+    }
+    if (pend) {   // + (aph + apl) q: exact high product, its error and the low product into lo
+        const float p = aph * q;
+        float e = fmaf(aph, q, -p);
+        e = fmaf(apl, q, e);
+        const float t = s + p, v = t - s;
+        const float r = (s - (t - v)) + (p - v);
+        s = t;
+        lo = (lo + e) + r;
+    }
+    const float H = s + lo, v = H - s;
+    float L = (s - (H - v)) + (lo - v);
+    if (H != 0.f) {
+        const int eh = ilogbf(H);
+        L = eh >= -97 ? ldexpf(rintf(ldexpf(L, 52 - eh)), eh - 52) : 0.f;
+    }
+    h = H;
+    l = L;
+    return (double)H + (double)L;
+}
+
+__global__ void k_fold_zero(double* U, long long bs, float* hi, float* lo, long long n, const PcgScalars* sc,
+                            const float* Qpend) {
+    const int inst = blockIdx.y;
+    const double ap = sc ? sc[inst].alpha_pend : 0.0;
+    const float aph = (float)ap, apl = (float)(ap - (double)aph);
+    const bool pend = ap != 0.0;
+    double2* U2 = reinterpret_cast<double2*>(U + (size_t)inst * bs);
+    float4* h4 = reinterpret_cast<float4*>(hi + (size_t)inst * bs);
+    float4* l4 = reinterpret_cast<float4*>(lo + (size_t)inst * bs);
+    const float4* q4 = reinterpret_cast<const float4*>(Qpend + (size_t)inst * bs);
+    const long long nv = n / 4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+        float4 h = h4[i], l = l4[i];
+        const float4 q = pend ? q4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        double2 a, b;
+        a.x = fold_zero_one(h.x, l.x, aph, apl, q.x, pend);
+        a.y = fold_zero_one(h.y, l.y, aph, apl, q.y, pend);
+        b.x = fold_zero_one(h.z, l.z, aph, apl, q.z, pend);
+        b.y = fold_zero_one(h.w, l.w, aph, apl, q.w, pend);
+        U2[2 * i] = a;
+        U2[2 * i + 1] = b;
+        h4[i] = h;
+        l4[i] = l;
     }
 }
 
@@ -713,7 +770,10 @@ mofem_status launch_fold_df(double* U64, float* hi, float* lo, long long bs, int
     if (bs % 4 != 0) return MOFEM_ERR_INVALID_ARG;   // internal layout: ld is a multiple of 64
     if (write_d < 0 || write_d > 2) return MOFEM_ERR_INVALID_ARG;
     dim3 grid(592, batch);
-    k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend, write_d);
+    if (write_d == 2)   // the iterate is zero before this fold: not read
+        k_fold_zero<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend);
+    else
+        k_fold_df<<<grid, 256, 0, st>>>(U64, bs, hi, lo, bs, sc, Qpend, write_d);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }
