@@ -5,12 +5,14 @@
 // for the step d of one refinement step, given as a double-float pair (dh, dl):
 // the FP64 iterate's actual change fl(U + d') - U, which the fold of the inner
 // solve's correction d' leaves in the correction buffers, so that R tracks
-// B - L(U) of the stored iterate.  From the second refinement step on this
-// replaces the FP64 recomputation R = B - L(U): |d| is ~1e-5 |U| there, so an
-// evaluation of L(d) with ~2^-44 relative arithmetic is accurate to ~1e-13 of
-// ||B||, and it runs on the FP32 pipes (FP64 throughput on this GPU is a small
-// fraction of FP32).  Plain (not difference) form: the coefficient tables are the
-// plain banded factors split into FP32 (hi, lo) pairs at setup.
+// B - L(U) of the stored iterate, in place of an FP64 recomputation R = B - L(U)
+// (FP64 throughput on this GPU is a small fraction of FP32).  Two kernels:
+//   k_resid_df   plain form, for steps after the first: |d| is ~1e-5 |U| there, so
+//                an evaluation of L(d) with ~2^-44 relative arithmetic is accurate to
+//                ~1e-13 of ||B||; tables: the plain banded factors split into FP32
+//                (hi, lo) pairs at setup;
+//   k_resid_dfd  difference form, for the step from zero (d of the size of U; see
+//                its own comment).
 //
 // Arithmetic: each product (ah + al)(bh + bl) as ah*bh exactly (FMA residual) plus
 // the two cross terms; sums of a chain (2K+1 products, or the NT term results)

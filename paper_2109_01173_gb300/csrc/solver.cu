@@ -649,14 +649,15 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
         // straight at rtol, no deeper than eta0 / 10.  Two FP64 residuals instead of
         // three for rtol = 1e-10 on that workload.
         const double eta0 = c->opts.inner_rtol > 0 ? c->opts.inner_rtol : 1e-5;
-        // The residual update tracks B - L(U) of the FP64 iterate up to its double-float
-        // evaluation error (~1e-13 ||B|| for a correction of 1e-5 ||U||) plus the
-        // evaluation noise of the last FP64 recomputation.  That noise (the t-pass
-        // intermediate rounded to FP64, then second-differenced) is ~u q^2 / pi^2 of
-        // ||B||, 4.7e-11 at q = 2047; an FP64 recomputation would carry the same.  Below
-        // twice that level (or 1e-11) a recomputation's stall is the honest verdict, so
-        // such targets, and the MOFEM_FLAG_TRUE_RESIDUAL flag, recompute B - L(U) after
-        // every step.
+        // The residual updates track B - L(U) of the FP64 iterate up to their double-float
+        // evaluation errors: ~2^-48 q of ||B|| for the step from zero (difference form,
+        // 1e-12 at q = 2047), ~1e-13 for a later correction of 1e-5 ||U||; where the
+        // difference form is not served, the anchor is an FP64 recomputation.  An FP64
+        // evaluation (the t-pass mass product rounded to FP64, then second-differenced)
+        // carries ~u q^2 / pi^2 of ||B||, 4.7e-11 at q = 2047: targets below twice that
+        // level (or 1e-11) are beyond what an FP64 check of the result could confirm, so
+        // such targets, and the MOFEM_FLAG_TRUE_RESIDUAL flag, recompute B - L(U) in FP64
+        // after every step, where a stall is the verdict that check would give.
         const double floor_est = std::max(1e-11, 2.0 * 0x1p-53 * (double)q * q / (M_PI * M_PI));
         bool df_update = (c->opts.flags & MOFEM_FLAG_TRUE_RESIDUAL) == 0;
         for (int i = 0; i < B; ++i) df_update = df_update && rtol * rtol * ref2[i] >= floor_est * floor_est * bb[i];
