@@ -367,6 +367,20 @@ mofem_status mofem_host_tables(const mofem_profile* g1, const mofem_profile* g2,
                                double gamma, mofem_bc bc, const mofem_opts* opts, int* n_terms, int* q,
                                double* S, double* T, double* Srh, double* Trh);
 
+/* Host-only view of the double-float difference-form tables that the residual update
+ * of a refinement step from zero reads (no device work; no counterpart in the paper:
+ * the operator of Sec. 5 written in difference form for double-float evaluation).
+ * S, T: FP32, a hi plane then a lo plane, each [n_terms][2K+1][q] as in
+ * mofem_host_tables (caller-allocated, 2 x n_terms x (2K+1) x q floats; either may be
+ * NULL).  Off the diagonal slot K: the FP64 coefficient c as (hi, lo) = (fl32(c),
+ * fl32(c - hi)).  On slot K: the row sum of the FP64 coefficients, exact before one
+ * rounding to (hi, lo), in every T table and in the S tables of the terms whose s-pass
+ * runs in difference form (terms 0, 3, 4 of five; 0, 4..7 of eight), the plain
+ * diagonal coefficient in the others.  T table 0 (the mass M_t of term 0) holds
+ * N = D^-1 (M_t - D) off the diagonal and D = rowsum M_t on it. */
+mofem_status mofem_host_dd_tables(const mofem_profile* g1, const mofem_profile* g2, int k, int n_nodes,
+                                  double gamma, mofem_bc bc, const mofem_opts* opts, float* S, float* T);
+
 #ifdef __cplusplus
 }
 #endif

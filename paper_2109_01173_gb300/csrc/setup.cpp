@@ -335,6 +335,68 @@ static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mo
     return MOFEM_OK;
 }
 
+// Double-float difference-form tables from the plain FP64 tables S [B][NT][P][q] and
+// T [NT][P][q]: each output is a hi plane followed by a lo plane of the same shape.  Off
+// the diagonal slot: the coefficient split into (hi, lo).  On it: the exact row sum of
+// the FP64 coefficients (TwoSum accumulation, then its (hi, lo) pair) for every t-table
+// and for the s-tables of the terms whose s-pass runs in difference form (0, 3, 4 of
+// five terms; 0, 4..7 of eight), the plain diagonal coefficient for the others.  Term
+// 0's t-table holds N = D^{-1}(M_t - D) off the diagonal and D = rowsum M_t on it (the
+// exact mass split of d M_t^T = D (d + d N^T)).  The row sum enters exactly so that,
+// with differences of the input taken exactly, no rounding that a stiffness factor
+// amplifies is larger than the differences themselves.
+static void build_dd_tables(const std::vector<double>& Sh, const std::vector<double>& Th, int B, int NT, int P, int K,
+                     int q, std::vector<float>& Sd, std::vector<float>& Td) {
+    const unsigned dmask = NT == 5 ? 0x19u : 0xF1u;   // s-passes in difference form
+    auto exact_rowsum = [&](const double* base, int r, double& s, double& e) {
+        s = 0.0;
+        e = 0.0;
+        for (int j = 0; j < P; ++j) {
+            const double a = base[(size_t)j * q + r];
+            const double t = s + a, v = t - s;
+            e += (s - (t - v)) + (a - v);
+            s = t;
+        }
+    };
+    auto put = [](float* hi, float* lo, size_t i, double s, double e) {
+        const float h = (float)s;
+        hi[i] = h;
+        lo[i] = (float)((s - (double)h) + e);
+    };
+    Sd.assign(2 * Sh.size(), 0.f);
+    Td.assign(2 * Th.size(), 0.f);
+    float *sh = Sd.data(), *sl = Sd.data() + Sh.size(), *th = Td.data(), *tl = Td.data() + Th.size();
+    for (int t = 0; t < NT; ++t) {
+        const double* base = Th.data() + (size_t)t * P * q;
+        for (int r = 0; r < q; ++r) {
+            double s, e;
+            exact_rowsum(base, r, s, e);
+            const double d = s + e;
+            for (int j = 0; j < P; ++j) {
+                const size_t o = (size_t)t * P * q + (size_t)j * q + r;
+                if (j == K) put(th, tl, o, s, e);
+                else if (t == 0 && NT > 1) put(th, tl, o, d != 0.0 ? base[(size_t)j * q + r] / d : 0.0, 0.0);
+                else put(th, tl, o, base[(size_t)j * q + r], 0.0);
+            }
+        }
+    }
+    for (int i = 0; i < B; ++i)
+        for (int t = 0; t < NT; ++t) {
+            const size_t b0 = ((size_t)i * NT + t) * P * q;
+            const double* base = Sh.data() + b0;
+            const bool diff = (dmask >> t) & 1u;
+            for (int r = 0; r < q; ++r) {
+                double s = 0.0, e = 0.0;
+                if (diff) exact_rowsum(base, r, s, e);
+                for (int j = 0; j < P; ++j) {
+                    const size_t o = b0 + (size_t)j * q + r;
+                    if (diff && j == K) put(sh, sl, o, s, e);
+                    else put(sh, sl, o, base[(size_t)j * q + r], 0.0);
+                }
+            }
+        }
+}
+
 // Builds every table of the handle; c->{batch,k,n,bc,opts} are set by the caller.
 mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_profile* g2,
                          const double* gamma, cudaStream_t st) {
@@ -379,58 +441,9 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
         MOFEM_TRY(split(Trh, &c->Trdf)); // [hi | lo] planes of [P][q]
     }
     // --- double-float difference-form tables (residual of a step from zero) -------------
-    // The row sum enters exactly (TwoSum accumulation of the FP64 coefficients, then the
-    // (hi, lo) pair of that sum): with differences of the input taken exactly, the only
-    // rounding that a stiffness factor amplifies is then of the size of the differences.
     {
-        const int P = c->P, K = c->K, NT = c->NT;
-        const unsigned dmask = NT == 5 ? 0x19u : 0xF1u;   // s-passes in difference form
-        auto exact_rowsum = [&](const double* base, int r, double& s, double& e) {
-            s = 0.0;
-            e = 0.0;
-            for (int j = 0; j < P; ++j) {
-                const double a = base[(size_t)j * q + r];
-                const double t = s + a, v = t - s;
-                e += (s - (t - v)) + (a - v);
-                s = t;
-            }
-        };
-        auto put = [](float* hi, float* lo, size_t i, double s, double e) {
-            const float h = (float)s;
-            hi[i] = h;
-            lo[i] = (float)((s - (double)h) + e);
-        };
-        std::vector<float> Sd(2 * Sh.size()), Td(2 * Th.size());
-        float *sh = Sd.data(), *sl = Sd.data() + Sh.size(), *th = Td.data(), *tl = Td.data() + Th.size();
-        for (int t = 0; t < NT; ++t) {
-            const double* base = Th.data() + (size_t)t * P * q;
-            for (int r = 0; r < q; ++r) {
-                double s, e;
-                exact_rowsum(base, r, s, e);
-                const double d = s + e;
-                for (int j = 0; j < P; ++j) {
-                    const size_t o = (size_t)t * P * q + (size_t)j * q + r;
-                    if (j == K) put(th, tl, o, s, e);
-                    else if (t == 0 && NT > 1) put(th, tl, o, d != 0.0 ? base[(size_t)j * q + r] / d : 0.0, 0.0);
-                    else put(th, tl, o, base[(size_t)j * q + r], 0.0);
-                }
-            }
-        }
-        for (int i = 0; i < B; ++i)
-            for (int t = 0; t < NT; ++t) {
-                const size_t b0 = ((size_t)i * NT + t) * P * q;
-                const double* base = Sh.data() + b0;
-                for (int r = 0; r < q; ++r) {
-                    double s = 0.0, e = 0.0;
-                    const bool diff = (dmask >> t) & 1u;
-                    if (diff) exact_rowsum(base, r, s, e);
-                    for (int j = 0; j < P; ++j) {
-                        const size_t o = b0 + (size_t)j * q + r;
-                        if (diff && j == K) put(sh, sl, o, s, e);
-                        else put(sh, sl, o, base[(size_t)j * q + r], 0.0);
-                    }
-                }
-            }
+        std::vector<float> Sd, Td;
+        build_dd_tables(Sh, Th, B, c->NT, c->P, c->K, q, Sd, Td);
         MOFEM_TRY(dev_alloc(&c->Sdd, Sd.size()));
         MOFEM_CUDA_TRY(cudaMemcpy(c->Sdd, Sd.data(), Sd.size() * sizeof(float), cudaMemcpyHostToDevice));
         MOFEM_TRY(dev_alloc(&c->Tdd, Td.size()));
@@ -617,5 +630,21 @@ extern "C" mofem_status mofem_host_tables(const mofem_profile* g1, const mofem_p
     if (T) std::memcpy(T, H.T.data(), H.T.size() * sizeof(double));
     if (Srh) std::memcpy(Srh, H.Srh.data(), H.Srh.size() * sizeof(double));
     if (Trh) std::memcpy(Trh, H.Trh.data(), H.Trh.size() * sizeof(double));
+    return MOFEM_OK;
+}
+
+extern "C" mofem_status mofem_host_dd_tables(const mofem_profile* g1, const mofem_profile* g2, int k, int n_nodes,
+                                             double gamma, mofem_bc bc, const mofem_opts* opts, float* S, float* T) {
+    if (!g1 || !g2 || k < 0 || k > 4 || n_nodes < 3) return MOFEM_ERR_INVALID_ARG;
+    const int d = k == 0 ? 1 : k;
+    if ((n_nodes - 1) % d != 0) return MOFEM_ERR_INVALID_ARG;
+    mofem_opts o{};
+    if (opts) o = *opts;
+    HostTables H;
+    MOFEM_TRY(build_host_tables(1, k, n_nodes, bc, o, g1, g2, &gamma, H));
+    std::vector<float> Sd, Td;
+    build_dd_tables(H.S, H.T, 1, H.NT, H.P, H.K, H.q, Sd, Td);
+    if (S) std::memcpy(S, Sd.data(), Sd.size() * sizeof(float));
+    if (T) std::memcpy(T, Td.data(), Td.size() * sizeof(float));
     return MOFEM_OK;
 }

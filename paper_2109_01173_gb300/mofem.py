@@ -95,6 +95,7 @@ def _load():
         "mofem_bench_kernel": [vp, c_int, c_int, c_int, vp],
         "mofem_host_tables": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), P(c_int), P(c_int),
                               vp, vp, vp, vp],
+        "mofem_host_dd_tables": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -114,7 +115,7 @@ EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply
             "mofem_dib_kinetics", "mofem_dib_run", "mofem_dib_equilibrium", "mofem_group_layout",
             "mofem_group_setup", "mofem_group_solve", "mofem_group_autotune", "mofem_group_destroy",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
-            "mofem_host_tables", "mofem_bench_kernel"]
+            "mofem_host_tables", "mofem_host_dd_tables", "mofem_bench_kernel"]
 
 
 def _check(fn, code):
@@ -165,6 +166,22 @@ def host_tables(g1, g2, k, n, gamma, bc=DIRICHLET, opts=None):
                                  Sr.ctypes.data, Tr.ctypes.data)
     _check("mofem_host_tables", code)
     return dict(n_terms=nt.value, q=qq.value, S=S[:nt.value], T=T[:nt.value], Srh=Sr, Trh=Tr, K=d)
+
+
+def host_dd_tables(g1, g2, k, n, gamma, bc=DIRICHLET, opts=None):
+    """Double-float difference-form tables (hi, lo planes) computed on the host by the
+    library: dict(S_hi, S_lo, T_hi, T_lo), each [n_terms][2K+1][q] float32."""
+    base = host_tables(g1, g2, k, n, gamma, bc, opts)
+    nt, q, P = base["n_terms"], base["q"], 2 * base["K"] + 1
+    p1, k1 = make_profile(g1)
+    p2, k2 = make_profile(g2)
+    S = np.zeros((2, nt, P, q), dtype=np.float32)
+    T = np.zeros((2, nt, P, q), dtype=np.float32)
+    o = opts or make_opts()
+    code = LIB.mofem_host_dd_tables(ctypes.byref(p1), ctypes.byref(p2), k, n, gamma, bc, ctypes.byref(o),
+                                    S.ctypes.data, T.ctypes.data)
+    _check("mofem_host_dd_tables", code)
+    return dict(S_hi=S[0], S_lo=S[1], T_hi=T[0], T_lo=T[1], base=base)
 
 
 class Handle:
