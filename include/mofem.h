@@ -102,7 +102,11 @@ typedef struct {
     int iterations;        /* total inner PCG iterations (max over instances) */
     int outer_steps;       /* FP64 refinement steps (mixed form); 1 for FP64 */
     int batch;
-    double rel_residual;   /* max over instances of ||B - L(U)||_F / ||B||_F, FP64, recomputed at exit */
+    double rel_residual;   /* max over instances of ||B - L(U)||_F / ||B||_F (IMEX rule: / ||R_0||_F) of
+                              the returned U: the FP64 form's recomputed residual; the mixed forms'
+                              residual carried by the double-float updates (exact up to their
+                              evaluation error, ~2^-48 q of ||B||), or recomputed in FP64 where
+                              mofem_pcg_solve says so */
     double ms_total;       /* device time of the solve (CUDA events) */
     long long kernel_launches; /* libmofem kernels launched by the solve (graph nodes included) */
 } mofem_solve_info;
