@@ -369,7 +369,11 @@ def run_mofem(a):
         prec_k = a.precision if a.precision != "fp64" else "fp16"
         torch.cuda.nvtx.range_push("hot_kernels")
         for kid in (1, 2, 3, 4, 9, 10, 8, 0, 5, 7):
-            h.bench_kernel(kid, prec_k, 1)
+            try:
+                h.bench_kernel(kid, prec_k, 1)
+            except RuntimeError:
+                if kid not in (8, 10):   # the double-float updates serve some (k, terms) forms only
+                    raise
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         h.close()
