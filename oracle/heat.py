@@ -31,7 +31,8 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .fem1d import trim
-from .operator import Problem
+from .operator import Problem, apply_terms, rhs
+from .pcg import ProductPreconditioner, mo_pcg, fro
 
 
 def kron_operator(terms):
@@ -91,3 +92,39 @@ def loss(UN, target):
     """J = ||U_N - U_target||_F^2 and dJ/dU_N."""
     D = np.asarray(UN) - np.asarray(target)
     return float(np.sum(D * D)), 2.0 * D
+
+
+def paper_heat_preconditioner(problem, d_u, tau):
+    """The paper's single-term preconditioner of an IMEX step (Sec. 6, Eq.
+    semilinear_heat_equation_fully_discrete_P), P^{-1}(U) = (M3 + d_u tau B1)^{-1} U
+    (M + d_u tau (A + B2))^{-1}, in this orientation (the factors of the elliptic
+    product preconditioner, Eq. vector_preconditioner, plus the masses):
+    (M_s[h] + d_u tau K_s[h])^{-1} U (M_t + d_u tau (K_t + K_t[t^2]))^{-T}."""
+    f = problem.factors()
+    i = problem.idx
+    E = trim(f['Ms_h'], i) + d_u * tau * trim(f['Ks_h'], i)
+    F = trim(f['Mt'], i) + d_u * tau * (trim(f['Kt_1'], i) + trim(f['Kt_t2'], i))
+    return ProductPreconditioner(E.tocsr(), F.tocsr())
+
+
+def imex_mo_pcg_step(problem, d_u, tau, U, F_all, precond, max_iter=100):
+    """One IMEX Euler step (Sec. 6, Eqs. semilinear_heat_equation_fully_discrete_sylvester_pk
+    and _R_pk) by MO-PCG from the guess U_n, stopped by the paper's rule
+    ||R_s|| <= tau ||R_0|| (Sec. 6).  F_all: nodal f on all n x n nodes (the load is the
+    mass of the interior test functions against it).  `problem` has gamma = 0.
+    Returns (U_{n+1}, iterations)."""
+    f = problem.factors()
+    i = problem.idx
+    Ms, Mt = trim(f['Ms_h'], i), trim(f['Mt'], i)
+    terms = [(S, T) for S, T in problem.terms() if abs(S).sum() > 0]
+
+    def L(X):
+        return Ms @ X @ Mt.T + d_u * tau * apply_terms(terms, X)
+
+    B = Ms @ U @ Mt.T + tau * rhs(problem, F_all)
+    R0 = B - L(U)
+    nb = np.sqrt(fro(B, B))
+    if nb == 0.0:
+        return U, 0
+    U1, info = mo_pcg(L, precond, B, U0=U, rtol=tau * np.sqrt(fro(R0, R0)) / nb, max_iter=max_iter)
+    return U1, info['iterations']

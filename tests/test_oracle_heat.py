@@ -16,6 +16,9 @@
   and its schedule more than the space discretisation (which the 2D assembly and the
   elliptic manufactured rates pin): a load without the boundary nodes' f still
   passes it.
+* Iterations: with the paper's heat preconditioner and stopping rule (Sec. 6, Test 2)
+  MO-PCG takes one iteration per step for P_k (at most two for lumped P1); the plain
+  mass preconditioner that the paper improves on takes more.
 """
 import json
 import os
@@ -24,7 +27,11 @@ import numpy as np
 import pytest
 
 from oracle import closed_form
-from oracle.heat import HeatOperators, imex_forward, imex_adjoint, loss
+from oracle.heat import (HeatOperators, imex_forward, imex_adjoint, loss, paper_heat_preconditioner,
+                         imex_mo_pcg_step)
+from oracle.fem1d import trim
+from oracle.pcg import ProductPreconditioner
+from oracle.operator import Problem
 from oracle.operator import rhs
 from paper_2109_01173_gb300.inputs import Profile, ZERO
 
@@ -141,3 +148,44 @@ def test_cap_heat_rates_match_the_paper(k, name, N):
     r = np.log2(e1 / e2)
     want = GOLD["heat_cap_domain_rates_mo_pcg"]["value"][name]
     assert abs(r - want) <= 0.15, (k, r, want)
+
+
+def _cap_heat_iterations(k, N, precond_kind, steps=10):
+    """MO-PCG iterations of each of the first IMEX steps of the cap-domain heat test."""
+    P2 = np.polynomial.polynomial
+    c = _pmul(_pmul(np.array([[0.0], [-1.0], [1.0]]), np.array([[1.0, 1.0], [0.0, 0.0], [-0.5, 0.0]])),
+              np.array([[-1.0, 1.0], [0.0, 0.0], [0.5, 0.0]]))
+    lap = np.pad(P2.polyder(c, 2, axis=0), ((0, 2), (0, 0))) + np.pad(P2.polyder(c, 2, axis=1), ((0, 0), (0, 2)))
+    g1, g2 = Profile(c0=-1.0, c2=0.5), Profile(c0=1.0, c2=-0.5)
+    d_u, tau = 0.1, 0.01
+    n = max(k, 1) * N + 1
+    P = Problem(g1, g2, k, n, 0.0)
+    if precond_kind == "paper":
+        pre = paper_heat_preconditioner(P, d_u, tau)
+    else:   # the plain mass preconditioner M3 U M
+        f = P.factors()
+        pre = ProductPreconditioner(trim(f['Ms_h'], P.idx).tocsr(), trim(f['Mt'], P.idx).tocsr())
+    s = np.arange(n) / (n - 1)
+    X = np.repeat(s[:, None], n, 1)
+    Y = g1.g(s)[:, None] + s[None, :] * (g2.g(s) - g1.g(s))[:, None]
+    u0 = P2.polyval2d(X, Y, c)
+    l0 = P2.polyval2d(X, Y, lap)
+    U = u0[1:-1, 1:-1].copy()
+    its = []
+    for st in range(steps):
+        U, it = imex_mo_pcg_step(P, d_u, tau, U, np.exp(st * tau) * (u0 - d_u * l0), pre)
+        its.append(it)
+    return its
+
+
+@pytest.mark.parametrize("k,N", [(1, 48), (2, 24), (3, 12), (4, 12)])
+def test_paper_heat_preconditioner_one_iteration_per_step(k, N):
+    its = _cap_heat_iterations(k, N, "paper")
+    assert all(i == GOLD["heat_mo_pcg_iterations_per_step"]["value"]["p_k"] for i in its), its
+
+
+def test_paper_heat_preconditioner_lumped_and_mass_only():
+    its = _cap_heat_iterations(0, 48, "paper")
+    assert max(its) <= GOLD["heat_mo_pcg_iterations_per_step"]["value"]["lumped_p1_at_most"], its
+    # the uncorrected mass preconditioner the paper starts from needs more iterations
+    assert max(_cap_heat_iterations(1, 48, "mass")) >= 3
