@@ -5,8 +5,8 @@ Workload (per rank): B independent elliptic problems -Lap u + u = f on the
 x-normal domain {0 <= x <= 1, 0 <= y <= 1 + 0.25 sin(2 pi x)}, zero Dirichlet
 data, P2 elements with 2049 nodes per direction, f a seeded sum of 32 Fourier
 modes (seed = rank * B + i).  One step = one batched solve (right-hand side,
-inner mixed-precision MO-PCG, iterative refinement with an FP64 residual after
-the first step and double-float residual updates after later ones) of the B
+inner mixed-precision MO-PCG, iterative refinement with double-float residual
+updates: difference form after the step from zero, plain form after later ones) of the B
 instances from U = 0 to ||B - L(U)||_F <= 1e-10 ||B||_F.  Setup (1D tables
 and the FP64 eigendecompositions) is done once before timing and reported
 separately.  Instances are independent: N ranks solve N * B problems with no
