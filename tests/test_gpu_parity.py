@@ -370,8 +370,8 @@ def _true_rel(h, F, U):
 
 
 def _solve_both(mf, g1, g2, k, n, gam, bc, F, prec, rtol=1e-10):
-    """The same solve with the residual updated after the first step (default) and
-    recomputed in FP64 after every step (FLAG_TRUE_RESIDUAL)."""
+    """The same solve with the residual updated in double-float arithmetic after every
+    step (default) and recomputed in FP64 after every step (FLAG_TRUE_RESIDUAL)."""
     torch = torch_()
     B = len(g1)
     out = []
