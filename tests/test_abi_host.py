@@ -60,6 +60,12 @@ def test_invalid_arguments_rejected_without_gpu(mofem):
     # non-positive height h = g2 - g1 is reported by the host tables without touching the GPU
     with pytest.raises(mofem.MofemError):
         mofem.host_tables(SIN_TOP, ZERO, 2, 9, 1.0)
+    # the double-float difference-form tables: same argument checks
+    assert L.mofem_host_dd_tables(ctypes.byref(p), ctypes.byref(p2), 5, 65, 1.0, 0, None, None, None) == 1
+    assert L.mofem_host_dd_tables(ctypes.byref(p), ctypes.byref(p2), 3, 65, 1.0, 0, None, None, None) == 1
+    assert L.mofem_host_dd_tables(None, ctypes.byref(p2), 2, 65, 1.0, 0, None, None, None) == 1
+    with pytest.raises(mofem.MofemError):
+        mofem.host_dd_tables(SIN_TOP, ZERO, 2, 9, 1.0)
     assert L.mofem_apply(None, None, None, 0, 0, None) == 1
     assert L.mofem_precond(None, None, None, 0, 0, None) == 1
     assert L.mofem_pcg_direction(None, None, None, None, None, None, None, 0, None, 0, None) == 1
