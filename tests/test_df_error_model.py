@@ -19,21 +19,9 @@ import numpy as np
 import pytest
 
 from paper_2109_01173_gb300.inputs import ZERO, SIN_TOP
+from ddref import apply_dd, shift as _shift
 
 f32 = np.float32
-
-
-def _shift(X, off, axis):
-    Y = np.zeros_like(X)
-    n = X.shape[axis]
-    src = [slice(None)] * 2
-    dst = [slice(None)] * 2
-    if off >= 0:
-        src[axis], dst[axis] = slice(off, n), slice(0, n - off)
-    else:
-        src[axis], dst[axis] = slice(0, n + off), slice(-off, n)
-    Y[tuple(dst)] = X[tuple(src)]
-    return Y
 
 
 # ---- FP32 error-free transforms (numpy float32 rounds each operation once) ----------
@@ -164,41 +152,6 @@ def _diff_fp64(S, T, K, x):
     return y
 
 
-def _two_prod64(a, b):
-    def split(v):
-        c = 134217729.0 * v
-        hi = c - (c - v)
-        return hi, v - hi
-    p = a * b
-    ah, al = split(a)
-    bh, bl = split(b)
-    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
-
-
-def _reference(S, T, K, x):
-    """Double-double evaluation (products exact, sums with their errors carried)."""
-    P = 2 * K + 1
-    yh = np.zeros_like(x)
-    yl = np.zeros_like(x)
-    for i in range(S.shape[0]):
-        vh = np.zeros_like(x)
-        vl = np.zeros_like(x)
-        for l in range(P):
-            p, e = _two_prod64(T[i][l][None, :], _shift(x, l - K, 1))
-            s = vh + p
-            v = s - vh
-            vl = vl + ((vh - (s - v)) + (p - v)) + e
-            vh = s
-        for j in range(P):
-            c = S[i][j][:, None]
-            p, e = _two_prod64(c, _shift(vh, j - K, 0))
-            s = yh + p
-            v = s - yh
-            yl = yl + ((yh - (s - v)) + (p - v)) + e + c * _shift(vl, j - K, 0)
-            yh = s
-    return yh, yl
-
-
 def _errors(mf, n):
     tb = mf.host_tables(ZERO, SIN_TOP, 2, n, 1.0)
     dd = mf.host_dd_tables(ZERO, SIN_TOP, 2, n, 1.0)
@@ -212,7 +165,7 @@ def _errors(mf, n):
     xh = d.astype(f32)
     xl = (d - xh.astype(np.float64)).astype(f32)
     x64 = xh.astype(np.float64) + xl.astype(np.float64)     # the step exactly
-    rh, rl = _reference(S, T, K, x64)
+    rh, rl = apply_dd(S, T, K, x64)
     nrm = np.linalg.norm(rh)
     err = lambda y: np.linalg.norm((y - rh) - rl) / nrm
     x = _DF(xh, xl)

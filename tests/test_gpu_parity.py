@@ -23,6 +23,7 @@ import pytest
 from oracle.operator import Problem, apply_terms, rhs, apply_entry
 from oracle import pcg
 from paper_2109_01173_gb300.inputs import Profile, ZERO, SIN_TOP, fourier_f, metric_instance
+from ddref import residual_dd
 
 pytestmark = pytest.mark.gpu
 
@@ -419,62 +420,6 @@ def test_residual_update_tracks_recomputed(mf, k, n, dname, bc, gamma):
     assert abs(rel1[0] - rep1) <= 1e-13, (rep1, rel1)
 
 
-def _two_prod(a, b):
-    """a * b = p + e exactly (Dekker's product with Veltkamp's split; no FMA needed)."""
-    def split(x):
-        c = 134217729.0 * x
-        hi = c - (c - x)
-        return hi, x - hi
-    p = a * b
-    ah, al = split(a)
-    bh, bl = split(b)
-    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
-
-
-def _two_sum(a, b):
-    s = a + b
-    v = s - a
-    return s, (a - (s - v)) + (b - v)
-
-
-def _shift(X, off, axis):
-    """Y[.., i] = X[.., i + off] along axis, zero outside."""
-    Y = np.zeros_like(X)
-    n = X.shape[axis]
-    src = [slice(None)] * 2
-    dst = [slice(None)] * 2
-    if off >= 0:
-        src[axis], dst[axis] = slice(off, n), slice(0, n - off)
-    else:
-        src[axis], dst[axis] = slice(0, n + off), slice(-off, n)
-    Y[tuple(dst)] = X[tuple(src)]
-    return Y
-
-
-def _residual_dd(S, T, K, B, U):
-    """B - sum_i S_i U T_i^T for band tables S, T [term][slot][row] (slot j of row r:
-    column r + j - K), in double-double arithmetic (products exact, sums with their
-    errors carried): accurate to far below the FP64 rounding of U's apply."""
-    P = 2 * K + 1
-    yh = np.zeros_like(U)
-    yl = np.zeros_like(U)
-    for i in range(S.shape[0]):
-        vh = np.zeros_like(U)
-        vl = np.zeros_like(U)
-        for l in range(P):
-            p, e = _two_prod(T[i][l][None, :], _shift(U, l - K, 1))
-            vh, t = _two_sum(vh, p)
-            vl = vl + (t + e)
-        vh, vl = _two_sum(vh, vl)
-        for j in range(P):
-            c = S[i][j][:, None]
-            p, e = _two_prod(c, _shift(vh, j - K, 0))
-            yh, t = _two_sum(yh, p)
-            yl = yl + (t + e + c * _shift(vl, j - K, 0))
-    r, t = _two_sum(B, -yh)
-    return r + (t - yl)
-
-
 @pytest.mark.parametrize("k,n", [(2, 2049), (1, 1025)])
 def test_first_step_residual_double_float(mf, k, n):
     """One refinement step from zero: the residual B - L(U) that the solver carries
@@ -495,7 +440,7 @@ def test_first_step_residual_double_float(mf, k, n):
     h.rhs(F, Bt)
     B = Bt.cpu().numpy()
     tb = mf.host_tables(inst["g1"], inst["g2"], k, n, 1.0)
-    R = _residual_dd(tb["S"], tb["T"], tb["K"], B, U.cpu().numpy())
+    R = residual_dd(tb["S"], tb["T"], tb["K"], B, U.cpu().numpy())
     bn = np.linalg.norm(B)
     ref = np.linalg.norm(R) / bn
     assert abs(info.rel_residual - ref) <= 5e-12, (info.rel_residual, ref)
