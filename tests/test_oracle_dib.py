@@ -3,7 +3,11 @@
 * Kinetics: with C = 4 the pair (0, 1/2) zeroes f and g (D printed to 4 decimals,
   so g(0, 1/2) = 4 * 0.45 - 3.2727 * 0.55 = 1.5e-5); the hand-written Jacobian
   equals central differences of f and g.
-* Equilibrium: Newton's answer zeroes the kinetics (cap and jar parameters).
+* Kinetics at the points where the printed formulas collapse (theta = 0 and 1,
+  eta = 0, the odd part in eta): every factor (k2, k3, the gamma brackets, A1, A2,
+  B, alpha) sits where Sec. 7 prints it.
+* Equilibrium: Newton's answer zeroes the kinetics (cap and jar parameters) and,
+  for the cap parameters, equals the value obtained without the oracle.
 * Lumped P1 with Neumann BC: the cosine vectors cos(i pi j / N) satisfy
   A v = lam M v with lam = 2 N^2 (1 - cos(i pi / N)) (closed form).
 * Coupled IMEX Euler: the homogeneous equilibrium is a fixed point (constants are
@@ -11,6 +15,9 @@
   the equilibrium on the unit square evolves by the 2 x 2 amplification matrix
   G = diag(1 + tau lam, 1 + d_theta tau lam)^-1 (I + tau rho J) per step.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -81,3 +88,39 @@ def test_small_cosine_mode_follows_the_amplification_matrix():
     a = np.linalg.matrix_power(G, steps) @ a0
     assert np.abs((eta - e) - a[0] * mode).max() <= 1e-5 * np.abs(a).max()
     assert np.abs((theta - t) - a[1] * mode).max() <= 1e-5 * np.abs(a).max()
+
+
+GOLD_IND = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "independent_values.json")))
+
+
+@pytest.mark.parametrize("params", [dib.CAP, dib.JAR])
+def test_kinetics_special_cases_place_every_factor(params):
+    """Sec. 7, Eqs. dib_kinetics_f and dib_kinetics_g at the points where they collapse:
+    theta = 1 leaves only the D-term of g, -D (1 + gamma)(1 + k3 eta) (places k3 and the
+    gamma theta factor); theta = 0 leaves only the C-term, C (1 - gamma)(1 + k2 eta)
+    (places k2 and the bracket); g is affine in eta; f(0, theta) = -B (theta - alpha),
+    f - f(0, .) is odd in eta with cubic coefficient -A2 and linear coefficient
+    A1 (1 - theta)."""
+    p = params
+    for eta in (-0.7, -0.2, 0.0, 0.3, 1.1):
+        assert dib.g(eta, 1.0, p) == pytest.approx(-p['D'] * (1 + p['gamma']) * (1 + p['k3'] * eta), rel=1e-14, abs=1e-14)
+        assert dib.g(eta, 0.0, p) == pytest.approx(p['C'] * (1 - p['gamma']) * (1 + p['k2'] * eta), rel=1e-14, abs=1e-14)
+    for theta in (0.1, 0.5, 0.8):
+        g = [dib.g(e, theta, p) for e in (-1.0, 0.0, 1.0)]
+        assert abs(g[0] - 2 * g[1] + g[2]) <= 1e-12 * max(1.0, abs(g[1]))
+        assert dib.f(0.0, theta, p) == pytest.approx(-p['B'] * (theta - p['alpha']), rel=1e-14, abs=1e-14)
+        odd = [(dib.f(e, theta, p) - dib.f(-e, theta, p)) / 2 for e in (0.5, 1.0)]
+        # odd part c1 e + c3 e^3 from two samples
+        c3 = (odd[1] - 2 * odd[0]) / (1.0 - 2 * 0.125)
+        c1 = odd[1] - c3
+        assert c3 == pytest.approx(-p['A2'], rel=1e-12)
+        assert c1 == pytest.approx(p['A1'] * (1 - theta), rel=1e-12)
+
+
+def test_cap_equilibrium_matches_the_independent_value():
+    """Newton's zero of the oracle kinetics with the printed cap parameters equals the
+    value obtained without the oracle (elimination of eta from g = 0, bisection in theta;
+    tests/golden/independent_values.json), to its 4 digits."""
+    e, t = dib.equilibrium(dib.CAP)
+    want = GOLD_IND["dib_cap_equilibrium"]
+    assert abs(e - want["eta"]) <= 0.6e-4 and abs(t - want["theta"]) <= 0.6e-4, (e, t)

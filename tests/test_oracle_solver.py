@@ -183,3 +183,23 @@ def test_paper_aua_two_iterations(k):
     hist = [np.zeros_like(U)] + info['history']
     stop = next(i for i in range(1, len(hist)) if np.linalg.norm(hist[i] - hist[i - 1]) <= 0.05 * errv)
     assert stop == GOLD['square_aua_pcg_iterations']['value']
+
+
+@pytest.mark.parametrize("k,n", [(0, 11), (1, 11), (2, 11), (4, 13)])
+@pytest.mark.parametrize("bc", ["dirichlet", "neumann"])
+def test_averaged_pencil_is_the_t_mean_of_the_operator_terms(k, n, bc):
+    """The 'averaged' second pencil E2 = M_s[e2] is the mean over t in [0, 1] of the
+    operator's K_t-paired s-factors.  H^_tt = (1 + (g1' + t h')^2)/h splits as
+    (1 + g1'^2)/h + t (2 g1' h'/h) + t^2 (h'^2/h), which the operator pairs with K_t[1],
+    K_t[t] and K_t[t^2] (terms 1, 2, 3); replacing t and t^2 by their means 1/2 and 1/3
+    gives M_s[e2] = S_1 + S_2 / 2 + S_3 / 3 exactly, with the S_i of terms() (pinned
+    against the physical-mesh 2D assembly).  Two curved profiles, so every piece is
+    nonzero."""
+    P = Problem(*TWO, k, n, gamma=1.0, bc=bc)
+    t = P.terms()
+    assert min(abs(t[i][0]).sum() for i in (1, 2, 3)) > 0
+    E2 = P.pencils('averaged')[1]
+    want = (t[1][0] + 0.5 * t[2][0] + t[3][0] / 3.0).toarray()
+    assert np.abs(E2 - want).max() <= 1e-13 * np.abs(want).max()
+    # and it is not the 'dominant' (t-free) pencil on this domain
+    assert np.abs(P.pencils('dominant')[1] - want).max() > 1e-6 * np.abs(want).max()
