@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--k", type=int, default=2)
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--fp64-samples", type=int, default=3, help="timed FP64-form solves (after one warm-up)")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle's reference solution of instance 0 (rel_err_vs_oracle)")
+    ap.add_argument("--no-precision-matrix", action="store_true",
+                    help="skip the BF16/TF32 rows and the P2 n=1025 / P4 n=2049 lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-heat", action="store_true", help="skip the differentiation workload (heat IMEX + adjoint)")
     ap.add_argument("--no-dib", action="store_true", help="skip the reaction-diffusion (DIB) workload")
@@ -284,6 +289,37 @@ def oracle_sample(inst, iters):
     return t_setup, t_it
 
 
+def oracle_solution_job(n, k, out_q):
+    """Child process: the oracle's reference solution of instance 0 (rtol 1e-12)."""
+    from oracle.operator import Problem
+    from oracle import pcg
+    inst = make_inputs(1, n, k, 0)[0]
+    t0 = time.perf_counter()
+    P = Problem(inst["g1"], inst["g2"], inst["k"], inst["n"], inst["gamma"])
+    Uo, info = pcg.solve(P, inst["F"], rtol=1e-12, max_iter=400)
+    out_q.put((Uo, {"rel_residual": info["rel_residual"], "iterations": info["iterations"],
+                    "seconds": time.perf_counter() - t0}))
+
+
+def timed_solves(h, F, U, prec, rtol, B, stream, samples=3):
+    """One warm-up solve, then the median of `samples` CUDA-event-timed batched solves."""
+    import torch
+    h.pcg_solve(F, U.zero_(), rtol=rtol, max_iter=500, precision=prec)
+    ts, info = [], None
+    for _ in range(samples):
+        U.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        info, code = h.pcg_solve(F, U, rtol=rtol, max_iter=500, precision=prec, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(ts)
+    return {"solves_per_s": B / t, "ms_per_step": t * 1e3, "iterations": info.iterations,
+            "outer_steps": info.outer_steps, "rel_residual_max": info.rel_residual, "status": code}
+
+
 def cpu_cores():
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
         if os.environ.get(v):
@@ -461,18 +497,62 @@ def run_mofem(a):
     # even iteration: read R, L(Q); write R, FP16 R (14 B); odd: + read/write dU hi/lo, read Q_prev, Q (38 B)
     upd_bytes = 26.0 * B * q * q
 
-    # ---- FP64 form (same instances, same stopping rule) ------------------------------
+    # ---- the oracle's reference solution of instance 0 (spawned process, overlaps the GPU work) --
+    oracle_job = None
+    if rank == 0 and world == 1 and not a.no_oracle_check:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        oracle_q = ctx.Queue()
+        oracle_job = ctx.Process(target=oracle_solution_job, args=(a.n, a.k, oracle_q), daemon=True)
+        oracle_job.start()
+
+    # ---- FP64 form (same instances, same stopping rule): one untimed warm-up solve, then
+    # CUDA-event samples; the achieved FP64 rate of its cuBLAS DGEMM preconditioner
     fp64 = None
     if not a.no_fp64_form and a.precision != "fp64":
         U64 = torch.zeros_like(U)
-        torch.cuda.synchronize()
-        f0 = time.perf_counter()
-        info64 = step(U64, F, prec="fp64", max_iter=500)
-        f_el = time.perf_counter() - f0
+        info64 = step(U64, F, prec="fp64", max_iter=500)   # warm-up (cuBLAS, workspaces)
+        samples64 = []
+        for _ in range(a.fp64_samples):
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            f0.record(stream)
+            info64 = step(U64, F, prec="fp64", max_iter=500)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            samples64.append(f0.elapsed_time(f1) / 1e3)
+        f_el = statistics.median(samples64)
         diff = float(((U64 - U).norm() / U64.norm()).item())
-        fp64 = {"solves_per_s": B / f_el, "ms_per_step": f_el * 1e3, "iterations": info64.iterations,
-                "ms_per_iter": f_el * 1e3 / max(info64.iterations, 1), "rel_residual": info64.rel_residual,
-                "mixed_speedup": value / world / (B / f_el), "rel_diff_mixed_vs_fp64": diff}
+        t_pre64 = time_kernel(11, "fp64")
+        fp64 = {"solves_per_s": B / f_el, "ms_per_step": f_el * 1e3, "ms_samples": [x * 1e3 for x in samples64],
+                "iterations": info64.iterations, "ms_per_iter": f_el * 1e3 / max(info64.iterations, 1),
+                "rel_residual": info64.rel_residual, "mixed_speedup": value / world / (B / f_el),
+                "rel_diff_mixed_vs_fp64": diff,
+                "dgemm_precond_ms": t_pre64 * 1e3,
+                "dgemm_fp64_tflops": 4 * flops_gemm / t_pre64 / 1e12,
+                "timing": f"1 warm-up solve, median of {a.fp64_samples} CUDA-event samples; the preconditioner "
+                          f"(4 cuBLAS DGEMMs per instance + division) timed alone on the same stream"}
+
+    # ---- the same workload with the other operand precisions (solves/s, inner iterations) --
+    precisions = {}
+    if not a.no_precision_matrix and a.precision != "fp64":
+        for pr in ("fp16", "bf16", "tf32"):
+            if pr == a.precision:
+                precisions[pr] = {"solves_per_s": value / world, "iterations": statistics.mean(iters),
+                                  "rel_residual_max": max(rels)}
+                continue
+            precisions[pr] = timed_solves(h, F, U, pr, a.rtol, B, stream)
+    # P2 at 1025 and P4 at 2049 nodes (the precision form's other two sizes)
+    other_sizes = {}
+    if not a.no_precision_matrix and a.n == 2049 and a.k == 2 and rank == 0:
+        for n2, k2 in ((1025, 2), (2049, 4)):
+            ins2 = make_inputs(B, n2, k2, rank)
+            h2 = mf.Handle([i["g1"] for i in ins2], [i["g2"] for i in ins2], k2, n2, [i["gamma"] for i in ins2])
+            F2 = torch.tensor(np.stack([i["F"] for i in ins2]), dtype=torch.float64, device="cuda")
+            U2 = torch.zeros((B, h2.q, h2.q), dtype=torch.float64, device="cuda")
+            other_sizes[f"P{k2}_n{n2}"] = timed_solves(h2, F2, U2, a.precision, a.rtol, B, stream)
+            h2.close()
+            del F2, U2
 
     # ---- CPU baseline: the oracle on a bounded sample ----------------------------------
     cpu = None
@@ -485,6 +565,18 @@ def run_mofem(a):
                          f"1/(s_per_iter x {fp64_iters} iterations of the FP64 GPU form)"}
 
     h.close()
+    rel_err_oracle = None
+    if oracle_job is not None:
+        Uo, info_o = oracle_q.get()
+        oracle_job.join()
+        U0 = U[0].cpu().numpy()
+        rel_err_oracle = {"instance": 0, "rel_err_mixed": float(np.linalg.norm(U0 - Uo) / np.linalg.norm(Uo)),
+                          "oracle_rel_residual": info_o["rel_residual"], "oracle_iterations": info_o["iterations"],
+                          "oracle_s": info_o["seconds"],
+                          "note": "FP64 oracle MO-PCG (numpy/scipy, reduced preconditioner) to relative residual "
+                                  "1e-12 on the host cores, outside the timed region"}
+        if fp64 is not None:
+            rel_err_oracle["rel_err_fp64_form"] = float(np.linalg.norm(U64[0].cpu().numpy() - Uo) / np.linalg.norm(Uo))
     if rank != 0:
         return 0
     working_set_mb = B * (q * q * (6 * 4 + 8 * 2 + 3 * 8)) / 1e6
@@ -531,6 +623,9 @@ def run_mofem(a):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * n * n * 8,
                 "d2h_bytes_per_step": B * q * q * 8, "max_abs_diff_vs_device_run": err_e2e},
         "fp64_form": fp64,
+        "rel_err_vs_oracle": rel_err_oracle,
+        "precision_matrix": precisions or None,
+        "other_sizes": other_sizes or None,
         "cpu_baseline": cpu,
     }
     if not a.no_heat and rank == 0:

@@ -64,15 +64,29 @@ typedef enum { MOFEM_BC_DIRICHLET = 0, MOFEM_BC_NEUMANN = 1 } mofem_bc;
  * refinement around the inner FP32 solve. */
 typedef enum { MOFEM_FP64 = 0, MOFEM_MIXED_TF32 = 1, MOFEM_MIXED_BF16 = 2, MOFEM_MIXED_FP16 = 3 } mofem_precision;
 
-/* Second pencil of the two-term Sylvester preconditioner (see mofem_precond). */
 /* Preconditioner of MO-PCG.  AVERAGED / DOMINANT: the two-term Sylvester
  * preconditioner E1 Z F1^T + E2 Z F2^T = R (E1 = K_s[h] + gamma M_s[h], F1 = M_t,
  * F2 = K_t, E2 = M_s[e2] with e2 the t-average of H^_tt or its t-free part).
- * PRODUCT: the paper's single-term preconditioner of Sec. 5, Eq.
- * vector_preconditioner, P(Z) = K_s[h] Z (K_t + K_t[t^2])^T (B1 U (A + B2) in the
- * paper's orientation), Dirichlet only; applied by the same reduced approach with
- * standard eigenpairs on each side and the divisor lambda_a mu_b. */
-typedef enum { MOFEM_PENCIL_AVERAGED = 0, MOFEM_PENCIL_DOMINANT = 1, MOFEM_PENCIL_PRODUCT = 2 } mofem_pencil;
+ * The others are the paper's single-term preconditioners P(Z) = E Z F^T, applied by
+ * the same reduced approach with standard eigenpairs of E and F and the divisor
+ * lambda_a mu_b:
+ *  PRODUCT   (Sec. 5, Eq. vector_preconditioner): E = K_s[h], F = K_t + K_t[t^2]
+ *            (B1 U (A + B2) in the paper's orientation); Dirichlet only.
+ *  PARABOLIC (Sec. 6, Eqs. semilinear_heat_equation_fully_discrete_P and its lumped
+ *            form _P_lumped, k = 0): the IMEX-step preconditioner
+ *            (M3 + d_u tau B1)^-1 U (M + d_u tau (A + B2))^-1, i.e. for a handle set up
+ *            with gamma = 1/(d_u tau) (the step scaled by 1/(d_u tau)):
+ *            E = K_s[h] + gamma M_s[h], F = M_t + (K_t + K_t[t^2]) / gamma.  Needs
+ *            gamma > 0, the same in every instance (F and Q2 are shared); both BCs.
+ *  AUA       (Sec. 5.1, Eq. precSquare): E = K_s[h], F = K_t, which on the unit
+ *            square is A U A with A the 1D stiffness matrix; Dirichlet only. */
+typedef enum {
+    MOFEM_PENCIL_AVERAGED = 0,
+    MOFEM_PENCIL_DOMINANT = 1,
+    MOFEM_PENCIL_PRODUCT = 2,
+    MOFEM_PENCIL_PARABOLIC = 3,
+    MOFEM_PENCIL_AUA = 4
+} mofem_pencil;
 
 /* Domain profile y = g(x) on [0, 1]: host callbacks for g and g', called during
  * setup only (at the quadrature points). */
@@ -324,7 +338,9 @@ mofem_status mofem_group_destroy(mofem_group g);
  *   9 = the preconditioner's four GEMMs as the solver runs them, one chained
  *       launch (prec MIXED_TF32, MIXED_BF16 or MIXED_FP16),
  *  10 = the residual update of 8 in difference form (the step from zero;
- *       MOFEM_ERR_UNSUPPORTED for forms it does not serve).
+ *       MOFEM_ERR_UNSUPPORTED for forms it does not serve),
+ *  11 = the FP64 form's preconditioner (four cuBLAS DGEMMs per instance and the
+ *       Hadamard division; prec ignored).
  * The buffers' contents are whatever the last solve left (timing only). */
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps,
                                 cudaStream_t stream);
@@ -341,11 +357,25 @@ mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec
  * (4 MiB), held by every GPU that loads the library until the process exits.
  * Limit: batch * q * round_up(q, 64) <= 262144 (e.g. one instance with
  * q <= 512); larger handles get MOFEM_ERR_INVALID_ARG (see mofem_last_error).
- * The first call on a device looks up the array's device address (a CUDA
- * runtime query, no allocation); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
- * calls that overlap on the GPU race and must be serialised by the caller. */
+ * The first call on a device looks up the array's device address; with lazy
+ * module loading (the CUDA default) that first call may also load this part of
+ * the library, which allocates the 4 MiB array and may synchronise the device.
+ * Make one warm-up call on each device before the latency-critical loop and
+ * before any stream capture; later calls allocate nothing.  All calls share the
+ * array and it keeps the last call's contents: calls that overlap on the GPU race
+ * and must be serialised by the caller. */
 mofem_status mofem_precond_noalloc(mofem_handle h, const float* R, float* Z, int ld, cudaStream_t stream);
+
+/* Copy of the preconditioner's eigen data computed at setup (Sec. 4, Eq.
+ * diagonalisation_1; the pencils of mofem_setup, or the single-term factors of
+ * mofem_pencil): Q1 [batch][q][q] (row-major, column i = eigenvector i of instance
+ * b's s-pencil), Q2 [q][q] (shared t-pencil), lambda [batch][q] and mu [q], all FP64
+ * DEVICE arrays owned by the caller with leading dimension q; any pointer may be
+ * NULL.  The preconditioner is Z = Q1 ((Q1^T R Q2) ./ D) Q2^T with D_ab = lambda_a +
+ * mu_b, or lambda_a mu_b for the single-term pencils (*divisor_product = 1; may be
+ * NULL).  Stream-ordered on `stream`; no synchronisation. */
+mofem_status mofem_get_eigen(mofem_handle h, double* Q1, double* Q2, double* lambda, double* mu,
+                             int* divisor_product, cudaStream_t stream);
 
 /* Release every buffer the handle owns. */
 mofem_status mofem_destroy(mofem_handle h);

@@ -54,12 +54,22 @@ mofem_status mofem_setup_batched(int batch, const mofem_profile* g1, const mofem
         if (bc == MOFEM_BC_NEUMANN && !(gamma[i] > 0.0)) return MOFEM_ERR_INVALID_ARG;   // singular operator
     }
     if (opts && (opts->quad_points < 0 || opts->quad_points > 16)) return MOFEM_ERR_INVALID_ARG;
-    if (opts && (opts->pencil < MOFEM_PENCIL_AVERAGED || opts->pencil > MOFEM_PENCIL_PRODUCT))
+    if (opts && (opts->pencil < MOFEM_PENCIL_AVERAGED || opts->pencil > MOFEM_PENCIL_AUA))
         return MOFEM_ERR_INVALID_ARG;
-    if (opts && opts->pencil == MOFEM_PENCIL_PRODUCT && bc != MOFEM_BC_DIRICHLET) {
-        mofem_set_last_error("product preconditioner: K_s[h] and K_t + K_t[t^2] are singular under Neumann BC",
-                             __FILE__, __LINE__);
+    if (opts && (opts->pencil == MOFEM_PENCIL_PRODUCT || opts->pencil == MOFEM_PENCIL_AUA) &&
+        bc != MOFEM_BC_DIRICHLET) {
+        mofem_set_last_error("single-term stiffness preconditioner: K_s[h] and K_t (+ K_t[t^2]) are singular under "
+                             "Neumann BC", __FILE__, __LINE__);
         return MOFEM_ERR_INVALID_ARG;
+    }
+    if (opts && opts->pencil == MOFEM_PENCIL_PARABOLIC) {
+        // the t-factor M_t + (K_t + K_t[t^2]) / gamma and its eigenvectors are shared by the batch
+        for (int i = 0; i < batch; ++i)
+            if (!(gamma[i] > 0.0) || gamma[i] != gamma[0]) {
+                mofem_set_last_error("parabolic preconditioner: gamma = 1/(d_u tau) must be positive and equal in "
+                                     "every instance", __FILE__, __LINE__);
+                return MOFEM_ERR_INVALID_ARG;
+            }
     }
     mofem_ctx* c = new (std::nothrow) mofem_ctx();
     if (!c) return MOFEM_ERR_OOM;
@@ -209,9 +219,23 @@ mofem_status mofem_dib_run(mofem_handle h, const mofem_dib_params* p, double rho
 }
 
 mofem_status mofem_bench_kernel(mofem_handle h, int kernel, mofem_precision prec, int reps, cudaStream_t stream) {
-    if (!h || kernel < 0 || kernel > 10 || reps < 0 || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
+    if (!h || kernel < 0 || kernel > 11 || reps < 0 || !valid_precision(prec)) return MOFEM_ERR_INVALID_ARG;
     if (kernel >= 1 && kernel <= 4 && prec == MOFEM_FP64) return MOFEM_ERR_INVALID_ARG;
     return bench_kernel(h, kernel, prec, reps, stream);
+}
+
+mofem_status mofem_get_eigen(mofem_handle h, double* Q1, double* Q2, double* lambda, double* mu,
+                             int* divisor_product, cudaStream_t stream) {
+    if (!h) return MOFEM_ERR_INVALID_ARG;
+    const int q = h->q, ld = h->ld, B = h->batch;
+    const size_t w = sizeof(double) * q, lw = sizeof(double) * ld;
+    if (Q1)
+        MOFEM_CUDA_TRY(cudaMemcpy2DAsync(Q1, w, h->Q1_64, lw, w, (size_t)q * B, cudaMemcpyDeviceToDevice, stream));
+    if (Q2) MOFEM_CUDA_TRY(cudaMemcpy2DAsync(Q2, w, h->Q2_64, lw, w, q, cudaMemcpyDeviceToDevice, stream));
+    if (lambda) MOFEM_CUDA_TRY(cudaMemcpy2DAsync(lambda, w, h->lam64, lw, w, B, cudaMemcpyDeviceToDevice, stream));
+    if (mu) MOFEM_CUDA_TRY(cudaMemcpyAsync(mu, h->mu64, w, cudaMemcpyDeviceToDevice, stream));
+    if (divisor_product) *divisor_product = h->div_product;
+    return MOFEM_OK;
 }
 
 mofem_status mofem_destroy(mofem_handle h) {

@@ -32,6 +32,8 @@ constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // dst[r][c] = bf16(src[c][r]) (transpose = 1) or bf16(src[r][c]); n x n, leading dimensions given.
+// Rounded through FP32, as the handle's own BF16 operand copies are, so both entry points
+// multiply by the same operands.
 __global__ void k_f64_to_bf16(const double* src, long long s_bs, int s_ld, __nv_bfloat16* dst, long long d_bs,
                               int d_ld, int n, int transpose) {
     __shared__ double tile[32][33];
@@ -47,10 +49,10 @@ __global__ void k_f64_to_bf16(const double* src, long long s_bs, int s_ld, __nv_
     for (int j = threadIdx.y; j < 32; j += blockDim.y) {
         if (transpose) {
             const int y = bx + j, x = by + threadIdx.x;   // dst row = src column
-            if (x < n && y < n) dst[(size_t)y * d_ld + x] = __double2bfloat16(tile[threadIdx.x][j]);
+            if (x < n && y < n) dst[(size_t)y * d_ld + x] = __float2bfloat16_rn((float)tile[threadIdx.x][j]);
         } else {
             const int y = by + j, x = bx + threadIdx.x;
-            if (x < n && y < n) dst[(size_t)y * d_ld + x] = __double2bfloat16(tile[j][threadIdx.x]);
+            if (x < n && y < n) dst[(size_t)y * d_ld + x] = __float2bfloat16_rn((float)tile[j][threadIdx.x]);
         }
     }
 }
@@ -70,6 +72,8 @@ extern "C" mofem_status mofem_precond_noalloc(mofem_handle h, const float* R, fl
     }
     // Device address of the static array, looked up once per device with that
     // device current (the host-side symbol is only a stand-in, not a device address).
+    // Under lazy module loading this first lookup may load the module, which is when
+    // the array itself is allocated.
     int dev = 0;
     MOFEM_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return MOFEM_ERR_UNSUPPORTED;

@@ -263,9 +263,15 @@ static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mo
     Band Ctt = assemble(Qd, n, KIND_G, tw);
     H.Mt = Mt;
     H.Kt = Kt;
-    const bool product = opts.pencil == MOFEM_PENCIL_PRODUCT;
-    H.F1 = product ? identity_band(n, Mt.K) : Mt;
-    H.F2 = product ? add(Kt, Ktt2, 1.0) : Kt;
+    // t-pencil F2 Q2 = F1 Q2 diag(mu).  Single-term preconditioners E Z F^T take the
+    // standard eigenpairs of F (F1 = I): PRODUCT F = K_t + K_t[t^2]; PARABOLIC F = M_t +
+    // (K_t + K_t[t^2]) / gamma (the IMEX step scaled by 1/(d_u tau)); AUA F = K_t.
+    const bool single = opts.pencil == MOFEM_PENCIL_PRODUCT || opts.pencil == MOFEM_PENCIL_PARABOLIC ||
+                        opts.pencil == MOFEM_PENCIL_AUA;
+    H.F1 = single ? identity_band(n, Mt.K) : Mt;
+    if (opts.pencil == MOFEM_PENCIL_PRODUCT) H.F2 = add(Kt, Ktt2, 1.0);
+    else if (opts.pencil == MOFEM_PENCIL_PARABOLIC) H.F2 = add(Mt, add(Kt, Ktt2, 1.0), 1.0 / gamma[0]);
+    else H.F2 = Kt;
 
     std::vector<double>& Th = H.T;
     Th.assign((size_t)NT * P * q, 0.0);
@@ -324,9 +330,13 @@ static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mo
             trimmed_table(Gdh, q, off, lo, hi, true, -1.0, sslot(7));
         }
         trimmed_table(Msh, q, off, 0, n - 1, false, 1.0, H.Srh.data() + (size_t)i * P * q);
-        if (product) {   // K_s[h] Z (K_t + K_t[t^2])^T: standard eigenpairs on each side
+        if (opts.pencil == MOFEM_PENCIL_PRODUCT || opts.pencil == MOFEM_PENCIL_AUA) {
+            // K_s[h] Z F^T: standard eigenpairs on each side
             H.E1s[i] = Ksh;
             H.E2s[i] = identity_band(n, Ksh.K);
+        } else if (opts.pencil == MOFEM_PENCIL_PARABOLIC) {   // (K_s[h] + gamma M_s[h]) Z F^T
+            H.E1s[i] = S0;
+            H.E2s[i] = identity_band(n, S0.K);
         } else {
             H.E1s[i] = S0;
             H.E2s[i] = (opts.pencil == MOFEM_PENCIL_DOMINANT) ? Msa : assemble(Qd, n, KIND_M, we2[i]);
@@ -562,7 +572,10 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
         };
         // t-pencil (shared): K_t x = mu M_t x (product form: (K_t + K_t[t^2]) x = mu x)
         if ((result = solve_pencil(H.F2, H.F1, c->Q2_64, c->mu64)) != MOFEM_OK) break;
-        c->div_product = c->opts.pencil == MOFEM_PENCIL_PRODUCT ? 1 : 0;
+        c->div_product = (c->opts.pencil == MOFEM_PENCIL_PRODUCT || c->opts.pencil == MOFEM_PENCIL_PARABOLIC ||
+                          c->opts.pencil == MOFEM_PENCIL_AUA)
+                             ? 1
+                             : 0;
         for (int i = 0; i < B && result == MOFEM_OK; ++i)
             result = solve_pencil(E1s[i], E2s[i], c->Q1_64 + (size_t)i * q * ld, c->lam64 + (size_t)i * ld);
         if (result != MOFEM_OK) break;

@@ -931,6 +931,12 @@ mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int re
                                                  &nblk, st));
         return MOFEM_OK;
     }
+    if (kernel == 11) {   // the FP64 form's preconditioner: four cuBLAS DGEMMs per instance + division
+        MOFEM_TRY(ensure_w64(c, st));
+        for (int r = 0; r < reps; ++r)
+            MOFEM_TRY(precond64(c, w64(c, W64_R), bs, c->ld, w64(c, W64_Z), bs, c->ld, st));
+        return MOFEM_OK;
+    }
     if (kernel == 8) {   // double-float residual update of a refinement step
         int nblk = 0;
         for (int r = 0; r < reps; ++r)

@@ -199,3 +199,34 @@ def hetero_instances(count, n_choices=(129, 257, 513, 1025, 2049), k_choices=(1,
         out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet',
                         F=fourier_f(ZERO, g2, n, seed * 100000 + i)))
     return out
+
+
+CAP_LOWER = Profile(c0=-1.0, c2=0.5)     # y = x^2/2 - 1
+CAP_UPPER = Profile(c0=1.0, c2=-0.5)     # y = 1 - x^2/2
+
+
+def _poly_mul(a, b):
+    """Product of two 2D coefficient arrays c[i, j] of x^i y^j."""
+    out = np.zeros((a.shape[0] + b.shape[0] - 1, a.shape[1] + b.shape[1] - 1))
+    for i in range(a.shape[0]):
+        for j in range(a.shape[1]):
+            out[i:i + b.shape[0], j:j + b.shape[1]] += a[i, j] * b
+    return out
+
+
+def cap_heat_problem(k, N, d_u=0.1):
+    """The heat test on the cap-shaped domain (Sec. 6; x and y swapped to this
+    orientation): x^2/2 - 1 <= y <= 1 - x^2/2, zero Dirichlet data,
+    u(x, y, t) = u0(x, y) e^t with u0 = x (x - 1)(-x^2/2 + y + 1)(x^2/2 + y - 1), so
+    f = e^t (u0 - d_u Lap u0).  N elements per direction of degree max(k, 1).
+    Returns dict(g1, g2, k, n, d_u, u0 (n x n nodal), f(t) -> n x n nodal)."""
+    P2 = np.polynomial.polynomial
+    c = _poly_mul(_poly_mul(np.array([[0.0], [-1.0], [1.0]]), np.array([[1.0, 1.0], [0.0, 0.0], [-0.5, 0.0]])),
+                  np.array([[-1.0, 1.0], [0.0, 0.0], [0.5, 0.0]]))
+    lap = (np.pad(P2.polyder(c, 2, axis=0), ((0, 2), (0, 0))) +
+           np.pad(P2.polyder(c, 2, axis=1), ((0, 0), (0, 2))))
+    n = max(k, 1) * N + 1
+    X, Y = nodal_xy(CAP_LOWER, CAP_UPPER, n)
+    u0 = P2.polyval2d(X, Y, c)
+    f0 = u0 - d_u * P2.polyval2d(X, Y, lap)
+    return dict(g1=CAP_LOWER, g2=CAP_UPPER, k=k, n=n, d_u=d_u, u0=u0, f=lambda t: math.exp(t) * f0)

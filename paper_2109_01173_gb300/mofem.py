@@ -17,7 +17,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_EIG, ERR_NONFINITE, ERR_BREAKDOWN, ERR_NOT_CO
     ERR_OOM, ERR_UNSUPPORTED = range(10)
 DIRICHLET, NEUMANN = 0, 1
 FP64, MIXED_TF32, MIXED_BF16, MIXED_FP16 = 0, 1, 2, 3
-PENCIL_AVERAGED, PENCIL_DOMINANT, PENCIL_PRODUCT = 0, 1, 2
+PENCIL_AVERAGED, PENCIL_DOMINANT, PENCIL_PRODUCT, PENCIL_PARABOLIC, PENCIL_AUA = 0, 1, 2, 3, 4
 FLAG_HOST_LOOP, FLAG_FIXED_ITERS, FLAG_TRUE_RESIDUAL = 1, 2, 4
 
 PRECISIONS = {"fp64": FP64, "tf32": MIXED_TF32, "bf16": MIXED_BF16, "fp16": MIXED_FP16}
@@ -91,6 +91,7 @@ def _load():
                           P(SolveInfo), vp],
         "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
                                     vp],
+        "mofem_get_eigen": [vp, vp, vp, vp, vp, P(c_int), vp],
         "mofem_destroy": [vp],
         "mofem_bench_kernel": [vp, c_int, c_int, c_int, vp],
         "mofem_host_tables": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), P(c_int), P(c_int),
@@ -115,7 +116,7 @@ EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply
             "mofem_dib_kinetics", "mofem_dib_run", "mofem_dib_equilibrium", "mofem_group_layout",
             "mofem_group_setup", "mofem_group_solve", "mofem_group_autotune", "mofem_group_destroy",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
-            "mofem_host_tables", "mofem_host_dd_tables", "mofem_bench_kernel"]
+            "mofem_host_tables", "mofem_host_dd_tables", "mofem_bench_kernel", "mofem_get_eigen"]
 
 
 def _check(fn, code):
@@ -298,6 +299,21 @@ class Handle:
         if check:
             _check("mofem_dib_run", code)
         return info, code, (list(inc)[:n_steps] if increments else None)
+
+    def eigen(self):
+        """Preconditioner eigen data as FP64 device tensors (Q1 [batch][q][q], Q2 [q][q],
+        lambda [batch][q], mu [q]) and whether the divisor is lambda_a mu_b (True) or
+        lambda_a + mu_b (False)."""
+        import torch
+        q, B = self.q, self.batch
+        Q1 = torch.empty((B, q, q), dtype=torch.float64, device="cuda")
+        Q2 = torch.empty((q, q), dtype=torch.float64, device="cuda")
+        lam = torch.empty((B, q), dtype=torch.float64, device="cuda")
+        mu = torch.empty((q,), dtype=torch.float64, device="cuda")
+        prod = ctypes.c_int()
+        _check("mofem_get_eigen", LIB.mofem_get_eigen(self.h, _ptr(Q1), _ptr(Q2), _ptr(lam), _ptr(mu),
+                                                      ctypes.byref(prod), _stream()))
+        return Q1, Q2, lam, mu, bool(prod.value)
 
     def bench_kernel(self, kernel, precision="bf16", reps=1):
         """Launch one hot kernel `reps` times on internal buffers (timing hook)."""

@@ -77,6 +77,22 @@ def test_invalid_arguments_rejected_without_gpu(mofem):
     assert L.mofem_dib_kinetics(None, 1.0, None, None, None, None, 0, None) == 1
     assert L.mofem_dib_run(None, None, 1.0, 1.0, 1, None, 0.0, 0, None, None, None) == 1
     assert L.mofem_destroy(None) == 1
+    assert L.mofem_get_eigen(None, None, None, None, None, None, None) == 1
+    # the single-term stiffness preconditioners are singular under Neumann BC; the parabolic
+    # one needs one positive gamma for the whole batch (its t-factor is shared)
+    for pencil in (mofem.PENCIL_PRODUCT, mofem.PENCIL_AUA):
+        o = mofem.make_opts(pencil=pencil)
+        assert L.mofem_setup(ctypes.byref(p), ctypes.byref(p2), 2, 65, 1.0, 1, ctypes.byref(o), None,
+                             ctypes.byref(h)) == 1
+    o = mofem.make_opts(pencil=mofem.PENCIL_PARABOLIC)
+    arr1, arr2 = (mofem.Profile * 2)(p, p), (mofem.Profile * 2)(p2, p2)
+    gam = (ctypes.c_double * 2)(100.0, 50.0)
+    assert L.mofem_setup_batched(2, arr1, arr2, 2, 65, gam, 0, ctypes.byref(o), None, ctypes.byref(h)) == 1
+    assert L.mofem_setup(ctypes.byref(p), ctypes.byref(p2), 2, 65, 0.0, 0, ctypes.byref(o), None,
+                         ctypes.byref(h)) == 1
+    o = mofem.make_opts(pencil=5)
+    assert L.mofem_setup(ctypes.byref(p), ctypes.byref(p2), 2, 65, 1.0, 0, ctypes.byref(o), None,
+                         ctypes.byref(h)) == 1
 
 
 def band_to_dense(tab, q, K, cols, off):

@@ -1,0 +1,174 @@
+"""Full-size GPU checks on the metric workload (P2, 2049 x 2049 nodes, q = 2047).
+
+* The tensor-core preconditioner (mofem_precond, FP16 / BF16 / TF32 operands) is
+  checked element by element on a batch of four instances, against an FP64 host
+  evaluation of the same four products Z = Q1 ((Q1^T R Q2) ./ (lambda_a + mu_b)) Q2^T
+  on the handle's own FP64 eigen data (Sec. 4, Eq. reduced_formula_for_u).  Every
+  output element must lie within a running forward-error bound of the chain: operand
+  rounding (u_op), FP32 accumulation (gamma = q 2^-23), the rounding of each stored
+  intermediate (u_st relative, plus the subnormal quantum of FP16), propagated through
+  |Q1|, |Q2| and 1/|lambda + mu|.  The chain runs once alone (static tile order) and
+  once while a second handle's chain is in flight (dynamic tile order); both results
+  must be bitwise equal.
+* One instance of the metric workload is solved by the FP64 oracle (reduced
+  preconditioner, relative residual 1e-12) and the GPU solutions of the mixed FP16 form
+  (rtol 1e-10, as in the benchmark) and of the FP64 form must agree with it to 1e-8.
+"""
+import numpy as np
+import pytest
+
+from paper_2109_01173_gb300.inputs import metric_instance
+
+pytestmark = pytest.mark.gpu
+
+N, K, B = 2049, 2, 4
+U16, UBF, UTF = 2.0 ** -11, 2.0 ** -8, 2.0 ** -10
+FP16_RMS = 2e-3   # RMS of the scaled FP16 residual operand
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    torch.cuda.set_device(0)
+    import paper_2109_01173_gb300.mofem as mf
+    insts = [metric_instance(n=N, k=K, seed=i) for i in range(B)]
+    h = mf.Handle([i["g1"] for i in insts], [i["g2"] for i in insts], K, N, [i["gamma"] for i in insts])
+    Q1, Q2, lam, mu, prod = h.eigen()
+    torch.cuda.synchronize()
+    eig = dict(Q1=Q1.cpu().numpy(), Q2=Q2.cpu().numpy(), lam=lam.cpu().numpy(), mu=mu.cpu().numpy(), prod=prod)
+    yield torch, mf, insts, h, eig
+    h.close()
+
+
+def _stored(x_abs, pre, u, eps):
+    """Error bound after storing a value of magnitude <= x_abs + pre (pre: error before
+    storage) in a format of unit roundoff u and absolute subnormal quantum eps."""
+    m = x_abs + pre
+    return pre + u * m + np.minimum(eps, m)
+
+
+def chain_and_bound(Q1, Q2, lam, mu, R, u_op, u_st, eps_st, eps_r, q):
+    """FP64 value of the four products and an elementwise bound of the GPU's error."""
+    gam = q * 2.0 ** -23
+    D = lam[:, None] + mu[None, :]
+    X1 = R @ Q2
+    W = (Q1.T @ X1) / D
+    Y = Q1 @ W
+    Z = Y @ Q2.T
+    f32 = np.float32
+    aQ1, aQ2 = np.abs(Q1).astype(f32), np.abs(Q2).astype(f32)
+    # G1: X1 = R~ Q2~, R~ with relative u_op and absolute eps_r, Q2~ relative u_op
+    p1 = ((2 * u_op + gam) * (np.abs(R).astype(f32) @ aQ2)).astype(np.float64) + eps_r * aQ2.sum(0)[None, :]
+    e1 = _stored(np.abs(X1), p1, u_st, eps_st)
+    # G2: W = (Q1~^T X1~) ./ D (FP32 divide of FP32 lambda + mu)
+    pT = (aQ1.T @ (e1 + (u_op + gam) * np.abs(X1)).astype(f32)).astype(np.float64)
+    eW = _stored(np.abs(W), pT / np.abs(D) + 2.0 ** -21 * np.abs(W), u_st, eps_st)
+    # G3: Y = Q1~ W~
+    pY = (aQ1 @ (eW + (u_op + gam) * np.abs(W)).astype(f32)).astype(np.float64)
+    eY = _stored(np.abs(Y), pY, u_st, eps_st)
+    # G4: Z = Y~ Q2~^T (FP32 output, unscaled)
+    eZ = ((eY + (u_op + gam) * np.abs(Y)).astype(f32) @ aQ2.T).astype(np.float64) + 2.0 ** -22 * np.abs(Z)
+    return Z, eZ
+
+
+def _precision_model(prec, R, q):
+    """(u_op, u_st, eps_st, eps_r) of a precision in the units of the unscaled chain."""
+    if prec == "fp16":
+        s = FP16_RMS * np.sqrt(q * q / float(np.sum(R.astype(np.float64) ** 2)))
+        eps = 2.0 ** -25 / s          # half the FP16 subnormal spacing, unscaled
+        return U16 + 2.0 ** -24, U16 + 2.0 ** -24, eps, eps
+    if prec == "bf16":
+        return UBF + 2.0 ** -24, UBF + 2.0 ** -24, 1e-37, 1e-37
+    # TF32: operands and stored FP32 intermediates read by the next product at 10 bits
+    return UTF, UTF + 2.0 ** -24, 1e-37, 1e-37
+
+
+def _inputs(torch, h, insts, kind):
+    q = h.q
+    if kind == "random":
+        R = np.random.default_rng(11).standard_normal((B, q, q)).astype(np.float32)
+    else:   # the solver's first residual: the right-hand side of each instance (smooth)
+        F = torch.tensor(np.stack([i["F"] for i in insts]), dtype=torch.float64, device="cuda")
+        Bt = torch.zeros((B, q, q), dtype=torch.float64, device="cuda")
+        h.rhs(F, Bt)
+        torch.cuda.synchronize()
+        R = Bt.float().cpu().numpy()
+    return R
+
+
+# White noise puts most FP16 spectral coefficients of the divided product in the FP16
+# subnormal range, where a worst-case bound of the quantum summed over q^2 terms says
+# nothing; FP16 is checked on the solver's own kind of residual (smooth), the other two
+# operand formats on both.
+CASES = [("fp16", "rhs"), ("bf16", "rhs"), ("tf32", "rhs"), ("bf16", "random"), ("tf32", "random")]
+
+
+@pytest.mark.parametrize("prec,kind", CASES)
+def test_precond_elementwise_full_size(env, prec, kind):
+    torch, mf, insts, h, eig = env
+    q = h.q
+    R = _inputs(torch, h, insts, kind)
+    Rt = torch.tensor(R, device="cuda")
+    Z1 = torch.zeros_like(Rt)
+    h.precond(Rt, Z1, prec)                    # alone: static tile order
+    torch.cuda.synchronize()
+    # concurrently with a second handle's chain on another stream: dynamic tile order
+    h2 = mf.Handle([i["g1"] for i in insts], [i["g2"] for i in insts], K, N, [i["gamma"] for i in insts])
+    R2 = torch.tensor(np.random.default_rng(5).standard_normal((B, q, q)).astype(np.float32), device="cuda")
+    Z2o = torch.zeros_like(R2)
+    h2.precond(R2, Z2o, prec)                  # plans and buffers ready before the overlapped run
+    Z2 = torch.zeros_like(Rt)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        with torch.cuda.stream(s2):
+            h2.precond(R2, Z2o, prec)
+        with torch.cuda.stream(s1):
+            h.precond(Rt, Z2, prec)
+        torch.cuda.synchronize()
+        assert torch.equal(Z1, Z2)
+    h2.close()
+    Zg = Z1.cpu().numpy().astype(np.float64)
+    worst = []
+    for i in range(B):
+        u_op, u_st, eps_st, eps_r = _precision_model(prec, R[i], q)
+        Zx, eZ = chain_and_bound(eig["Q1"][i], eig["Q2"], eig["lam"][i], eig["mu"], R[i].astype(np.float64),
+                                 u_op, u_st, eps_st, eps_r, q)
+        err = np.abs(Zg[i] - Zx)
+        ratio = err / (eZ + 1e-300)
+        bad = np.argwhere(ratio > 1.0)
+        assert bad.size == 0, (prec, kind, i, bad[:5].tolist(), float(ratio.max()))
+        # the bound is informative: far below the size of Z itself
+        assert float(np.median(eZ / (np.abs(Zx).max()))) < 0.05, (prec, kind, i)
+        worst.append(float(ratio.max()))
+    print(f"{prec} {kind}: max err/bound per instance {worst}")
+
+
+def test_full_size_solution_matches_the_oracle(env):
+    """Instance 0 of the metric workload: the oracle's FP64 MO-PCG solution (reduced
+    preconditioner, relative residual 1e-12) against the GPU's mixed FP16 solution at the
+    benchmark's rtol 1e-10 (batched, as timed) and the FP64 GPU form's, both to 1e-8."""
+    torch, mf, insts, h, eig = env
+    from oracle.operator import Problem
+    from oracle import pcg
+    q = h.q
+    F = torch.tensor(np.stack([i["F"] for i in insts]), dtype=torch.float64, device="cuda")
+    U = torch.zeros((B, q, q), dtype=torch.float64, device="cuda")
+    info, _ = h.pcg_solve(F, U, rtol=1e-10, max_iter=500, precision="fp16")
+    assert info.rel_residual <= 1e-10
+    i0 = insts[0]
+    h1 = mf.Handle(i0["g1"], i0["g2"], K, N, i0["gamma"])
+    U64 = torch.zeros((q, q), dtype=torch.float64, device="cuda")
+    info64, _ = h1.pcg_solve(F[0], U64, rtol=1e-10, max_iter=500, precision="fp64")
+    h1.close()
+    P = Problem(i0["g1"], i0["g2"], K, N, i0["gamma"])
+    Uo, oinfo = pcg.solve(P, i0["F"], rtol=1e-12, max_iter=400)
+    assert oinfo["rel_residual"] <= 1e-12
+    nrm = np.linalg.norm(Uo)
+    e16 = np.linalg.norm(U[0].cpu().numpy() - Uo) / nrm
+    e64 = np.linalg.norm(U64.cpu().numpy() - Uo) / nrm
+    print(f"full size vs oracle: fp16 {e16:.2e} ({info.iterations} it), fp64 {e64:.2e} ({info64.iterations} it), "
+          f"oracle {oinfo['iterations']} it")
+    assert e16 <= 1e-8 and e64 <= 1e-8, (e16, e64)

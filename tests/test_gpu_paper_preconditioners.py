@@ -1,0 +1,147 @@
+"""The paper's single-term preconditioners on the GPU, through the C ABI.
+
+* AUA (Sec. 5.1, Eq. precSquare; mofem_pencil AUA): Z solving A Z A^T = R on the unit
+  square equals the oracle's banded solves, and MO-PCG with it stops after the
+  printed two iterations under the paper's increment rule (Table 1: Poisson on the
+  square, ||U(s+1) - U(s)||_F <= 0.05 ||err_v||_F with err_v the direct solver's error).
+* The IMEX-step preconditioner (Sec. 6, Eqs. semilinear_heat_equation_fully_discrete_P
+  and its lumped form; mofem_pencil PARABOLIC): Z equals d_u tau times the oracle's
+  (M3 + d_u tau B1)^-1 R (M + d_u tau (A + B2))^-T (the handle's operator is the step
+  scaled by 1/(d_u tau)), on one- and two-instance handles; and on the paper's heat test
+  on the cap-shaped domain (Sec. 6, Test 2: d_u = 0.1, tau = 0.01, the N = 480 row of its
+  table) each IMEX step with the paper's stopping rule ||R_s|| <= tau ||R_0|| takes the
+  printed one MO-PCG iteration for P_k, k = 1..4, and at most two for lumped P1.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle.operator import Problem, apply_terms, rhs
+from oracle.fem1d import trim
+from oracle import pcg, assembly2d
+from oracle.heat import paper_heat_preconditioner
+from paper_2109_01173_gb300.inputs import Profile, ZERO, SIN_TOP, cap_heat_problem
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_printed_values.json")))
+ONE = Profile(c0=1.0)
+TWO = (Profile(c2=0.1), Profile(c0=1.0, ca=0.2, cf=1.0))
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    torch.cuda.set_device(0)
+    import paper_2109_01173_gb300.mofem as m
+    return m
+
+
+def _t():
+    import torch
+    return torch
+
+
+@pytest.mark.parametrize("k,n", [(1, 50), (2, 61), (4, 97)])
+def test_aua_preconditioner_parity(mf, k, n):
+    torch = _t()
+    h = mf.Handle(ZERO, ONE, k, n, 0.0, opts=mf.make_opts(pencil=mf.PENCIL_AUA))
+    P = Problem(ZERO, ONE, k, n, 0.0)
+    A = trim(P.factors()['Kt_1'], P.idx)
+    R = np.random.default_rng(k).standard_normal((h.q, h.q))
+    Zo = pcg.ProductPreconditioner(A, A)(R)
+    Z = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+    h.precond(torch.tensor(R, device="cuda"), Z, "fp64")
+    assert np.linalg.norm(Z.cpu().numpy() - Zo) <= 1e-9 * np.linalg.norm(Zo)
+    h.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [24, 48])
+def test_aua_two_iterations_on_the_square(mf, k, N):
+    """Table 1 (Sec. 5.1): MO-PCG with AUA stops after two iterations under the paper's
+    increment rule.  U(s) after s iterations from U = 0 comes from FP64 solves with exactly
+    s iterations; err_v is the oracle's direct vector-form solution against the exact
+    u = sin(2 pi x) sin(2 pi y)."""
+    torch = _t()
+    n = k * N + 1
+    s = np.arange(n) / (n - 1)
+    F = 8 * np.pi ** 2 * np.outer(np.sin(2 * np.pi * s), np.sin(2 * np.pi * s))
+    Uex = np.outer(np.sin(2 * np.pi * s), np.sin(2 * np.pi * s))[1:-1, 1:-1]
+    errv = np.linalg.norm(assembly2d.direct_solve(Problem(ZERO, ONE, k, n, 0.0), F) - Uex)
+    h = mf.Handle(ZERO, ONE, k, n, 0.0,
+                  opts=mf.make_opts(pencil=mf.PENCIL_AUA, flags=mf.FLAG_FIXED_ITERS))
+    Ft = torch.tensor(F, device="cuda")
+    prev = np.zeros((h.q, h.q))
+    stop = None
+    for it in range(1, 5):
+        U = torch.zeros((h.q, h.q), dtype=torch.float64, device="cuda")
+        info, code = h.pcg_solve(Ft, U, rtol=1e-15, max_iter=it, precision="fp64", check=False)
+        assert info.iterations == it, (it, info.iterations, code)
+        Un = U.cpu().numpy()
+        if stop is None and np.linalg.norm(Un - prev) <= 0.05 * errv:
+            stop = it
+        prev = Un
+    h.close()
+    assert stop == GOLD["square_aua_pcg_iterations"]["value"], stop
+
+
+@pytest.mark.parametrize("k,n,bc", [(2, 61, 0), (0, 70, 1), (1, 81, 0)])
+def test_parabolic_preconditioner_parity(mf, k, n, bc):
+    torch = _t()
+    d_u, tau = 0.1, 0.01
+    gam = 1.0 / (d_u * tau)
+    tops = [TWO[1], Profile(c0=1.0, sa=0.25)]
+    bots = [TWO[0], ZERO]
+    h = mf.Handle(bots, tops, k, n, gam, bc=bc, opts=mf.make_opts(pencil=mf.PENCIL_PARABOLIC))
+    R = np.random.default_rng(n).standard_normal((2, h.q, h.q))
+    Z = torch.zeros((2, h.q, h.q), dtype=torch.float64, device="cuda")
+    h.precond(torch.tensor(R, device="cuda"), Z, "fp64")
+    for i in range(2):
+        P = Problem(bots[i], tops[i], k, n, 0.0, bc="dirichlet" if bc == 0 else "neumann")
+        Zo = d_u * tau * paper_heat_preconditioner(P, d_u, tau)(R[i])
+        assert np.linalg.norm(Z[i].cpu().numpy() - Zo) <= 1e-9 * np.linalg.norm(Zo), i
+    h.close()
+
+
+def test_parabolic_rejects_unequal_gamma(mf):
+    with pytest.raises(mf.MofemError):
+        mf.Handle([ZERO, ZERO], [SIN_TOP, SIN_TOP], 1, 33, [100.0, 200.0],
+                  opts=mf.make_opts(pencil=mf.PENCIL_PARABOLIC))
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
+def test_heat_one_iteration_per_step_cap_domain(mf, k):
+    """Sec. 6, Test 2, N = 480 (the first row of its table; N elements per direction),
+    d_u = 0.1, tau = 0.01: the first ten IMEX steps, each by mofem_imex_step (the paper's
+    rule ||R_s|| <= tau ||R_0||) in the FP64 form with the PARABOLIC preconditioner; the
+    mixed form's inner iterations are reported beside it."""
+    torch = _t()
+    N, d_u, tau = 480, 0.1, 0.01
+    prob = cap_heat_problem(k, N, d_u)
+    n = prob["n"]
+    h = mf.Handle(prob["g1"], prob["g2"], k, n, 1.0 / (d_u * tau), opts=mf.make_opts(pencil=mf.PENCIL_PARABOLIC))
+    U = torch.tensor(prob["u0"][1:-1, 1:-1].copy(), device="cuda")
+    its, its_mixed = [], []
+    Um = U.clone()
+    for step in range(10):
+        Ft = torch.tensor(prob["f"](step * tau), device="cuda")
+        Un = torch.empty_like(U)
+        info, _ = h.imex_step(d_u, tau, U, Ft, Un, precision="fp64")
+        its.append(info.iterations)
+        U = Un
+        Umn = torch.empty_like(Um)
+        info_m, _ = h.imex_step(d_u, tau, Um, Ft, Umn, precision="fp16")
+        its_mixed.append(info_m.iterations)
+        Um = Umn
+    h.close()
+    want = GOLD["heat_mo_pcg_iterations_per_step"]["value"]
+    print(f"k={k}: FP64 iterations per step {its}, mixed (TF32 operands) {its_mixed}")
+    if k == 0:
+        assert max(its) <= want["lumped_p1_at_most"], its
+    else:
+        assert all(i == want["p_k"] for i in its), its

@@ -255,6 +255,36 @@ def test_batched_solve(mf):
     h.close()
 
 
+@pytest.mark.parametrize("prec", ["fp16", "fp64"])
+def test_zero_right_hand_side(mf, prec):
+    """F = 0 gives U = 0 at once (the initialisation marks the instance inactive), alone
+    and as one instance of a batch whose other instances solve as they do alone."""
+    torch = torch_()
+    n, k = 97, 2
+    h1 = mf.Handle(ZERO, SIN_TOP, k, n, 1.0)
+    U1 = torch.full((h1.q, h1.q), 0.0, dtype=torch.float64, device="cuda")
+    info, code = h1.pcg_solve(torch.zeros((n, n), dtype=torch.float64, device="cuda"), U1, rtol=1e-10,
+                              max_iter=100, precision=prec, check=False)
+    assert code == mf.OK and info.iterations == 0 and info.rel_residual == 0.0
+    assert bool((U1 == 0).all())
+    h1.close()
+    g2s = [Profile(c0=1.0, sa=0.1, sf=1), Profile(c0=1.0, sa=0.25, sf=2), Profile(c0=1.0, sa=0.2, sf=1),
+           Profile(c0=1.0, sa=0.3, sf=3)]
+    gam = [1.0, 3.5, 2.0, 9.0]
+    Fs = [fourier_f(ZERO, g, n, seed=i) for i, g in enumerate(g2s)]
+    Fs[2] = np.zeros((n, n))
+    h = mf.Handle([ZERO] * 4, g2s, k, n, gam)
+    U = torch.zeros((4, h.q, h.q), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(torch.tensor(np.stack(Fs), device="cuda"), U, rtol=1e-10, max_iter=400,
+                             precision=prec)
+    assert code == mf.OK and info.rel_residual <= 1e-10
+    assert bool((U[2] == 0).all())
+    for i in (0, 1, 3):
+        Uo, _ = pcg.solve(Problem(ZERO, g2s[i], k, n, gam[i]), Fs[i], rtol=1e-13)
+        assert np.linalg.norm(U[i].cpu().numpy() - Uo) <= 1e-8 * np.linalg.norm(Uo), i
+    h.close()
+
+
 def test_deterministic(mf):
     torch = torch_()
     inst = metric_instance(n=129, k=2, seed=3)
