@@ -25,6 +25,16 @@ discrete adjoint (derived here; the paper does not differentiate) is
     dJ/dU_0 = lam_0,
 
 from differentiating S U_{n+1} = M U_n:  S dU_{n+1} = M dU_n - tau dd_u A U_{n+1}.
+With a source and a linear reaction, u_t - d_u Lap u = f(x) - r u, both explicit as
+Sec. 6 treats the reaction term (f nodal on all n x n nodes, constant in time):
+
+    S U_{n+1} = (1 - tau r) M U_n + tau M_all f,      M_all f := M_s[h]_{int,all} F M_t_{int,all}^T,
+
+and differentiating, S dU_{n+1} = (1 - tau r) M dU_n - tau dr M U_n + tau M_all df
+- tau dd_u A U_{n+1}, so with y = S^{-1} lam_{n+1}:
+
+    lam_n = (1 - tau r) M y,   dJ/df += tau M_all^T y,   dJ/dr += -tau <y, M U_n>,
+    dJ/dd_u += -tau <y, A U_{n+1}>.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -54,6 +64,8 @@ class HeatOperators:
         self.A = kron_operator(P.terms())
         f = P.factors()
         self.M = sp.kron(trim(f['Ms_h'], P.idx), trim(f['Mt'], P.idx), format='csc')
+        self.M_all = sp.kron(trim(f['Ms_h'], P.idx, np.arange(n)), trim(f['Mt'], P.idx, np.arange(n)),
+                             format='csc')
 
     def system(self, d_u, tau):
         """Factorised S = M + d_u tau A."""
@@ -128,3 +140,36 @@ def imex_mo_pcg_step(problem, d_u, tau, U, F_all, precond, max_iter=100):
         return U, 0
     U1, info = mo_pcg(L, precond, B, U0=U, rtol=tau * np.sqrt(fro(R0, R0)) / nb, max_iter=max_iter)
     return U1, info['iterations']
+
+
+def imex_forward_src(ops, d_u, tau, U0, n_steps, F, r):
+    """States U_0 .. U_N of S U_{n+1} = (1 - tau r) M U_n + tau M_all F (module docstring):
+    a nodal source F (n x n, constant in time) and a linear reaction r u, both explicit."""
+    lu = ops.system(d_u, tau)
+    q = ops.q
+    U = np.asarray(U0, dtype=np.float64).reshape(q, q)
+    src = tau * (ops.M_all @ np.asarray(F, dtype=np.float64).ravel())
+    states = [U]
+    for _ in range(n_steps):
+        U = lu.solve((1.0 - tau * r) * (ops.M @ U.ravel()) + src).reshape(q, q)
+        states.append(U)
+    return states
+
+
+def imex_adjoint_src(ops, d_u, tau, r, states, dJ_dUN):
+    """(dJ/dU_0, dJ/dd_u, dJ/dF (n x n), dJ/dr) of imex_forward_src by the adjoint
+    recursion of the module docstring."""
+    lu = ops.system(d_u, tau)
+    q = ops.q
+    n = int(round(np.sqrt(ops.M_all.shape[1])))
+    lam = np.asarray(dJ_dUN, dtype=np.float64).ravel()
+    g_du, g_r = 0.0, 0.0
+    g_F = np.zeros(n * n)
+    for i in range(len(states) - 2, -1, -1):
+        y = lu.solve(lam)
+        g_du -= tau * float(y @ (ops.A @ states[i + 1].ravel()))
+        My = ops.M @ y          # M symmetric
+        g_r -= tau * float(My @ states[i].ravel())
+        g_F += tau * (ops.M_all.T @ y)
+        lam = (1.0 - tau * r) * My
+    return lam.reshape(q, q), g_du, g_F.reshape(n, n), g_r

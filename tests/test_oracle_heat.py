@@ -8,7 +8,12 @@
   closed form in d.
 * Adjoint against the forward map: on curved two-profile domains (eight terms,
   Dirichlet and Neumann, P1/P2) the adjoint gradient equals central finite
-  differences of the forward solve, for U_0 along random directions and for d_u.
+  differences of the forward solve, for U_0 along random directions and for d_u;
+  with a nodal source f and an explicit linear reaction r u, also for f along random
+  nodal directions and for r.
+* Source and reaction: with f = 0 the square's sine mode is multiplied by
+  (1 - tau r) / (1 + d tau (lam_i + lam_j)) per step, so J and dJ/dr have a closed
+  form; f = 0 and r = 0 reduce the extended recursion to the plain one.
 * Convergence: the paper's heat test on the cap-shaped domain (Sec. 6, Test 1:
   d_u = 0.1, u = u(x, y, 0) e^t, the step shrinking by 2^(k+1) per mesh halving)
   reaches its printed rates (k + 1; lumped P1 and P1: 2) on two coarse meshes.  At
@@ -28,7 +33,7 @@ import pytest
 
 from oracle import closed_form
 from oracle.heat import (HeatOperators, imex_forward, imex_adjoint, loss, paper_heat_preconditioner,
-                         imex_mo_pcg_step)
+                         imex_mo_pcg_step, imex_forward_src, imex_adjoint_src)
 from oracle.fem1d import trim
 from oracle.pcg import ProductPreconditioner
 from oracle.operator import Problem
@@ -189,3 +194,66 @@ def test_paper_heat_preconditioner_lumped_and_mass_only():
     assert max(its) <= GOLD["heat_mo_pcg_iterations_per_step"]["value"]["lumped_p1_at_most"], its
     # the uncorrected mass preconditioner the paper starts from needs more iterations
     assert max(_cap_heat_iterations(1, 48, "mass")) >= 3
+
+
+def test_square_reaction_gradient_closed_form():
+    N, d, tau, steps, c0, r = 12, 0.2, 0.02, 5, 0.5, 1.5
+    ops = HeatOperators(ZERO, ONE, 1, N + 1, 'dirichlet')
+    U0, Lam = _mode(N, 2, 1)
+    F0 = np.zeros((N + 1, N + 1))
+    states = imex_forward_src(ops, d, tau, U0, steps, F0, r)
+    J, dJ = loss(states[-1], c0 * U0)
+    _, g_du, g_F, g_r = imex_adjoint_src(ops, d, tau, r, states, dJ)
+    g = (1.0 - tau * r) / (1.0 + d * tau * Lam)
+    c = g ** steps
+    dc_dr = steps * g ** (steps - 1) * (-tau) / (1.0 + d * tau * Lam)
+    uu = float(np.sum(U0 * U0))
+    assert abs(J - (c - c0) ** 2 * uu) <= 1e-12 * J
+    assert abs(g_r - 2.0 * (c - c0) * dc_dr * uu) <= 1e-10 * abs(2.0 * (c - c0) * dc_dr * uu)
+    dc_dd = steps * g ** (steps - 1) * (1.0 - tau * r) * (-tau * Lam) / (1.0 + d * tau * Lam) ** 2
+    assert abs(g_du - 2.0 * (c - c0) * dc_dd * uu) <= 1e-10 * abs(2.0 * (c - c0) * dc_dd * uu)
+
+
+def test_source_reaction_recursion_reduces_to_the_plain_one():
+    ops = HeatOperators(G1, G2, 2, 9, 'neumann')
+    q = ops.q
+    rng = np.random.default_rng(4)
+    U0, T = rng.uniform(0, 1, (q, q)), rng.uniform(0, 1, (q, q))
+    st0 = imex_forward(ops, 0.05, 2e-2, U0, 4)
+    st1 = imex_forward_src(ops, 0.05, 2e-2, U0, 4, np.zeros((9, 9)), 0.0)
+    assert max(np.abs(a - b).max() for a, b in zip(st0, st1)) == 0.0
+    dJ = loss(st0[-1], T)[1]
+    g0 = imex_adjoint(ops, 0.05, 2e-2, st0, dJ)
+    g1 = imex_adjoint_src(ops, 0.05, 2e-2, 0.0, st1, dJ)
+    assert np.abs(g0[0] - g1[0]).max() <= 1e-14 * np.abs(g0[0]).max() and abs(g0[1] - g1[1]) <= 1e-14 * abs(g0[1])
+
+
+@pytest.mark.parametrize("k,n,bc", [(1, 9, "dirichlet"), (2, 9, "neumann"), (0, 8, "dirichlet")])
+def test_source_reaction_adjoint_equals_central_differences(k, n, bc):
+    d, tau, steps, r = 0.05, 2e-2, 6, 0.7
+    ops = HeatOperators(G1, G2, k, n, bc)
+    q = ops.q
+    rng = np.random.default_rng(7 * k + n)
+    U0, T = rng.uniform(0, 1, (q, q)), rng.uniform(0, 1, (q, q))
+    F = rng.standard_normal((n, n))
+
+    def J_of(U=U0, dd=d, FF=F, rr=r):
+        return loss(imex_forward_src(ops, dd, tau, U, steps, FF, rr)[-1], T)[0]
+
+    states = imex_forward_src(ops, d, tau, U0, steps, F, r)
+    dJ = loss(states[-1], T)[1]
+    gU, g_du, g_F, g_r = imex_adjoint_src(ops, d, tau, r, states, dJ)
+    for _ in range(2):   # J is quadratic in U_0 and in F: central differences exact up to rounding
+        V = rng.standard_normal((q, q))
+        fd = (J_of(U=U0 + 1e-3 * V) - J_of(U=U0 - 1e-3 * V)) / 2e-3
+        assert abs(fd - float(np.sum(gU * V))) <= 1e-8 * abs(fd) + 1e-12
+        W = rng.standard_normal((n, n))
+        fd = (J_of(FF=F + 1e-3 * W) - J_of(FF=F - 1e-3 * W)) / 2e-3
+        assert abs(fd - float(np.sum(g_F * W))) <= 1e-8 * abs(fd) + 1e-12
+    for name, val, g in (("d_u", d, g_du), ("r", r, g_r)):
+        eps = 1e-5 * val
+        if name == "d_u":
+            fd = (J_of(dd=d + eps) - J_of(dd=d - eps)) / (2 * eps)
+        else:
+            fd = (J_of(rr=r + eps) - J_of(rr=r - eps)) / (2 * eps)
+        assert abs(fd - g) <= 1e-6 * abs(fd), (name, fd, g)
