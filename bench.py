@@ -183,25 +183,31 @@ def measure_heat():
     def run(n_steps):
         U0 = torch.tensor(smoothed_uniform(q, 0)[None], device="cuda", requires_grad=True)
         du = torch.tensor(cfg["d_u"], dtype=torch.float64, device="cuda", requires_grad=True)
+        F = torch.zeros((1, q, q), dtype=torch.float64, device="cuda", requires_grad=True)   # Neumann: n = q
+        r = torch.tensor(0.0, dtype=torch.float64, device="cuda", requires_grad=True)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         torch.cuda.synchronize()
         ev[0].record()
-        UN = adj.heat_imex(U0, du, setup, n_steps, every)
+        UN = adj.heat_imex(U0, du, setup, n_steps, every, F=F, r=r)
         ev[1].record()
         ((UN - T) ** 2).sum().backward()
         ev[2].record()
         torch.cuda.synchronize()
-        return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), float(du.grad.item())
+        return (ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), float(du.grad.item()), float(r.grad.item()),
+                float(F.grad.norm().item()), float(U0.grad.norm().item()))
 
     run(10)   # warm-up
-    fwd, bwd, g = run(steps)
+    fwd, bwd, g, g_r, g_f, g_u0 = run(steps)
     setup.close()
     return {"workload": f"u_t - d_u Lap u = 0, P{cfg['k']} {q}x{q} nodes, Neumann, 0.1x^2<=y<=1+0.2cos(pi x), "
                         f"dt {cfg['tau']:g}, {steps} steps, d_u {cfg['d_u']:g}, checkpoints every {every}",
             "precision": "fp16-gemm/f32-vec/f64-refine, every solve to rel. residual 1e-11",
             "forward_ms": fwd, "backward_ms": bwd, "forward_steps_per_s": steps / (fwd / 1e3),
-            "backward_steps_per_s": steps / (bwd / 1e3), "dJ_ddu": g,
-            "check": "gradients vs central differences to 1e-5: tests/test_gpu_heat.py"}
+            "backward_steps_per_s": steps / (bwd / 1e3), "dJ_ddu": g, "dJ_dr": g_r, "norm_dJ_df": g_f,
+            "norm_dJ_dU0": g_u0,
+            "gradients": "U0, d_u, nodal source f and reaction r (at the workload's f = 0, r = 0)",
+            "check": "gradients vs central differences to 1e-5 and vs the FP64 oracle's adjoint: "
+                     "tests/test_gpu_heat.py"}
 
 
 def measure_dib(steps=300):

@@ -243,6 +243,34 @@ mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, con
                                      const double* U_np1, double* Lam_n, double* Y, double* dd_u, double rtol,
                                      mofem_precision prec, mofem_solve_info* info, cudaStream_t stream);
 
+/* One IMEX Euler step of u_t - d_u Lap u = f - r u with a nodal source f and a linear
+ * reaction -r u, both explicit as Sec. 6 treats the reaction term (Eqs.
+ * semilinear_heat_equation_fully_discrete_sylvester_pk and _R_pk with f(u) = f - r u):
+ *   (M~ + d_u tau A~) U_np1 = (1 - tau r) M~ U_n + tau M~_all F,
+ * M~_all F = M_s[h]_(int,all) F M_t_(int,all)^T.  F: n x n nodal per instance (ld n),
+ * FP64 device, constant in time; r: host scalar (r = 0: mofem_imex_step_tol).  The handle
+ * must have gamma = 1/(d_u tau).  Layouts and the stopping rule as mofem_imex_step_tol. */
+mofem_status mofem_imex_step_src(mofem_handle h, double d_u, double tau, double r, const double* U_n,
+                                 const double* F, double* U_np1, double rtol, mofem_precision prec,
+                                 mofem_solve_info* info, cudaStream_t stream);
+
+/* One backward step of the discrete adjoint of mofem_imex_step_src (no counterpart in
+ * the paper, which does not differentiate; derived from the step above by
+ * differentiating it in U_n, F, r and d_u):
+ *   Y = S^{-1} Lam_np1   (S = M~ + d_u tau A~ symmetric; the same MO-PCG solve),
+ *   Lam_n = (1 - tau r) M~ Y,
+ *   dF += tau M~_all^T Y = tau M_s[h] pad(Y) M_t^T   (n x n nodal, accumulated; pad puts
+ *                                                    zeros on Dirichlet boundary nodes),
+ *   dr[i] = -tau <Y, M~ U_n>_F,   dd_u[i] = -tau <Y, A~ U_np1>_F.
+ * Summed over the steps n = N-1 .. 0 these give dJ/dF, dJ/dr and dJ/dd_u of a loss
+ * J(U_N), and Lam_0 = dJ/dU_0.  U_n, U_np1: the forward states before and after step n.
+ * dF (device, may be NULL), dr and dd_u (host arrays of `batch` doubles; dr may be
+ * NULL, then U_n may be NULL).  Y as in mofem_imex_adjoint_step.  Synchronises. */
+mofem_status mofem_imex_adjoint_step_src(mofem_handle h, double d_u, double tau, double r, const double* Lam_np1,
+                                         const double* U_n, const double* U_np1, double* Lam_n, double* Y,
+                                         double* dF, double* dd_u, double* dr, double rtol, mofem_precision prec,
+                                         mofem_solve_info* info, cudaStream_t stream);
+
 /* One IMEX Euler step of a batch of reaction-diffusion species (Sec. 6 applied
  * to each species of a system such as Sec. 7's): instance i solves
  *   (M~ + d_i tau A~) U_np1 = M~ (U_n + tau F_n),  d_i = 1/(gamma_i tau),

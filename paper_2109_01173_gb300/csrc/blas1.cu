@@ -401,10 +401,11 @@ __global__ void k_init(InitArgs g) {
     }
 }
 
-// IMEX right-hand side in nodal form: Fbar = gam * (pad(U_n) + tau F_n), n x n
-// per instance; U_n is q x q (boundary nodes zero under Dirichlet).
+// IMEX right-hand side in nodal form: Fbar = gam * (cu pad(U_n) + tau F_n), n x n
+// per instance; U_n is q x q (boundary nodes zero under Dirichlet); cu = 1 - tau r
+// for an explicit linear reaction -r u.
 __global__ void k_imex_rhs(const double* Un, const double* Fn, double* Fbar, int n, int q, int off, double gam,
-                           double tau) {
+                           double tau, double cu) {
     const int inst = blockIdx.z, r = blockIdx.y;
     const double* fn = Fn + (size_t)inst * n * n + (size_t)r * n;
     double* fb = Fbar + (size_t)inst * n * n + (size_t)r * n;
@@ -413,7 +414,7 @@ __global__ void k_imex_rhs(const double* Un, const double* Fn, double* Fbar, int
         const int uc = cc - off;
         double u = 0.0;
         if (ur >= 0 && ur < q && uc >= 0 && uc < q) u = Un[(size_t)inst * q * q + (size_t)ur * q + uc];
-        fb[cc] = gam * (u + tau * fn[cc]);
+        fb[cc] = gam * (cu * u + tau * fn[cc]);
     }
 }
 
@@ -644,7 +645,25 @@ __global__ void k_scale_copy64(const double* src, long long s_bs, int s_ld, doub
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) b[c] = s * a[c];
 }
 
+// dst += a * src, rows x cols per instance (FP64).
+__global__ void k_axpy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld, int cols,
+                         double a) {
+    const int inst = blockIdx.z, r = blockIdx.y;
+    const double* x = src + (size_t)inst * s_bs + (size_t)r * s_ld;
+    double* y = dst + (size_t)inst * d_bs + (size_t)r * d_ld;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) y[c] += a * x[c];
+}
+
 }  // namespace
+
+mofem_status launch_axpy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld, int rows,
+                           int cols, int batch, double a, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || batch <= 0) return MOFEM_OK;
+    dim3 grid((cols + 255) / 256, rows, batch);
+    k_axpy64<<<grid, 256, 0, st>>>(src, s_bs, s_ld, dst, d_bs, d_ld, cols, a);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
 
 // ---------------------------------------------------------------------------
 mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo, void* R, const void* Q,
@@ -693,9 +712,9 @@ mofem_status launch_pcg_init(const mofem_ctx* c, const double* rr_partials, int 
 }
 
 mofem_status launch_imex_rhs(const double* Un, const double* Fn, double* Fbar, int n, int q, int off, double gam,
-                             double tau, int batch, cudaStream_t st) {
+                             double tau, double cu, int batch, cudaStream_t st) {
     dim3 grid((n + 255) / 256, n, batch);
-    k_imex_rhs<<<grid, 256, 0, st>>>(Un, Fn, Fbar, n, q, off, gam, tau);
+    k_imex_rhs<<<grid, 256, 0, st>>>(Un, Fn, Fbar, n, q, off, gam, tau, cu);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

@@ -176,7 +176,30 @@ mofem_status mofem_imex_adjoint_step(mofem_handle h, double d_u, double tau, con
         return MOFEM_ERR_INVALID_ARG;
     if (Y && (Y == Lam_np1 || Y == Lam_n || Y == U_np1)) return MOFEM_ERR_INVALID_ARG;
     if (!imex_gamma_ok(h, d_u, tau)) return MOFEM_ERR_INVALID_ARG;
-    return solve_imex_adjoint(h, d_u, tau, Lam_np1, U_np1, Lam_n, Y, dd_u, rtol, prec, info, stream);
+    return solve_imex_adjoint(h, d_u, tau, 0.0, Lam_np1, nullptr, U_np1, Lam_n, Y, nullptr, dd_u, nullptr, rtol, prec,
+                              info, stream);
+}
+
+mofem_status mofem_imex_step_src(mofem_handle h, double d_u, double tau, double r, const double* U_n, const double* F,
+                                 double* U_np1, double rtol, mofem_precision prec, mofem_solve_info* info,
+                                 cudaStream_t stream) {
+    if (!h || !U_n || !F || !U_np1 || !(d_u > 0.0) || !(tau > 0.0) || !(rtol >= 0.0) || !std::isfinite(r) ||
+        !valid_precision(prec))
+        return MOFEM_ERR_INVALID_ARG;
+    if (!imex_gamma_ok(h, d_u, tau)) return MOFEM_ERR_INVALID_ARG;
+    return solve_imex(h, d_u, tau, U_n, F, U_np1, rtol, prec, info, stream, 1.0 - tau * r);
+}
+
+mofem_status mofem_imex_adjoint_step_src(mofem_handle h, double d_u, double tau, double r, const double* Lam_np1,
+                                         const double* U_n, const double* U_np1, double* Lam_n, double* Y, double* dF,
+                                         double* dd_u, double* dr, double rtol, mofem_precision prec,
+                                         mofem_solve_info* info, cudaStream_t stream) {
+    if (!h || !Lam_np1 || !U_np1 || !Lam_n || !dd_u || !(d_u > 0.0) || !(tau > 0.0) || !(rtol > 0.0) ||
+        !std::isfinite(r) || !valid_precision(prec) || Lam_n == Lam_np1 || (dr && !U_n))
+        return MOFEM_ERR_INVALID_ARG;
+    if (Y && (Y == Lam_np1 || Y == Lam_n || Y == U_np1 || Y == U_n)) return MOFEM_ERR_INVALID_ARG;
+    if (!imex_gamma_ok(h, d_u, tau)) return MOFEM_ERR_INVALID_ARG;
+    return solve_imex_adjoint(h, d_u, tau, r, Lam_np1, U_n, U_np1, Lam_n, Y, dF, dd_u, dr, rtol, prec, info, stream);
 }
 
 mofem_status mofem_rds_step(mofem_handle h, double tau, const double* U_n, const double* F_n, double* U_np1,

@@ -85,6 +85,8 @@ struct mofem_ctx {
     int s2_row = 0;           // floats per S2dup row
     double* T64 = nullptr;  float* T32 = nullptr;   // [NT][P][q]
     double* Sr64 = nullptr; double* Tr64 = nullptr; // RHS mass factors: [batch][P][q], [P][q] (offset off)
+    double* Smf64 = nullptr; double* Tmf64 = nullptr; // untrimmed masses M_s[h], M_t: [batch][P][n], [P][n]
+                                                      // (T with its row sum in the diagonal slot)
 
     // preconditioner eigen data (FP64 masters)
     double* Q1_64 = nullptr;   // [batch][q][ld]  Q1 row-major (columns = eigenvectors)
@@ -270,13 +272,15 @@ mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs,
 mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rtol, int max_iter,
                             mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
 mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
-                        double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
+                        double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st, double cu = 1.0);
 mofem_status dib_run(mofem_ctx* c, const mofem_dib_params& p, double rho, double tau, int n_steps, double* U,
                      double rtol, mofem_precision prec, double* incr, mofem_solve_info* info, cudaStream_t st);
 mofem_status dib_equilibrium(const mofem_dib_params& p, double* eta, double* theta);
 mofem_status launch_dib_kinetics(const mofem_dib_params& p, double rho, const double* eta, const double* theta,
                                  double* f, double* g, long long n, cudaStream_t st);
-mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const double* Lam1, const double* U1,
-                                double* Lam0, double* Y, double* dd, double rtol, mofem_precision prec, mofem_solve_info* info,
-                                cudaStream_t st);
+mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, double r, const double* Lam1, const double* U0,
+                                const double* U1, double* Lam0, double* Y, double* dF, double* dd, double* dr, double rtol,
+                                mofem_precision prec, mofem_solve_info* info, cudaStream_t st);
+mofem_status launch_axpy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld, int rows,
+                           int cols, int batch, double a, cudaStream_t st);
 void mofem_free_extra(mofem_ctx* c);

@@ -192,6 +192,7 @@ mofem_status dev_alloc(T** p, size_t count) {
 struct HostTables {
     int NT = 5, K = 1, P = 3, q = 0, off = 1, nq = 0;
     std::vector<double> S, T, Srh, Trh;   // [B][NT][P][q], [NT][P][q], [B][P][q], [P][q]
+    std::vector<double> Smf, Tmf;         // untrimmed masses M_s[h], M_t: [B][P][n], [P][n]
     std::vector<Band> E1s, E2s;
     Band Mt, Kt;
     Band F1, F2;                          // t-pencil F2 Q2 = F1 Q2 diag(mu)
@@ -295,11 +296,15 @@ static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mo
     // RHS t-factor: rows = kept nodes, columns = all nodes
     H.Trh.assign((size_t)P * q, 0.0);
     trimmed_table(Mt, q, off, 0, n - 1, false, 1.0, H.Trh.data());
+    // untrimmed t-mass (rows and columns = all nodes): transpose of the right-hand side's map
+    H.Tmf.assign((size_t)P * n, 0.0);
+    trimmed_table(Mt, n, 0, 0, n - 1, false, 1.0, H.Tmf.data());
 
     // --- s-direction factors per instance ------------------------------------
     std::vector<double>& Sh = H.S;
     Sh.assign((size_t)B * NT * P * q, 0.0);
     H.Srh.assign((size_t)B * P * q, 0.0);
+    H.Smf.assign((size_t)B * P * n, 0.0);
     H.E1s.resize(B);
     H.E2s.resize(B);
     for (int i = 0; i < B; ++i) {
@@ -330,6 +335,7 @@ static mofem_status build_host_tables(int B, int k, int n, mofem_bc bc, const mo
             trimmed_table(Gdh, q, off, lo, hi, true, -1.0, sslot(7));
         }
         trimmed_table(Msh, q, off, 0, n - 1, false, 1.0, H.Srh.data() + (size_t)i * P * q);
+        trimmed_table(Msh, n, 0, 0, n - 1, false, 1.0, H.Smf.data() + (size_t)i * P * n);
         if (opts.pencil == MOFEM_PENCIL_PRODUCT || opts.pencil == MOFEM_PENCIL_AUA) {
             // K_s[h] Z F^T: standard eigenpairs on each side
             H.E1s[i] = Ksh;
@@ -477,6 +483,11 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
             if ((smask >> t) & 1u) rowsum_one(Sh.data() + ((size_t)i * c->NT + t) * c->P * q);
     for (int t = 0; t < c->NT; ++t) rowsum_one(Th.data() + (size_t)t * c->P * q);
     rowsum_one(Trh.data());
+    for (int r = 0; r < n; ++r) {   // untrimmed t-mass: row sum in the diagonal slot as well
+        double sum = 0.0;
+        for (int j = 0; j < c->P; ++j) sum += H.Tmf[(size_t)j * n + r];
+        H.Tmf[(size_t)c->K * n + r] = sum;
+    }
     std::vector<float> tmp;
     auto up64 = [&](double** d, const std::vector<double>& h) -> mofem_status {
         MOFEM_TRY(dev_alloc(d, h.size()));
@@ -494,6 +505,8 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
     MOFEM_TRY(up64(&c->T64, Th));
     MOFEM_TRY(up32(&c->T32, Th));
     MOFEM_TRY(up64(&c->Sr64, Srh));
+    MOFEM_TRY(up64(&c->Smf64, H.Smf));
+    MOFEM_TRY(up64(&c->Tmf64, H.Tmf));
     {   // FP32 S rows for the packed apply: [batch][q][W], coefficient e = t*P + j at 2e and 2e+1
         const int ntp = c->NT * c->P;
         const int W = apply_s2_row_floats(c->K, c->NT);
@@ -607,7 +620,7 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
 }
 
 void mofem_free(mofem_ctx* c) {
-    void* ptrs[] = {c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->Sdd, c->Tdd, c->Srdf, c->Trdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
+    void* ptrs[] = {c->Smf64, c->Tmf64, c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->Sdd, c->Tdd, c->Srdf, c->Trdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
                     c->lam32, c->mu32, c->w64, c->w32, c->Bm64, c->R64, c->d_part, c->d_sc, c->d_status,
                     c->d_red};
     for (void* p : ptrs) cudaFree(p);

@@ -42,7 +42,7 @@ mofem_status launch_dot_partials(const void* A, const void* B, bool fp64, long l
                                  double* part, int nblk, cudaStream_t st, PcgScalars* sc = nullptr,
                                  unsigned* counter = nullptr, int flex = 0);
 mofem_status launch_imex_rhs(const double* Un, const double* Fn, double* Fbar, int n, int q, int off, double gam,
-                             double tau, int batch, cudaStream_t st);
+                             double tau, double cu, int batch, cudaStream_t st);
 
 namespace {
 
@@ -760,15 +760,16 @@ mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rto
 }
 
 mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, const double* Fn, double* Unp1,
-                        double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st) {
+                        double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st, double cu) {
     MOFEM_TRY(ensure_common(c, st));
     double* Fbar = nullptr;
     const long long nn = (long long)c->n * c->n, qq0 = (long long)c->q * c->q;
     MOFEM_CUDA_TRY(cudaMallocAsync((void**)&Fbar, sizeof(double) * (size_t)nn * c->batch, st));
-    // nodal gamma_i (U_n + tau F_n) per instance (each instance its own diffusion d_i = 1/(gamma_i tau))
+    // nodal gamma_i (cu U_n + tau F_n) per instance (each instance its own diffusion d_i = 1/(gamma_i tau))
     mofem_status s = MOFEM_OK;
     for (int i = 0; i < c->batch && s == MOFEM_OK; ++i)
-        s = launch_imex_rhs(Un + qq0 * i, Fn + nn * i, Fbar + nn * i, c->n, c->q, c->off, c->gamma[i], tau, 1, st);
+        s = launch_imex_rhs(Un + qq0 * i, Fn + nn * i, Fbar + nn * i, c->n, c->q, c->off, c->gamma[i], tau, cu, 1,
+                            st);
     if (s == MOFEM_OK) s = op_rhs(c, Fbar, c->Bm64, (long long)per(c), c->ld, st);
     cudaFreeAsync(Fbar, st);
     MOFEM_TRY(s);
@@ -783,19 +784,24 @@ mofem_status solve_imex(mofem_ctx* c, double d_u, double tau, const double* Un, 
     return r;
 }
 
-// One backward step of IMEX Euler with f = 0 (discrete adjoint of solve_imex):
-// S = M~ + d_u tau A~ = d_u tau L with L the handle's operator (gamma = 1/(d_u tau)),
-//   Y = S^{-1} Lam_np1,  Lam_n = M~ Y,  dd[i] = -tau <Y, A~ U_np1> = -tau (<Y, L U> - gamma <Y, M~ U>).
-mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const double* Lam1, const double* U1,
-                                double* Lam0, double* Y_io, double* dd, double rtol, mofem_precision prec,
-                                mofem_solve_info* info, cudaStream_t st) {
+// One backward step of the discrete adjoint of solve_imex with a nodal source F and an
+// explicit linear reaction -r u:  S U_np1 = (1 - tau r) M~ U_n + tau M~_all F,
+// S = M~ + d_u tau A~ = d_u tau L with L the handle's operator (gamma = 1/(d_u tau)):
+//   Y = S^{-1} Lam_np1,  Lam_n = (1 - tau r) M~ Y,  dF += tau M~_all^T Y,
+//   dr[i] = -tau <Y, M~ U_n>,  dd[i] = -tau <Y, A~ U_np1> = -tau (<Y, L U_np1> - gamma <Y, M~ U_np1>).
+// M~_all^T Y = M_s pad(Y) M_t^T with the untrimmed masses (pad: zero boundary rows and columns).
+mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, double r, const double* Lam1, const double* U0,
+                                const double* U1, double* Lam0, double* Y_io, double* dF, double* dd, double* dr,
+                                double rtol, mofem_precision prec, mofem_solve_info* info, cudaStream_t st) {
     MOFEM_TRY(ensure_common(c, st));
     Extra& e = extras()[c];
-    const int q = c->q, B = c->batch;
-    const long long qq = (long long)q * q;
+    const int q = c->q, B = c->batch, n = c->n;
+    const long long qq = (long long)q * q, nn = (long long)n * n;
     double* buf = nullptr;
-    MOFEM_CUDA_TRY(cudaMallocAsync((void**)&buf, sizeof(double) * (size_t)qq * B * 3, st));
+    const size_t nbuf = (size_t)qq * B * 3 + (dF ? (size_t)nn * B * 2 : 0);
+    MOFEM_CUDA_TRY(cudaMallocAsync((void**)&buf, sizeof(double) * nbuf, st));
     double *Y = Y_io ? Y_io : buf, *LU = buf + qq * B, *MU = buf + 2 * qq * B;
+    double *Ypad = buf + 3 * qq * B, *G = Ypad + nn * B;
     mofem_status s = launch_scale_copy64(Lam1, qq, q, c->Bm64, (long long)per(c), c->ld, q, q, B, 1.0 / (d_u * tau), st);
     if (s == MOFEM_OK && !Y_io)   // no guess: start from zero
         s = cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)qq * B, st) == cudaSuccess ? MOFEM_OK : MOFEM_ERR_CUDA;
@@ -804,22 +810,54 @@ mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, const doub
         solve = solve_core(c, Y, qq, q, rtol, 100000, prec, 0, info, st);
         if (solve != MOFEM_OK && solve != MOFEM_ERR_NOT_CONVERGED) s = solve;
     }
+    long long launches = 6;
     if (s == MOFEM_OK) s = op_mass(c, Y, qq, q, Lam0, qq, q, st);
+    if (s == MOFEM_OK && r != 0.0) {
+        s = launch_scale_copy64(Lam0, qq, q, Lam0, qq, q, q, q, B, 1.0 - tau * r, st);
+        launches += 1;
+    }
     if (s == MOFEM_OK) s = op_apply(c, true, U1, qq, q, LU, qq, q, nullptr, st);
     if (s == MOFEM_OK) s = op_mass(c, U1, qq, q, MU, qq, q, st);
-    std::vector<double> yl, ym;
-    std::vector<double> both;   // <Y, L U> and <Y, M~ U>, read back with one synchronisation
+    std::vector<double> both;   // <Y, L U_np1>, <Y, M~ U_np1> [, <Y, M~ U_n>], read back with one synchronisation
+    const int nd = dr ? 3 : 2;
     if (s == MOFEM_OK) s = launch_dot_partials(Y, LU, true, qq, qq, B, e.bb_part, c->part.n_rz, st);
     if (s == MOFEM_OK) s = launch_dot_partials(Y, MU, true, qq, qq, B, e.bb_part + (size_t)B * c->part.n_rz, c->part.n_rz, st);
-    if (s == MOFEM_OK) s = sum_partials(e.bb_part, c->part.n_rz, 2 * B, both, st);
-    if (s == MOFEM_OK) {
-        yl.assign(both.begin(), both.begin() + B);
-        ym.assign(both.begin() + B, both.end());
+    if (s == MOFEM_OK && dr) {
+        // the third product needs its own partial slice: reuse LU's storage once <Y, L U> is summed
+        s = sum_partials(e.bb_part, c->part.n_rz, 2 * B, both, st);
+        if (s == MOFEM_OK) s = op_mass(c, U0, qq, q, MU, qq, q, st);
+        if (s == MOFEM_OK) s = launch_dot_partials(Y, MU, true, qq, qq, B, e.bb_part, c->part.n_rz, st);
+        std::vector<double> third;
+        if (s == MOFEM_OK) s = sum_partials(e.bb_part, c->part.n_rz, B, third, st);
+        if (s == MOFEM_OK) both.insert(both.end(), third.begin(), third.end());
+        launches += 2;
+    } else if (s == MOFEM_OK) {
+        s = sum_partials(e.bb_part, c->part.n_rz, 2 * B, both, st);
+    }
+    if (s == MOFEM_OK && dF) {
+        // dF += tau M_s pad(Y) M_t^T (untrimmed masses; the generic apply with one mass term)
+        s = cudaMemsetAsync(Ypad, 0, sizeof(double) * (size_t)nn * B, st) == cudaSuccess ? MOFEM_OK : MOFEM_ERR_CUDA;
+        if (s == MOFEM_OK)
+            s = launch_convert(Y, 1, qq, q, Ypad + (size_t)c->off * n + c->off, 1, nn, n, q, q, B, st);
+        if (s == MOFEM_OK) {
+            ApplyArgs a{};
+            a.X = Ypad; a.x_bs = nn; a.x_ld = n;
+            a.Y = G; a.y_bs = nn; a.y_ld = n;
+            a.S = c->Smf64; a.s_bs = (long long)c->P * n; a.T = c->Tmf64;
+            a.rows_in = a.cols_in = a.rows_out = a.cols_out = n;
+            a.off = 0;
+            s = launch_apply(c->K, 1, true, APPLY_PLAIN, a, B, st);
+        }
+        if (s == MOFEM_OK) s = launch_axpy64(G, nn, n, dF, nn, n, n, n, B, tau, st);
+        launches += 3;
     }
     cudaFreeAsync(buf, st);
     MOFEM_TRY(s);
-    for (int i = 0; i < B; ++i) dd[i] = -tau * (yl[i] - c->gamma[i] * ym[i]);
-    if (info) info->kernel_launches += 6;
+    for (int i = 0; i < B; ++i) {
+        dd[i] = -tau * (both[i] - c->gamma[i] * both[B + i]);
+        if (dr) dr[i] = -tau * both[2 * B + i];
+    }
+    if (info) info->kernel_launches += launches;
     return solve;
 }
 

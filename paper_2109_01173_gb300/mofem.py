@@ -92,6 +92,9 @@ def _load():
         "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
                                     vp],
         "mofem_get_eigen": [vp, vp, vp, vp, vp, P(c_int), vp],
+        "mofem_imex_step_src": [vp, c_double, c_double, c_double, vp, vp, vp, c_double, c_int, P(SolveInfo), vp],
+        "mofem_imex_adjoint_step_src": [vp, c_double, c_double, c_double, vp, vp, vp, vp, vp, vp, P(c_double),
+                                        P(c_double), c_double, c_int, P(SolveInfo), vp],
         "mofem_destroy": [vp],
         "mofem_bench_kernel": [vp, c_int, c_int, c_int, vp],
         "mofem_host_tables": [P(Profile), P(Profile), c_int, c_int, c_double, c_int, P(Opts), P(c_int), P(c_int),
@@ -116,7 +119,8 @@ EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply
             "mofem_dib_kinetics", "mofem_dib_run", "mofem_dib_equilibrium", "mofem_group_layout",
             "mofem_group_setup", "mofem_group_solve", "mofem_group_autotune", "mofem_group_destroy",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
-            "mofem_host_tables", "mofem_host_dd_tables", "mofem_bench_kernel", "mofem_get_eigen"]
+            "mofem_host_tables", "mofem_host_dd_tables", "mofem_bench_kernel", "mofem_get_eigen",
+            "mofem_imex_step_src", "mofem_imex_adjoint_step_src"]
 
 
 def _check(fn, code):
@@ -280,6 +284,30 @@ class Handle:
         if check:
             _check("mofem_imex_adjoint_step", code)
         return list(dd), info, code
+
+    def imex_step_src(self, d_u, tau, r, Un, F, Unp1, rtol, precision="fp16", check=True):
+        """U_np1 from (M~ + d_u tau A~) U_np1 = (1 - tau r) M~ U_n + tau M~_all F."""
+        info = SolveInfo()
+        code = LIB.mofem_imex_step_src(self.h, d_u, tau, r, _ptr(Un), _ptr(F), _ptr(Unp1), rtol,
+                                       PRECISIONS[precision], ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_imex_step_src", code)
+        return info, code
+
+    def imex_adjoint_step_src(self, d_u, tau, r, Lam1, U0, U1, Lam0, rtol, dF=None, precision="fp16", check=True,
+                              Y=None):
+        """Lam0 = (1 - tau r) M~ S^{-1} Lam1, dF += tau M~_all^T S^{-1} Lam1 (if given); returns
+        (dJ/dd_u and dJ/dr contributions per instance, info, code)."""
+        dd = (ctypes.c_double * self.batch)()
+        dr = (ctypes.c_double * self.batch)()
+        info = SolveInfo()
+        code = LIB.mofem_imex_adjoint_step_src(self.h, d_u, tau, r, _ptr(Lam1), _ptr(U0), _ptr(U1), _ptr(Lam0),
+                                               _ptr(Y) if Y is not None else None,
+                                               _ptr(dF) if dF is not None else None, dd, dr, rtol,
+                                               PRECISIONS[precision], ctypes.byref(info), _stream())
+        if check:
+            _check("mofem_imex_adjoint_step_src", code)
+        return list(dd), list(dr), info, code
 
     def rds_step(self, tau, Un, Fn, Unp1, rtol=0.0, precision="fp16", check=True):
         info = SolveInfo()
