@@ -313,9 +313,16 @@ mofem_status mofem_dib_run(mofem_handle h, const mofem_dib_params* p, double rho
 /* ---- heterogeneous batches ------------------------------------------------
  * Many independent elliptic problems of different (k, n, bc, profiles, gamma)
  * solved together: problems of equal (k, n, bc) form one batched handle (as
- * mofem_setup_batched); the groups are solved concurrently, one CUDA stream each,
- * from host threads.  No counterpart in the paper (it solves one problem at a
- * time); the arithmetic per problem is that of mofem_pcg_solve. */
+ * mofem_setup_batched).  Two ways to run the groups:
+ *  - lockstep (the default for the mixed forms): every group's inner MO-PCG runs in
+ *    one CUDA graph whose conditional loop body holds, per iteration, each group's
+ *    operator apply and update (side by side, one graph branch per group) and ONE
+ *    persistent tensor-core launch with the preconditioner GEMMs of all groups (any
+ *    q); the refinement steps are taken together;
+ *  - apart: each group one batched solve on its own stream from a host thread, a
+ *    chosen number of groups in flight (the FP64 form always runs this way).
+ * No counterpart in the paper (it solves one problem at a time); the arithmetic per
+ * problem is that of mofem_pcg_solve, and both ways give the same bits. */
 typedef struct {
     mofem_profile g1, g2;   /* host callbacks, used during setup only */
     int k, n_nodes;
@@ -342,12 +349,18 @@ mofem_status mofem_group_setup(int count, const mofem_problem* problems, const m
 mofem_status mofem_group_solve(mofem_group g, const double* const* F, double* const* U, double rtol,
                                int max_iter, mofem_precision prec, mofem_solve_info* infos, cudaStream_t stream);
 
-/* Run-time tuning of the number of groups solved at once: one warm-up solve, then
- * one timed solve per candidate (1, 2, 4, 8, 16 groups, all), each from the
- * caller's initial guesses; the fastest is kept for later solves and written to
- * *chosen (may be NULL).  U holds the caller's initial guesses again on return. */
+/* Run-time tuning of how the groups run: one warm-up solve of each way, then one
+ * timed solve per candidate (lockstep for the mixed forms; apart with 1, 2, 4, 8,
+ * 16 or all groups in flight), each from the caller's initial guesses; the fastest
+ * is kept for later solves and written to *chosen (may be NULL): -1 lockstep, else
+ * the number of groups in flight.  U holds the caller's initial guesses again on
+ * return. */
 mofem_status mofem_group_autotune(mofem_group g, const double* const* F, double* const* U, double rtol,
                                   int max_iter, mofem_precision prec, int* chosen);
+
+/* Choose how later solves run: -1 lockstep (the default), 0 apart with all groups in
+ * flight, m > 0 apart with m groups in flight. */
+mofem_status mofem_group_set_mode(mofem_group g, int mode);
 
 mofem_status mofem_group_destroy(mofem_group g);
 

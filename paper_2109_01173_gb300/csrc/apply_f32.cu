@@ -49,7 +49,7 @@ static mofem_status pcg_f32(const CUtensorMap& mZ, const CUtensorMap& mQ, const 
                            const ApplyPcgArgs& a, int batch, cudaStream_t st) {
     if constexpr (packed_apply_ok(K, NT)) {
         if (!mS) return MOFEM_ERR_INVALID_ARG;
-        return launch_pcg2_t<K, NT>(mZ, mQ, *mS, a, batch, st);
+        return launch_pcg3_t<K, NT>(mZ, mQ, *mS, a, batch, st);
     } else {
         return launch_pcg_t<float, K, NT, false>(mZ, mQ, a, batch, st);
     }
@@ -77,20 +77,10 @@ mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, c
 
 bool apply_pcg_packed(int K, int nt, bool fp64) { return !fp64 && packed_apply_ok(K, nt); }
 
-template <int K>
-static int geo2_rows(int nt) {
-    return nt == 5 ? Geo2<K, 5>::TA : Geo2<K, 8>::TA;
-}
-
+// Rows per CTA of the tiled PCG-form apply (FP64 and the wide FP32 forms).
 int apply_pcg_rows_per_cta(int K, int nt, bool fp64) {
-    if (apply_pcg_packed(K, nt, fp64)) {
-        switch (K) {
-            case 1: return geo2_rows<1>(nt);
-            case 2: return geo2_rows<2>(nt);
-            case 3: return geo2_rows<3>(nt);
-            default: return geo2_rows<4>(nt);
-        }
-    }
+    (void)nt;
+    (void)fp64;
     switch (K) {
         case 1: return Geo<1>::TA_T;
         case 2: return Geo<2>::TA_T;
@@ -99,9 +89,42 @@ int apply_pcg_rows_per_cta(int K, int nt, bool fp64) {
     }
 }
 
+// Rows of one TMA box of Z / Q_prev: a staged chunk of the streaming apply, or the tile
+// with its K-row halo of the tiled one.
 int apply_pcg_box_rows(int K, int nt, bool fp64) {
-    return apply_pcg_rows_per_cta(K, nt, fp64) + 2 * K;   // the tile and its K-row halo, one box
+    if (apply_pcg_packed(K, nt, fp64)) return Geo3<2, 5>::CR;
+    return apply_pcg_rows_per_cta(K, nt, fp64) + 2 * K;
 }
 
-// 2 * SR2 of Geo2: the duplicated S row, an even number of float2 (16-byte rows)
-int apply_s2_row_floats(int K, int nt) { return 2 * (((nt * (2 * K + 1) + 1) / 2) * 2); }
+// Rows of one TMA box of the duplicated S rows (streaming apply).
+int apply_pcg_s_box_rows() { return Geo3<2, 5>::CR; }
+
+// 2 * SR2 of Geo3: the duplicated S row, a multiple of 4 float2 (32-byte rows)
+int apply_s2_row_floats(int K, int nt) { return 2 * (((nt * (2 * K + 1) + 3) / 4) * 4); }
+
+template <int K>
+static int ctas_k(int nt) {
+    if constexpr (packed_apply_ok(K, 8)) {
+        if (nt == 8) return apply3_ctas_wanted_t<K, 8>();
+    }
+    if constexpr (packed_apply_ok(K, 5)) return apply3_ctas_wanted_t<K, 5>();
+    return 1;
+}
+
+// CTAs per instance of the PCG-form apply of (K, nt, precision) at size q and batch: the
+// number of per-CTA partials each launch writes.
+int apply_pcg_ctas_per_instance(int K, int nt, bool fp64, int q, int batch) {
+    const int strips = (q + TB - 1) / TB;
+    if (!apply_pcg_packed(K, nt, fp64)) {
+        const int TA = apply_pcg_rows_per_cta(K, nt, fp64);
+        return strips * ((q + TA - 1) / TA);
+    }
+    int want = 1;
+    switch (K) {
+        case 1: want = ctas_k<1>(nt); break;
+        case 2: want = ctas_k<2>(nt); break;
+        case 3: want = ctas_k<3>(nt); break;
+        default: want = ctas_k<4>(nt); break;
+    }
+    return strips * apply3_segments(q, strips, batch, want, K);
+}

@@ -1,23 +1,27 @@
 // Packed-FP32 PCG form of the banded multiterm operator apply (Sec. 5, operator
 // L~ of the multiterm Sylvester equation), the FP32 operator of the mixed inner
 // solve.  Same arithmetic as compute_tile<float> (difference form, exact mass
-// split of term 0), restructured for the sm_100-family paired FP32 pipe:
+// split of term 0), restructured for the sm_100-family paired FP32 pipe and for
+// streaming:
 //
 //   * each thread owns two adjacent columns b, b+1 and every product, sum and
 //     fused multiply-add acts on the pair at once (one f32x2 instruction per two
 //     results), which halves the instruction count of the t- and s-passes;
-//   * the CTA is 128 columns x TA rows, 128 threads = 64 column pairs x 2 row
-//     groups; each group streams down its own TA/2 output rows with a register
-//     ring of the last 2K+1 t-pass rows (compile-time slots after unrolling);
-//   * Z and Q_prev arrive by TMA as one box each (the tile with its K-row halo)
-//     together with the tile's S rows, all on one mbarrier waited once (a
-//     per-row wait on 4-row chunks measured 4% slower: overlap between the 3
-//     resident CTAs of an SM hides the load better than overlap within one); the
-//     search direction X = Z + beta Q_prev is formed on the fly from both staged
-//     tiles and the owned rows of the new direction are written from registers;
-//   * the s-pass coefficients arrive by TMA as well, from a copy of the S tables
-//     laid out per row with every coefficient duplicated into both lanes of a
-//     float2, so a shared-memory broadcast feeds a paired FMA directly.
+//   * a CTA is 64 threads = 64 column pairs (a strip of 128 columns) and streams
+//     down a long segment of rows of one instance (grid: strips x segments x
+//     instances, sized to one wave of resident CTAs), with a register ring of the
+//     last 2K+1 t-pass rows (compile-time slots after unrolling by 2K+1): the
+//     T coefficients are loaded once per segment and only 2K halo rows per
+//     segment are recomputed;
+//   * Z, Q_prev and the segment's S rows arrive by TMA in chunks of CR rows into a
+//     ring of D chunks (one mbarrier per slot, bounded waits); a chunk slot is
+//     refilled CR * D rows ahead once every thread has passed its last row, so the
+//     loads overlap the arithmetic of the rows before them; the search direction
+//     X = Z + beta Q_prev is formed on the fly from both staged rows and the owned
+//     rows of the new direction are written from registers;
+//   * the s-pass coefficients come from a copy of the S tables laid out per row
+//     with every coefficient duplicated into both lanes of a float2, so a
+//     shared-memory broadcast feeds a paired FMA directly.
 //
 // Fused epilogue: per-CTA FP64 partials of <X, L(X)> and <L(X), Z> and, in the
 // last CTA of each instance, alpha = <R, Z> / <Q, L(Q)> and the flexible-beta
@@ -28,30 +32,29 @@
 
 namespace mofem_apply_impl {
 
-#ifndef MOFEM_APPLY_ROWS
-#define MOFEM_APPLY_ROWS 20   // target output rows per row group (rounded up to whole ring periods)
-#endif
-#ifndef MOFEM_APPLY_MINB
-#define MOFEM_APPLY_MINB 3    // resident CTAs per SM the register budget is sized for
-#endif
-
 template <int K, int NT>
-struct Geo2 {
+struct Geo3 {
     static constexpr int P = 2 * K + 1;
-    static constexpr int NPAIR = TB / 2;                 // column pairs per CTA
-    static constexpr int RG = 2;                         // row groups
-    static constexpr int NTH = NPAIR * RG;               // threads per CTA
-    static constexpr int MRG = (MOFEM_APPLY_ROWS + P - 1) / P;   // ring periods per group
-    static constexpr int TAG = MRG * P;                  // output rows per group
-    static constexpr int TA = RG * TAG;                  // output rows per CTA
-    static constexpr int HR = TA + 2 * K;                // staged rows
-    static constexpr int ROWS = (HR + 3) / 4 * 4;        // staging rows (4 x 544 B: 128-byte multiple)
-    static constexpr int ZBUF = ROWS * WCT;              // floats per staging buffer
-    static constexpr int SR2 = ((NT * P + 1) / 2) * 2;   // float2 per duplicated S row (16-byte rows)
+    static constexpr int NTH = 64;                       // threads = column pairs per CTA
+    static constexpr int CR = 4;                         // rows per staged chunk
+    static constexpr int D = 4;                          // chunks in the ring
+    static constexpr int RING = CR * D;                  // staged rows (power of two)
+    static constexpr int SR2 = ((NT * P + 3) / 4) * 4;   // float2 per duplicated S row (a chunk of S rows
+                                                         // stays a 128-byte multiple)
     static constexpr bool TREG = NT * P <= 25;           // T coefficients in registers, else shared
     static constexpr int KE = K + (K & 1);               // left reach rounded to an even column
-    static constexpr size_t SMEM = (size_t)2 * ZBUF * 4 + (size_t)TA * SR2 * 8 +
-                                   (TREG ? 0 : (size_t)NT * P * NPAIR * 8) + 128;
+    static constexpr int ZCH = CR * WCT;                 // floats per chunk of Z (and of Q_prev)
+    static constexpr int SCH = CR * SR2;                 // float2 per chunk of S rows
+    static constexpr uint32_t CHUNK_BYTES = 2u * ZCH * 4u + (uint32_t)SCH * 8u;
+    static constexpr size_t SMEM = (size_t)D * CHUNK_BYTES + (TREG ? 0 : (size_t)NT * P * NTH * 8) + 128;
+    // register budget: 6 resident CTAs (168 registers) with T in registers; with T in shared
+    // memory the staging caps residency lower, which leaves room for the longer ring
+    static constexpr int MINB = TREG ? 6 : 4;
+    static_assert((RING & (RING - 1)) == 0, "ring rows must be a power of two");
+    static_assert((ZCH * 4) % 128 == 0 && (SCH * 8) % 128 == 0, "TMA destinations stay 128-byte aligned");
+    // a chunk is refilled only after its last row is done; the rows that wait for it must
+    // not be the ones that release it: (D - 1) CR >= 2K (t-pass reach) + 2K (unrolled block)
+    static_assert((D - 1) * CR >= 4 * K, "ring too short for the stencil reach");
 };
 
 // Operator forms served by the packed kernel (the ring and, if TREG, the T
@@ -64,57 +67,79 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(
 // a - c, one rounding (fma with an exact -1 product)
 __device__ __forceinline__ float2 f2sub(float2 a, float2 c) { return __ffma2_rn(c, make_float2(-1.f, -1.f), a); }
 
+// Rows of one segment and the number of segments per strip: at most one wave of resident
+// CTAs over all strips and instances (a partial second wave would double the time of the
+// SMs that run it), at least 8 (2K + 8) rows per segment.
+__host__ __device__ inline int apply3_segments(int q, int strips, int batch, int ctas_wanted, int K) {
+    const int min_rows = 8 * (2 * K + 8);
+    int segs = ctas_wanted / (strips * batch);
+    const int max_segs = (q + min_rows - 1) / min_rows;
+    if (segs > max_segs) segs = max_segs;
+    return segs < 1 ? 1 : segs;
+}
+
 template <int K, int NT>
-__global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
-    k_apply_pcg2(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mQ,
-                 const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a) {
-    using G = Geo2<K, NT>;
-    constexpr int P = G::P, TAG = G::TAG, TA = G::TA, HR = G::HR, SR2 = G::SR2, KE = G::KE;
-    constexpr int NPAIR = G::NPAIR, MRG = G::MRG;
+__global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
+    k_apply_pcg3(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mQ,
+                 const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a, int seg_rows) {
+    using G = Geo3<K, NT>;
+    constexpr int P = G::P, SR2 = G::SR2, KE = G::KE, CR = G::CR, D = G::D, RING = G::RING, NTH = G::NTH;
     constexpr unsigned DM = DiffMask<NT>::value;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sbase =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-    float* Zs = reinterpret_cast<float*>(sbase);               // [ROWS][WCT]
-    float* Qs = Zs + G::ZBUF;                                   // [ROWS][WCT]
-    float2* S2s = reinterpret_cast<float2*>(Qs + G::ZBUF);      // [TA][SR2]
-    float2* T2s = S2s + TA * SR2;                               // [NT*P][NPAIR] (!TREG)
-    __shared__ __align__(8) unsigned long long bar;
-    __shared__ double red[G::NTH / 32];
+    float* Zs = reinterpret_cast<float*>(sbase);               // [RING][WCT]
+    float* Qs = Zs + RING * WCT;                                // [RING][WCT]
+    float2* S2s = reinterpret_cast<float2*>(Qs + RING * WCT);   // [RING][SR2]
+    float2* T2s = S2s + RING * SR2;                             // [NT*P][NTH] (!TREG)
+    __shared__ __align__(8) unsigned long long bar[D];
+    __shared__ double red[NTH / 32];
     __shared__ float beta_s;
     __shared__ int fail_s, last_s;
     const int tid = threadIdx.x, inst = blockIdx.z;
     PcgScalars* sc = a.sc + inst;
     if (a.use_sc && !sc->active) return;
-    const int a0 = blockIdx.y * TA, b0 = blockIdx.x * TB;
-    const uint32_t bar0 = smem_u32(&bar);
+    const int b0 = blockIdx.x * TB;
+    const int a_lo = blockIdx.y * seg_rows;
+    const int L = max(0, min(a.q, a_lo + seg_rows) - a_lo);   // output rows of this segment
+    // rows are computed in whole blocks of P (straight-line code, stores guarded): the
+    // last block may run past L into zero-filled or neighbouring rows, never stored
+    const int nblk_rows = (L + P - 1) / P;
+    const int LP = nblk_rows * P;
+    const int nch = (LP + 2 * K + CR - 1) / CR;                 // chunks of input rows a_lo - K ...
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        for (int i = 0; i < D; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail_s = 0;
         beta_s = (a.use_sc && sc->iters > 0) ? (float)sc->beta : 0.f;
     }
     __syncthreads();
-    if (tid == 0) {
+    // chunk c -> ring slot c % D: input rows a_lo - K + c CR .. (Z, Q_prev) and S rows a_lo + c CR ..
+    auto issue = [&](int c) {
+        const int slot = c % D;
+        const uint32_t b = smem_u32(&bar[slot]);
         const uint64_t pz = reinterpret_cast<uint64_t>(&mZ), pq = reinterpret_cast<uint64_t>(&mQ),
                        ps = reinterpret_cast<uint64_t>(&mS);
-        const int x0 = b0 - XPAD, y0 = a0 - K;
-        const uint32_t bytes = 2u * HR * WCT * 4u + (uint32_t)(TA * SR2 * 8);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar0), "r"(bytes) : "memory");
+        const int x0 = b0 - XPAD, y0 = a_lo - K + c * CR;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(G::CHUNK_BYTES)
+                     : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(S2s)), "l"(ps), "r"(bar0), "r"(0), "r"(a0), "r"(inst)
+            ::"r"(smem_u32(S2s + slot * G::SCH)), "l"(ps), "r"(b), "r"(0), "r"(a_lo + c * CR), "r"(inst)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(Zs)), "l"(pz), "r"(bar0), "r"(x0), "r"(y0), "r"(inst)
+            ::"r"(smem_u32(Zs + slot * G::ZCH)), "l"(pz), "r"(b), "r"(x0), "r"(y0), "r"(inst)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(Qs)), "l"(pq), "r"(bar0), "r"(x0), "r"(y0), "r"(inst)
+            ::"r"(smem_u32(Qs + slot * G::ZCH)), "l"(pq), "r"(b), "r"(x0), "r"(y0), "r"(inst)
             : "memory");
-    }
-    const int cp = tid % NPAIR, grp = tid / NPAIR;
+    };
+    if (tid == 0)
+        for (int c = 0; c < D && c < nch; ++c) issue(c);
+    const int cp = tid;
     const int b = b0 + 2 * cp;
     const float* Tt = reinterpret_cast<const float*>(a.T);
     auto tload = [&](int il) -> float2 {
@@ -128,8 +153,8 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
 #pragma unroll
             for (int l = 0; l < P; ++l) tc[i][l] = tload(i * P + l);
     } else {
-        for (int idx = tid; idx < NT * P * NPAIR; idx += G::NTH) {
-            const int il = idx / NPAIR, c = idx - il * NPAIR;
+        for (int idx = tid; idx < NT * P * NTH; idx += NTH) {
+            const int il = idx / NTH, c = idx - il * NTH;
             const int bb = b0 + 2 * c;
             const size_t o = (size_t)il * a.q + bb;
             T2s[idx] = make_float2(bb < a.q ? Tt[o] : 0.f, bb + 1 < a.q ? Tt[o + 1] : 0.f);
@@ -138,7 +163,7 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     }
     auto tcoef = [&](int i, int l) -> float2 {
         if constexpr (G::TREG) return tc[i][l];
-        else return T2s[(i * P + l) * NPAIR + cp];
+        else return T2s[(i * P + l) * NTH + cp];
     };
     // Term 0 exact mass split: X M_t^T = D (X + X N^T), N = D^{-1}(M_t - D) (zero row sums).
     const float2 d0 = tcoef(0, K);
@@ -153,13 +178,21 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     float* Qn = reinterpret_cast<float*>(a.Qnew) + (size_t)inst * a.bs;
     float* LQ = reinterpret_cast<float*>(a.LQ) + (size_t)inst * a.bs;
     const bool col_ok = b < a.ld;   // pad columns [q, ld) receive zeros
-    const int lr0 = grp * TAG;      // first staged row of this group's window
-    const bool failed = !mbar_wait_bounded(bar0, 0);   // the whole tile, its halo and the S rows
+    bool failed = false;
+    int waited = 0, released = 0;
+    auto wait_upto = [&](int need) {   // chunks 0 .. need-1 resident
+        while (waited < need) {
+            if (!failed) failed = !mbar_wait_bounded(smem_u32(&bar[waited % D]), (uint32_t)((waited / D) & 1));
+            ++waited;
+        }
+    };
     float2 ring[NT][P];
     float2 xr0[P];
-    auto tpass = [&](int lr, int slot) {
-        const float2* z2 = reinterpret_cast<const float2*>(Zs + lr * WCT + XPAD + 2 * cp - KE);
-        const float2* q2 = reinterpret_cast<const float2*>(Qs + lr * WCT + XPAD + 2 * cp - KE);
+    // t-pass of input index i (input row a_lo - K + i) into ring slot `slot`
+    auto tpass = [&](int i, int slot) {
+        const int rr = (i & (RING - 1)) * WCT + XPAD + 2 * cp - KE;
+        const float2* z2 = reinterpret_cast<const float2*>(Zs + rr);
+        const float2* q2 = reinterpret_cast<const float2*>(Qs + rr);
         float xs[2 * KE + 2];
 #pragma unroll
         for (int m = 0; m <= KE; ++m) {
@@ -169,11 +202,9 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
         }
         const float2 xc = make_float2(xs[KE], xs[KE + 1]);
         xr0[slot] = xc;
-        const int orow = lr - K - lr0;   // group-local output row whose centre this is
-        if (orow >= 0 && orow < TAG) {
-            const int gr = a0 + lr - K;
-            if (gr < a.q && col_ok) *reinterpret_cast<float2*>(Qn + (size_t)gr * a.ld + b) = xc;
-        }
+        const int orow = i - K;   // segment output row whose centre this is
+        if (orow >= 0 && orow < L && col_ok)
+            *reinterpret_cast<float2*>(Qn + (size_t)(a_lo + orow) * a.ld + b) = xc;
         float2 d[P];
 #pragma unroll
         for (int l = 0; l < P; ++l)
@@ -186,71 +217,88 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
             ring[0][slot] = w;
         }
 #pragma unroll
-        for (int i = 1; i < NT; ++i) {
-            float2 w = f2mul(tcoef(i, K), xc);
+        for (int t = 1; t < NT; ++t) {
+            float2 w = f2mul(tcoef(t, K), xc);
 #pragma unroll
             for (int l = 0; l < P; ++l)
-                if (l != K) w = f2fma(tcoef(i, l), d[l], w);
-            ring[i][slot] = w;
+                if (l != K) w = f2fma(tcoef(t, l), d[l], w);
+            ring[t][slot] = w;
         }
     };
+    wait_upto(min(nch, (2 * K - 1) / CR + 1));
 #pragma unroll
-    for (int r = 0; r < 2 * K; ++r) tpass(lr0 + r, r);
+    for (int r = 0; r < 2 * K; ++r) tpass(r, r);
     float2 acc = make_float2(0.f, 0.f), acz = make_float2(0.f, 0.f);
 #pragma unroll 1
-    for (int m = 0; m < MRG; ++m) {
+    for (int m = 0; m < nblk_rows; ++m) {
+        const int j0 = m * P;
+        const int jend = j0 + P;
+        wait_upto(min(nch, (jend - 1 + 2 * K) / CR + 1));
 #pragma unroll
         for (int u = 0; u < P; ++u) {
-            const int al = lr0 + m * P + u;   // tile-local output row
-            tpass(al + 2 * K, (u + P - 1) % P);
-            // row coefficients as 16-byte broadcasts: float4 e/2 holds coefficients e, e+1 (SR2 even)
-            const float4* srow4 = reinterpret_cast<const float4*>(S2s + al * SR2);
-            auto sc2 = [&](int e) -> float2 {
-                const float4 v = srow4[e >> 1];
-                return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
-            };
-            float2 yt[NT];
+            const int j = j0 + u;   // segment output row
             {
-                const float2 xc = xr0[(u + K) % P], wc = ring[0][(u + K) % P];
-                float2 ya = f2mul(sc2(K), xc), yb = f2mul(sc2(K), wc);
+                tpass(j + 2 * K, (u + P - 1) % P);
+                // row coefficients as 16-byte broadcasts: float4 e/2 holds coefficients e, e+1 (SR2 even)
+                const float4* srow4 = reinterpret_cast<const float4*>(S2s + (j & (RING - 1)) * SR2);
+                auto sc2 = [&](int e) -> float2 {
+                    const float4 v = srow4[e >> 1];
+                    return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+                };
+                float2 yt[NT];
+                {
+                    const float2 xc = xr0[(u + K) % P], wc = ring[0][(u + K) % P];
+                    float2 ya = f2mul(sc2(K), xc), yb = f2mul(sc2(K), wc);
 #pragma unroll
-                for (int j = 0; j < P; ++j)
-                    if (j != K) {
-                        ya = f2fma(sc2(j), f2sub(xr0[(u + j) % P], xc), ya);
-                        yb = f2fma(sc2(j), f2sub(ring[0][(u + j) % P], wc), yb);
-                    }
-                yt[0] = f2mul(d0, f2add(ya, yb));
-            }
+                    for (int jj = 0; jj < P; ++jj)
+                        if (jj != K) {
+                            ya = f2fma(sc2(jj), f2sub(xr0[(u + jj) % P], xc), ya);
+                            yb = f2fma(sc2(jj), f2sub(ring[0][(u + jj) % P], wc), yb);
+                        }
+                    yt[0] = f2mul(d0, f2add(ya, yb));
+                }
 #pragma unroll
-            for (int i = 1; i < NT; ++i) {
-                const float2 wc = ring[i][(u + K) % P];
-                float2 y = f2mul(sc2(i * P + K), wc);
+                for (int t = 1; t < NT; ++t) {
+                    const float2 wc = ring[t][(u + K) % P];
+                    float2 y = f2mul(sc2(t * P + K), wc);
 #pragma unroll
-                for (int j = 0; j < P; ++j)
-                    if (j != K) {
-                        if ((DM >> i) & 1u) y = f2fma(sc2(i * P + j), f2sub(ring[i][(u + j) % P], wc), y);
-                        else y = f2fma(sc2(i * P + j), ring[i][(u + j) % P], y);
-                    }
-                yt[i] = y;
-            }
-            // pairwise sum of the term results (independent chains above)
+                    for (int jj = 0; jj < P; ++jj)
+                        if (jj != K) {
+                            if ((DM >> t) & 1u) y = f2fma(sc2(t * P + jj), f2sub(ring[t][(u + jj) % P], wc), y);
+                            else y = f2fma(sc2(t * P + jj), ring[t][(u + jj) % P], y);
+                        }
+                    yt[t] = y;
+                }
+                // pairwise sum of the term results (independent chains above)
 #pragma unroll
-            for (int s = 1; s < NT; s *= 2)
+                for (int s = 1; s < NT; s *= 2)
 #pragma unroll
-                for (int i = 0; i + s < NT; i += 2 * s) yt[i] = f2add(yt[i], yt[i + s]);
-            const float2 y = yt[0];
-            const int gr = a0 + al;
-            if (gr < a.q && col_ok) {
-                *reinterpret_cast<float2*>(LQ + (size_t)gr * a.ld + b) = y;
-                acc = f2fma(xr0[(u + K) % P], y, acc);
-                acz = f2fma(*reinterpret_cast<const float2*>(Zs + (al + K) * WCT + XPAD + 2 * cp), y, acz);
+                    for (int t = 0; t + s < NT; t += 2 * s) yt[t] = f2add(yt[t], yt[t + s]);
+                const float2 y = yt[0];
+                if (col_ok && j < L) {
+                    *reinterpret_cast<float2*>(LQ + (size_t)(a_lo + j) * a.ld + b) = y;
+                    acc = f2fma(xr0[(u + K) % P], y, acc);
+                    const float2 zc = *reinterpret_cast<const float2*>(
+                        Zs + ((j + K) & (RING - 1)) * WCT + XPAD + 2 * cp);
+                    acz = f2fma(zc, y, acz);
+                }
             }
         }
+        // chunks whose last row (its S rows end at output row (c + 1) CR - 1) is done: refill
+        const int can = min(nch, jend / CR);
+        if (can > released) {
+            __syncthreads();   // every thread is past the rows of those slots
+            if (tid == 0)
+                for (int c = released; c < can; ++c)
+                    if (c + D < nch) issue(c + D);
+            released = can;
+        }
     }
+    wait_upto(nch);   // every issued copy has landed before the CTA exits
     if (failed) atomicOr(&fail_s, 1);
-    double s = block_sum<G::NTH>((double)acc.x + (double)acc.y, red);
+    double s = block_sum<NTH>((double)acc.x + (double)acc.y, red);
     __syncthreads();   // red[] is reused
-    const double s2 = a.partial2 ? block_sum<G::NTH>((double)acz.x + (double)acz.y, red) : 0.0;
+    const double s2 = a.partial2 ? block_sum<NTH>((double)acz.x + (double)acz.y, red) : 0.0;
     const int nblk = gridDim.x * gridDim.y;
     if (tid == 0) {
         if (fail_s) atomicOr(a.status, DEV_ERR_TIMEOUT);
@@ -281,15 +329,42 @@ __global__ void __launch_bounds__(Geo2<K, NT>::NTH, MOFEM_APPLY_MINB)
     }
 }
 
+// Resident CTAs of the streaming apply on the current device (one wave), per (K, NT).
 template <int K, int NT>
-mofem_status launch_pcg2_t(const CUtensorMap& mZ, const CUtensorMap& mQ, const CUtensorMap& mS,
+int apply3_ctas_wanted_t() {
+    using G = Geo3<K, NT>;
+    static std::atomic<int> cache[MOFEM_MAX_DEV];
+    const int slot = dev_slot();
+    int n = cache[slot].load(std::memory_order_relaxed);
+    if (!n) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
+        smem_attr_once(k_apply_pcg3<K, NT>, (int)G::SMEM, attr_done);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_pcg3<K, NT>, G::NTH, G::SMEM) !=
+                cudaSuccess ||
+            per < 1)
+            per = 1;
+        n = (sms > 0 ? sms : 1) * per;
+        cache[slot].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+template <int K, int NT>
+mofem_status launch_pcg3_t(const CUtensorMap& mZ, const CUtensorMap& mQ, const CUtensorMap& mS,
                            const ApplyPcgArgs& a, int batch, cudaStream_t st) {
-    using G = Geo2<K, NT>;
-    auto kern = k_apply_pcg2<K, NT>;
+    using G = Geo3<K, NT>;
+    auto kern = k_apply_pcg3<K, NT>;
     static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
     MOFEM_CUDA_TRY(smem_attr_once(kern, (int)G::SMEM, attr_done));
-    dim3 grid((a.q + TB - 1) / TB, (a.q + G::TA - 1) / G::TA, batch);
-    kern<<<grid, G::NTH, G::SMEM, st>>>(mZ, mQ, mS, a);
+    const int strips = (a.q + TB - 1) / TB;
+    const int segs = apply3_segments(a.q, strips, batch, apply3_ctas_wanted_t<K, NT>(), K);
+    constexpr int P = 2 * K + 1;   // segments of whole row blocks: only the last one is ragged
+    const int seg_rows = ((a.q + segs - 1) / segs + P - 1) / P * P;
+    dim3 grid(strips, segs, batch);
+    kern<<<grid, G::NTH, G::SMEM, st>>>(mZ, mQ, mS, a, seg_rows);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

@@ -645,6 +645,20 @@ __global__ void k_scale_copy64(const double* src, long long s_bs, int s_ld, doub
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) b[c] = s * a[c];
 }
 
+// Graph conditional of the heterogeneous lockstep loop: 1 while any instance of any group
+// is active.  One block.
+__global__ void k_set_cond_any(PcgScalars* const* scs, const int* batch, int ngroups, cudaGraphConditionalHandle h) {
+    __shared__ int any_s;
+    if (threadIdx.x == 0) any_s = 0;
+    __syncthreads();
+    int any = 0;
+    for (int gi = 0; gi < ngroups; ++gi)
+        for (int i = threadIdx.x; i < batch[gi]; i += blockDim.x) any |= __ldcg(&scs[gi][i].active);
+    if (any) atomicOr(&any_s, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any_s ? 1u : 0u);
+}
+
 // dst += a * src, rows x cols per instance (FP64).
 __global__ void k_axpy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld, int cols,
                          double a) {
@@ -655,6 +669,13 @@ __global__ void k_axpy64(const double* src, long long s_bs, int s_ld, double* ds
 }
 
 }  // namespace
+
+mofem_status launch_set_cond_any(PcgScalars* const* scs, const int* batch, int ngroups, cudaGraphConditionalHandle h,
+                                 cudaStream_t st) {
+    k_set_cond_any<<<1, 128, 0, st>>>(scs, batch, ngroups, h);
+    MOFEM_CUDA_TRY(cudaGetLastError());
+    return MOFEM_OK;
+}
 
 mofem_status launch_axpy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld, int rows,
                            int cols, int batch, double a, cudaStream_t st) {

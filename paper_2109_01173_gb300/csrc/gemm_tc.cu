@@ -349,7 +349,51 @@ struct GemmChain {
     unsigned* end_ticket;    // CTAs done; the last one resets panel_cnt and unit_ctr for the next launch
     unsigned* unit_ctr;      // next tile index (dynamic order): taken by each pair's leader as it goes
     unsigned* mode;          // this launch's tile order, set by its first CTA: 1 static, 2 dynamic
+    // Several problems of different sizes in one launch (heterogeneous batches): ngroups > 0
+    // chains in global memory, one per group (its own maps, shapes, scalars and panel
+    // counters; same stage count); the units are stage-major across groups: ubase[s * ngroups
+    // + g] is the first unit of stage s of group g and ubase[ns * ngroups] the unit count.
+    // This chain then holds only the launch-level fields (ns, end_ticket, unit_ctr, mode).
+    const GemmChain* groups;
+    const int* ubase;
+    int ngroups;
 };
+
+// One unit (pair tile) of a launch, resolved to its group's chain.
+struct UnitRef {
+    const GemmChain* C;
+    int stg, inst, r, ntn, ntm, per_inst;
+};
+
+__device__ __forceinline__ UnitRef resolve_unit(const GemmChain& ch, int u) {
+    UnitRef x;
+    int t;
+    if (ch.ngroups == 0) {
+        x.C = &ch;
+        x.ntn = (ch.g[0].N + 255) / 256;
+        x.ntm = (ch.g[0].M + 255) / 256;
+        x.per_inst = x.ntn * x.ntm;
+        const int total = x.per_inst * ch.g[0].batch;
+        x.stg = u / total;
+        t = u - x.stg * total;
+    } else {   // the last base <= u (bases are non-decreasing)
+        int lo = 0, hi = ch.ns * ch.ngroups - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(ch.ubase + mid) <= u) lo = mid;
+            else hi = mid - 1;
+        }
+        x.stg = lo / ch.ngroups;
+        x.C = ch.groups + (lo - x.stg * ch.ngroups);
+        x.ntn = (x.C->g[0].N + 255) / 256;
+        x.ntm = (x.C->g[0].M + 255) / 256;
+        x.per_inst = x.ntn * x.ntm;
+        t = u - __ldg(ch.ubase + lo);
+    }
+    x.inst = t / x.per_inst;
+    x.r = t - x.inst * x.per_inst;
+    return x;
+}
 
 // Chain launches in flight on this device (all handles).  A launch walks the static
 // round-robin order only when it is the only one: the static order needs its pairs to
@@ -409,14 +453,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
     const int cr = (int)cluster_rank();
     const bool leader = cr == 0;
     const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
-    const int ntn = (g0.N + 255) / 256, ntm = (g0.M + 255) / 256;
-    const int per_inst = ntn * ntm;   // pair tiles per instance and stage
-    const int total = per_inst * g0.batch;
-    const int units = total * ch.ns;
+    const int units = ch.ngroups ? ch.ubase[ch.ns * ch.ngroups]
+                                 : ((g0.N + 255) / 256) * ((g0.M + 255) / 256) * g0.batch * ch.ns;
     constexpr int BK = 128 / (KIND == 0 ? 4 : 2);
     auto bar_addr = [&](uint64_t* b) { return smem_u32(b); };
 
-    auto active = [&](int inst) { return !g0.sc || g0.sc[inst].active; };
+    auto active = [&](const UnitRef& x) { return !x.C->g[0].sc || x.C->g[0].sc[x.inst].active; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST2; ++s) {
@@ -471,10 +513,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
 
     if (warp == 4) {
         if (lane == 0) {   // ---- TMA producer (both CTAs): own halves of A and B
-            for (int st = 0; st < ch.ns; ++st) {
-                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mA[st])) : "memory");
-                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mB[st])) : "memory");
-            }
+            if (!ch.ngroups)
+                for (int st = 0; st < ch.ns; ++st) {
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mA[st])) : "memory");
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mB[st])) : "memory");
+                }
             int it = 0;
             // The leader publishes tile j + 1 as it starts tile j, so that the partner (and
             // the counter's round trip) never hold up the start of a tile.
@@ -513,18 +556,19 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
                     u = cid + j * ncl;
                 }
                 if (u >= units || *abort_flag) break;
-                const int stg = u / total, t = u - stg * total;
-                const GemmArgs& g = ch.g[stg];
-                const int inst = t / per_inst, r = t - inst * per_inst;
-                if (!active(inst)) continue;
-                if (ch.dep[stg] && ch.panel_cnt) {   // the operand panel written by the previous stage
-                    const int pan = ch.dep[stg] == 2 ? r % ntn : r / ntn;
-                    const unsigned* c = ch.panel_cnt + ((size_t)(stg - 1) * g0.batch + inst) * ntm + pan;
+                const UnitRef x = resolve_unit(ch, u);
+                const GemmChain& C = *x.C;
+                const int stg = x.stg, inst = x.inst, r = x.r, ntn = x.ntn;
+                const GemmArgs& g = C.g[stg];
+                if (!active(x)) continue;
+                if (C.dep[stg] && C.panel_cnt) {   // the operand panel written by the previous stage
+                    const int pan = C.dep[stg] == 2 ? r % ntn : r / ntn;
+                    const unsigned* c = C.panel_cnt + ((size_t)(stg - 1) * C.g[0].batch + inst) * x.ntm + pan;
                     if (!panel_wait(c, 8u * (unsigned)ntn, abort_flag)) break;
                     asm volatile("fence.proxy.async.global;" ::: "memory");   // generic writes -> TMA reads
                 }
-                const CUtensorMap* mA = &ch.mA[stg];
-                const CUtensorMap* mB = &ch.mB[stg];
+                const CUtensorMap* mA = &C.mA[stg];
+                const CUtensorMap* mB = &C.mB[stg];
                 const int m0 = (r / ntn) * 256 + cr * 128, nh = (r % ntn) * 256 + cr * 128;
                 const int za = g.a_shared ? 0 : inst, zb = g.b_shared ? 0 : inst;
                 for (int kb = 0; kb < g.nk; ++kb, ++it) {
@@ -553,15 +597,16 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
                     u = cid + j * ncl;
                 }
                 if (u >= units || *abort_flag) break;
-                const int inst = (u % total) / per_inst;
-                if (!active(inst)) continue;
+                const UnitRef x = resolve_unit(ch, u);
+                if (!active(x)) continue;
+                const int nk = x.C->g[0].nk;
                 const int b = tl & 1;
                 const uint32_t use = (uint32_t)(tl >> 1);
                 if (tl >= 2 && !pwait(bar_addr(&pb->tempty[b]), (use - 1u) & 1u, abort_flag)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(b * 256);
                 bool ok = true;
-                for (int kb = 0; kb < g0.nk; ++kb, ++it) {
+                for (int kb = 0; kb < nk; ++kb, ++it) {
                     const int s = it % ST2;
                     const uint32_t ph = (uint32_t)(it / ST2) & 1u;
                     if (!pwait(bar_addr(&pb->full[s]), ph, abort_flag)) {
@@ -582,7 +627,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
         }
     } else {   // ---- epilogue warps 0-3 (both CTAs): thread = TMEM lane = output row
         int tl = 0;
-        const int cta_per_inst = per_inst * 2;
         for (int j = 0;; ++j) {
             int u;
             if (dyn) {
@@ -603,10 +647,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
                 u = cid + j * ncl;
             }
             if (u >= units) break;
-            const int stg = u / total, t = u - stg * total;
-            const GemmArgs& g = ch.g[stg];
-            const int inst = t / per_inst, r = t - inst * per_inst;
-            if (!active(inst)) continue;
+            const UnitRef x = resolve_unit(ch, u);
+            const GemmChain& C = *x.C;
+            const int stg = x.stg, inst = x.inst, r = x.r, ntn = x.ntn;
+            const GemmArgs& g = C.g[stg];
+            if (!active(x)) continue;
+            const int cta_per_inst = x.per_inst * 2;
             const int m0 = (r / ntn) * 256 + cr * 128, n0 = (r % ntn) * 256;
             const int ct = ((r / ntn) * 2 + cr) * ntn + (r % ntn);
             const int b = tl & 1;
@@ -636,13 +682,13 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(mapa_shared(bar_addr(&pb->tempty[b]), 0));
-            if (stg + 1 < ch.ns && ch.dep[stg + 1] && ch.panel_cnt) {
+            if (stg + 1 < C.ns && C.dep[stg + 1] && C.panel_cnt) {
                 // publish this warp's 32 rows of the tile to the next stage's TMA reads
                 // (4 warps x 2 CTAs per tile: a panel of ntn tiles is complete at 8 ntn)
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) atomicAdd(ch.panel_cnt + ((size_t)stg * g0.batch + inst) * ntm + r / ntn, 1u);
+                if (lane == 0) atomicAdd(C.panel_cnt + ((size_t)stg * C.g[0].batch + inst) * x.ntm + r / ntn, 1u);
             }
             if (epi == EPI_Z && g.rz_part) {
 #pragma unroll
@@ -684,13 +730,25 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
     }
     __syncthreads();
     cluster_sync_all();   // the peer's copies, commits and arrivals have all landed
-    if (threadIdx.x == 0 && pb->abort && g0.status) atomicOr(g0.status, DEV_ERR_TIMEOUT);
-    if (threadIdx.x == 0 && ch.panel_cnt && ch.ns > 1) {
+    if (threadIdx.x == 0 && pb->abort) {
+        if (ch.ngroups)
+            for (int gi = 0; gi < ch.ngroups; ++gi) {
+                if (ch.groups[gi].g[0].status) atomicOr(ch.groups[gi].g[0].status, DEV_ERR_TIMEOUT);
+            }
+        else if (g0.status)
+            atomicOr(g0.status, DEV_ERR_TIMEOUT);
+    }
+    if (threadIdx.x == 0 && (ch.panel_cnt || ch.ngroups) && ch.ns > 1) {
         __threadfence();
         const unsigned tk = atomicAdd(ch.end_ticket, 1u);
         if (tk == gridDim.x - 1) {   // every CTA is done with the counters: reset them
-            const int ncnt = (ch.ns - 1) * g0.batch * ntm;
-            for (int i = 0; i < ncnt; ++i) ch.panel_cnt[i] = 0u;
+            const int ng = ch.ngroups ? ch.ngroups : 1;
+            for (int gi = 0; gi < ng; ++gi) {
+                const GemmChain& C = ch.ngroups ? ch.groups[gi] : ch;
+                if (!C.panel_cnt) continue;
+                const int ncnt = (C.ns - 1) * C.g[0].batch * ((C.g[0].M + 255) / 256);
+                for (int i = 0; i < ncnt; ++i) C.panel_cnt[i] = 0u;
+            }
             if (ch.unit_ctr) *ch.unit_ctr = 0u;
             if (ch.mode) {   // the launch's registration in the in-flight count ends here
                 *ch.mode = 0u;
@@ -826,6 +884,14 @@ mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
         max_pairs_slot.store(n, std::memory_order_release);
     }
     GemmChain ch = ch0;
+    if (ch.ngroups > 0) {   // heterogeneous launch: descriptors validated when they were built
+        if (!ch.groups || !ch.ubase || !ch.end_ticket || !ch.unit_ctr || !ch.mode || batch <= 0)
+            return MOFEM_ERR_INVALID_ARG;
+        const int pairs = batch < max_pairs ? batch : max_pairs;   // batch = the launch's unit count
+        cfg.gridDim = dim3(CM * pairs);
+        MOFEM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ch));
+        return MOFEM_OK;
+    }
     if (ch.ns < 1 || ch.ns > CHAIN_MAX ||
         (ch.ns > 1 && (!ch.panel_cnt || !ch.end_ticket || !ch.unit_ctr || !ch.mode)))
         return MOFEM_ERR_INVALID_ARG;
@@ -953,10 +1019,10 @@ mofem_status tc_gemm_one(const mofem_ctx* c, int which, int idx, float* Z, cudaS
     return launch_gemm_kind(which, p.mA[idx], p.mB[idx], g, c->batch, st);
 }
 
-// Z = P^{-1}(R) with R already in p.Rop (rounded operand).  R32 (FP32, same
-// layout as Z) feeds the fused <R, Z> partials when rz_partial != nullptr.
-mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z, int z_ld,
-                        long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st, bool z_internal) {
+// The four-stage chain of Z = P^{-1}(R) with R already in p.Rop (rounded operand).
+// R32 (FP32, same layout as Z) feeds the fused <R, Z> partials when rz_partial != nullptr.
+static GemmChain tc_chain(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z, int z_ld,
+                   long long z_bs, double* rz_partial, PcgScalars* sc, bool z_internal) {
     const TcPlan& p = c->tc[which];
     const int q = c->q, ld = c->ld;
     const int bk = which == 0 ? 32 : 64;
@@ -1001,7 +1067,69 @@ mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long lo
     ch.end_ticket = p.panel_cnt + p.n_panel_cnt;
     ch.unit_ctr = p.panel_cnt + p.n_panel_cnt + 1;
     ch.mode = p.panel_cnt + p.n_panel_cnt + 2;
-    return launch_chain_kind(which, ch, c->batch, st);
+    for (int s = 0; s < 4; ++s) ch.g[s].batch = c->batch;
+    return ch;
+}
+
+mofem_status tc_precond(const mofem_ctx* c, int which, const float* R32, long long r_bs, int r_ld, float* Z, int z_ld,
+                        long long z_bs, double* rz_partial, PcgScalars* sc, cudaStream_t st, bool z_internal) {
+    return launch_chain_kind(which, tc_chain(c, which, R32, r_bs, r_ld, Z, z_ld, z_bs, rz_partial, sc, z_internal),
+                             c->batch, st);
+}
+
+// ---- heterogeneous launches: the chains of several handles (any q) in one persistent launch
+mofem_status tc_multi_build(const TcGroupArgs* ga, int n, int which, TcMulti* out) {
+    *out = TcMulti{};
+    if (n < 1) return MOFEM_ERR_INVALID_ARG;
+    std::vector<GemmChain> chains(n);
+    std::vector<const mofem_ctx*> cs(n);
+    for (int gi = 0; gi < n; ++gi) {
+        const mofem_ctx* c = ga[gi].c;
+        cs[gi] = c;
+        if (!c->tc[which].ready) return MOFEM_ERR_INVALID_ARG;
+        const long long bs = (long long)c->q * c->ld;
+        chains[gi] = tc_chain(c, which, ga[gi].R32, bs, c->ld, ga[gi].Z, c->ld, bs, ga[gi].rz_partial, c->d_sc, true);
+    }
+    std::vector<int> ubase((size_t)4 * n + 1, 0);
+    int run = 0;
+    for (int s = 0; s < 4; ++s)
+        for (int gi = 0; gi < n; ++gi) {
+            ubase[(size_t)s * n + gi] = run;
+            const GemmArgs& g = chains[gi].g[0];
+            if (chains[gi].ns != 4 || g.M != g.N || g.batch != cs[gi]->batch) return MOFEM_ERR_INVALID_ARG;
+            run += ((g.N + BN - 1) / BN) * ((g.M + BM * GEMM_CM - 1) / (BM * GEMM_CM)) * g.batch;
+        }
+    ubase[(size_t)4 * n] = run;
+    out->ngroups = n;
+    out->units = run;
+    out->which = which;
+    MOFEM_CUDA_TRY(cudaMalloc(&out->d_groups, sizeof(GemmChain) * n));
+    static_assert(sizeof(GemmChain) % 64 == 0, "tensor maps in the descriptor array stay 64-byte aligned");
+    MOFEM_CUDA_TRY(cudaMalloc(&out->d_ubase, sizeof(int) * ubase.size()));
+    MOFEM_CUDA_TRY(cudaMalloc(&out->d_ctr, sizeof(unsigned) * 3));
+    MOFEM_CUDA_TRY(cudaMemcpy(out->d_groups, chains.data(), sizeof(GemmChain) * n, cudaMemcpyHostToDevice));
+    MOFEM_CUDA_TRY(cudaMemcpy(out->d_ubase, ubase.data(), sizeof(int) * ubase.size(), cudaMemcpyHostToDevice));
+    MOFEM_CUDA_TRY(cudaMemset(out->d_ctr, 0, sizeof(unsigned) * 3));
+    return MOFEM_OK;
+}
+
+mofem_status tc_multi_launch(const TcMulti& m, cudaStream_t st) {
+    GemmChain ch{};
+    ch.ns = 4;
+    ch.groups = static_cast<const GemmChain*>(m.d_groups);
+    ch.ubase = m.d_ubase;
+    ch.ngroups = m.ngroups;
+    ch.end_ticket = m.d_ctr;
+    ch.unit_ctr = m.d_ctr + 1;
+    ch.mode = m.d_ctr + 2;
+    return launch_chain_kind(m.which, ch, m.units, st);
+}
+
+void tc_multi_free(TcMulti* m) {
+    cudaFree(m->d_groups);
+    cudaFree(m->d_ubase);
+    cudaFree(m->d_ctr);
+    *m = TcMulti{};
 }
 
 // The four preconditioner GEMMs on caller-provided BF16 buffers (operand copies

@@ -25,8 +25,11 @@ struct mofem_group_ctx {
         double* U = nullptr;          // [B][q][q]
     };
     int count = 0;
-    int concurrency = 0;              // groups in flight (0: all)
+    int concurrency = -1;             // -1: all groups in lockstep (one graph, one GEMM launch per
+                                      // iteration); else groups solved apart, this many at once (0: all)
     std::vector<Group> groups;
+    FusedState fused;                 // lockstep graph and descriptors, kept between solves
+    cudaStream_t st = nullptr;        // the lockstep solve's stream
 };
 
 namespace {
@@ -46,6 +49,8 @@ void make_layout(int count, const mofem_problem* p, std::vector<std::vector<int>
 }
 
 void free_group(mofem_group_ctx* g) {
+    fused_free(&g->fused);
+    if (g->st) cudaStreamDestroy(g->st);
     for (auto& gr : g->groups) {
         if (gr.h) mofem_destroy(gr.h);
         cudaFree(gr.F);
@@ -113,12 +118,62 @@ extern "C" mofem_status mofem_group_setup(int count, const mofem_problem* proble
     return MOFEM_OK;
 }
 
+// All groups in lockstep on one stream (solve_fused): MOFEM_ERR_UNSUPPORTED when that form
+// does not apply (FP64, or an FP16 inner solve that needs the TF32 retry), the caller's U
+// untouched then.
+static mofem_status solve_lockstep(mofem_group g, const double* const* F, double* const* U, double rtol, int max_iter,
+                                   mofem_precision prec, mofem_solve_info* infos, cudaStream_t stream) {
+    if (prec == MOFEM_FP64) return MOFEM_ERR_UNSUPPORTED;
+    if (!g->st) MOFEM_CUDA_TRY(cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking));
+    cudaEvent_t ev_in = nullptr;
+    MOFEM_CUDA_TRY(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    MOFEM_CUDA_TRY(cudaEventRecord(ev_in, stream));
+    MOFEM_CUDA_TRY(cudaStreamWaitEvent(g->st, ev_in, 0));
+    cudaEventDestroy(ev_in);
+    const int ng = (int)g->groups.size();
+    std::vector<mofem_ctx*> cs(ng);
+    std::vector<const double*> Fg(ng);
+    std::vector<double*> Ug(ng);
+    for (int gi = 0; gi < ng; ++gi) {
+        auto& gr = g->groups[gi];
+        const size_t nn = (size_t)gr.n * gr.n, qq = (size_t)gr.q * gr.q;
+        for (size_t j = 0; j < gr.members.size(); ++j) {
+            const int i = gr.members[j];
+            MOFEM_CUDA_TRY(cudaMemcpyAsync(gr.F + j * nn, F[i], sizeof(double) * nn, cudaMemcpyDeviceToDevice, g->st));
+            MOFEM_CUDA_TRY(cudaMemcpyAsync(gr.U + j * qq, U[i], sizeof(double) * qq, cudaMemcpyDeviceToDevice, g->st));
+        }
+        cs[gi] = gr.h;
+        Fg[gi] = gr.F;
+        Ug[gi] = gr.U;
+    }
+    std::vector<mofem_solve_info> gi_info(ng);
+    const mofem_status s = solve_fused(cs.data(), ng, Fg.data(), Ug.data(), rtol, max_iter, prec, &g->fused,
+                                       gi_info.data(), g->st);
+    if (s != MOFEM_OK && s != MOFEM_ERR_NOT_CONVERGED) return s;
+    for (int gi = 0; gi < ng; ++gi) {
+        auto& gr = g->groups[gi];
+        const size_t qq = (size_t)gr.q * gr.q;
+        for (size_t j = 0; j < gr.members.size(); ++j)
+            MOFEM_CUDA_TRY(cudaMemcpyAsync(U[gr.members[j]], gr.U + j * qq, sizeof(double) * qq,
+                                           cudaMemcpyDeviceToDevice, g->st));
+        if (infos)
+            for (int i : gr.members) infos[i] = gi_info[gi];
+    }
+    MOFEM_CUDA_TRY(cudaStreamSynchronize(g->st));
+    return s;
+}
+
 extern "C" mofem_status mofem_group_solve(mofem_group g, const double* const* F, double* const* U, double rtol,
                                           int max_iter, mofem_precision prec, mofem_solve_info* infos,
                                           cudaStream_t stream) {
     if (!g || !F || !U || !(rtol > 0.0) || max_iter < 1) return MOFEM_ERR_INVALID_ARG;
     for (int i = 0; i < g->count; ++i)
         if (!F[i] || !U[i]) return MOFEM_ERR_INVALID_ARG;
+    if (g->concurrency < 0) {
+        const mofem_status s = solve_lockstep(g, F, U, rtol, max_iter, prec, infos, stream);
+        if (s != MOFEM_ERR_UNSUPPORTED) return s;
+        // otherwise: the groups apart, all at once
+    }
     // groups start after the caller's prior work on `stream`
     cudaEvent_t ev_in = nullptr;
     if (cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming) != cudaSuccess) return MOFEM_ERR_CUDA;
@@ -163,6 +218,7 @@ extern "C" mofem_status mofem_group_solve(mofem_group g, const double* const* F,
     };
     // `width` workers take the next group (largest first) as soon as they are free
     const int width = g->concurrency > 0 ? std::min(g->concurrency, ng) : ng;
+    if (g->concurrency < 0) cudaStreamSynchronize(g->st);   // a lockstep attempt's copies are done
     std::atomic<int> next{0};
     std::vector<std::thread> th;
     for (int w = 0; w < width; ++w)
@@ -182,6 +238,7 @@ extern "C" mofem_status mofem_group_autotune(mofem_group g, const double* const*
     if (!g) return MOFEM_ERR_INVALID_ARG;
     const int ng = (int)g->groups.size();
     std::vector<int> cand;
+    if (prec != MOFEM_FP64) cand.push_back(-1);   // lockstep: one graph, one GEMM launch per iteration
     for (int c : {1, 2, 4, 8, 16})
         if (c < ng) cand.push_back(c);
     cand.push_back(ng);
@@ -202,6 +259,11 @@ extern "C" mofem_status mofem_group_autotune(mofem_group g, const double* const*
     copy_all(true);
     g->concurrency = ng;   // warm-up: operand copies, graphs and scratch of every group
     mofem_status s = mofem_group_solve(g, F, U, rtol, max_iter, prec, nullptr, nullptr);
+    if ((s == MOFEM_OK || s == MOFEM_ERR_NOT_CONVERGED) && prec != MOFEM_FP64) {   // and of the lockstep form
+        copy_all(false);
+        g->concurrency = -1;
+        s = mofem_group_solve(g, F, U, rtol, max_iter, prec, nullptr, nullptr);
+    }
     double best = 1e300;
     int best_c = ng;
     for (size_t ci = 0; ci < cand.size() && (s == MOFEM_OK || s == MOFEM_ERR_NOT_CONVERGED); ++ci) {
@@ -220,6 +282,12 @@ extern "C" mofem_status mofem_group_autotune(mofem_group g, const double* const*
     g->concurrency = best_c;
     if (chosen) *chosen = best_c;
     return (s == MOFEM_OK || s == MOFEM_ERR_NOT_CONVERGED) ? MOFEM_OK : s;
+}
+
+extern "C" mofem_status mofem_group_set_mode(mofem_group g, int mode) {
+    if (!g || mode < -1) return MOFEM_ERR_INVALID_ARG;
+    g->concurrency = mode;
+    return MOFEM_OK;
 }
 
 extern "C" mofem_status mofem_group_destroy(mofem_group g) {

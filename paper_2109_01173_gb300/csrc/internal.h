@@ -216,6 +216,8 @@ mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, c
 // per CTA, rows per staging box (TMA map), floats per duplicated S row.
 int apply_pcg_rows_per_cta(int K, int nt, bool fp64);
 int apply_pcg_box_rows(int K, int nt, bool fp64);
+int apply_pcg_s_box_rows();
+int apply_pcg_ctas_per_instance(int K, int nt, bool fp64, int q, int batch);
 bool apply_pcg_packed(int K, int nt, bool fp64);
 int apply_s2_row_floats(int K, int nt);
 mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
@@ -259,6 +261,23 @@ struct TcBuffers {   // caller-provided BF16 buffers of the preconditioner GEMMs
 mofem_status tc_precond_buffers(const mofem_ctx* c, const TcBuffers& b, float* Z, int z_ld, long long z_bs,
                                 cudaStream_t st);
 mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int reps, cudaStream_t st);
+// Heterogeneous launch: the preconditioner chains of several handles (any q, one operand
+// precision) in one persistent launch; descriptors built once in device memory.
+struct TcGroupArgs {
+    const mofem_ctx* c;
+    const float* R32;      // FP32 residual (internal layout) for the fused <R, Z>
+    float* Z;              // output (internal layout; row padding may be written)
+    double* rz_partial;    // <R, Z> partial slots
+};
+struct TcMulti {
+    void* d_groups = nullptr;      // per-group chain descriptors (device)
+    int* d_ubase = nullptr;        // unit bases (device)
+    unsigned* d_ctr = nullptr;     // launch counters: end ticket, unit counter, order word
+    int ngroups = 0, units = 0, which = 0;
+};
+mofem_status tc_multi_build(const TcGroupArgs* ga, int n, int which, TcMulti* out);
+mofem_status tc_multi_launch(const TcMulti& m, cudaStream_t st);
+void tc_multi_free(TcMulti* m);
 
 // ---- solver (solver.cu) ------------------------------------------------------
 mofem_status solver_init(mofem_ctx* c, cudaStream_t st);
@@ -284,3 +303,22 @@ mofem_status solve_imex_adjoint(mofem_ctx* c, double d_u, double tau, double r, 
 mofem_status launch_axpy64(const double* src, long long s_bs, int s_ld, double* dst, long long d_bs, int d_ld, int rows,
                            int cols, int batch, double a, cudaStream_t st);
 void mofem_free_extra(mofem_ctx* c);
+// Heterogeneous lockstep solve (solve_fused): graph, branch streams and the multi-group
+// GEMM descriptors, kept between solves of the same groups.
+struct FusedState {
+    TcMulti mc{};
+    cudaGraphExec_t loop = nullptr;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> ev;
+    PcgScalars** d_scs = nullptr;
+    int* d_bat = nullptr;
+    int pe = -1, max_iter = 0, body_kernels = 0;
+    bool fixed = false;
+};
+void fused_free(FusedState* f);
+// Solve the problems of G handles (one right-hand side and one U per handle, layouts as
+// mofem_pcg_solve) in lockstep; mixed forms only (MOFEM_ERR_UNSUPPORTED otherwise, and when
+// an FP16 inner solve needs the TF32 retry: the caller then solves the groups apart).
+mofem_status solve_fused(mofem_ctx* const* cs, int G, const double* const* F, double* const* U, double rtol,
+                         int max_iter, mofem_precision prec, FusedState* f, mofem_solve_info* infos, cudaStream_t st);

@@ -98,9 +98,9 @@ static mofem_status ensure_common(mofem_ctx* c, cudaStream_t st) {
     Extra& e = extras()[c];
     if (c->d_part) return MOFEM_OK;
     const int B = c->batch;
-    // one partial per CTA of either PCG-form apply (FP32 and FP64 tiles differ)
-    const int TA = std::min(apply_pcg_rows_per_cta(c->K, c->NT, false), apply_pcg_rows_per_cta(c->K, c->NT, true));
-    c->part.n_apply = ((c->q + 127) / 128) * ((c->q + TA - 1) / TA);
+    // one partial per CTA of either PCG-form apply (FP32 and FP64 launches differ)
+    c->part.n_apply = std::max(apply_pcg_ctas_per_instance(c->K, c->NT, false, c->q, B),
+                               apply_pcg_ctas_per_instance(c->K, c->NT, true, c->q, B));
     const int TG = apply_rows_per_cta(c->K);
     e.n_res = ((c->q + 127) / 128) * ((c->q + TG - 1) / TG);
     e.n_res_alloc = std::max(e.n_res, residual_update_df_ctas(c->K, c->q));
@@ -181,8 +181,7 @@ static mofem_status ensure_apply_maps(mofem_ctx* c, bool fp64) {
         MOFEM_TRY(make_row_map(&e.mQB32, w32(c, W32_QB), 4, c->q, c->q, c->batch, c->ld, WCT, HR));
         if (apply_pcg_packed(c->K, c->NT, false)) {
             const int w = c->s2_row;
-            MOFEM_TRY(make_row_map(&e.mS32, c->S2dup, 4, w, c->q, c->batch, w, w,
-                                   apply_pcg_rows_per_cta(c->K, c->NT, false)));
+            MOFEM_TRY(make_row_map(&e.mS32, c->S2dup, 4, w, c->q, c->batch, w, w, apply_pcg_s_box_rows()));
         }
         e.maps32 = true;
     }
@@ -319,7 +318,7 @@ mofem_status precond_tc(mofem_ctx* c, int which, const float* R, long long r_bs,
 
 // ---- PCG iteration (captured) -----------------------------------------------------
 static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int max_iter, bool fixed,
-                                  const cudaGraphConditionalHandle* cond, cudaStream_t st) {
+                                  const cudaGraphConditionalHandle* cond, cudaStream_t st, bool with_precond = true) {
     Extra& e = extras()[c];
     const bool fp64 = prec == MOFEM_FP64;
     const int which = plan_of(prec);
@@ -355,6 +354,11 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
                                 fp64 ? 0 : (which == 1 ? 1 : (which == 2 ? 2 : 0)), (fp64 || packed) ? 0 : 1,
                                 max_iter, fixed, cond, st, true, fp64 ? nullptr : Qp));
     // 3) Z = P^{-1}(R) ; rz and beta (last CTA)
+    if (!with_precond) {   // heterogeneous lockstep: one GEMM launch for every group (solve_fused)
+        if (!fp64 && which == 0)
+            MOFEM_TRY(launch_convert(R, 0, bs, c->ld, c->tc[0].Rop, 0, bs, c->ld, c->q, c->q, c->batch, st));
+        return MOFEM_OK;
+    }
     if (fp64) {
         MOFEM_TRY(precond64(c, (const double*)R, bs, c->ld, (double*)Z, bs, c->ld, st));
         MOFEM_TRY(launch_dot_partials(R, Z, true, bs, bs, c->batch, e.rz_slots[0], c->part.n_rz, st, c->d_sc,
@@ -750,6 +754,317 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
 
 mofem_status solver_init(mofem_ctx* c, cudaStream_t st) { return ensure_common(c, st); }
 
+// ---- heterogeneous batches in lockstep ------------------------------------------------
+// Groups of different (k, n, bc) iterate together: one CUDA graph per inner solve whose
+// conditional WHILE body holds, per iteration, every group's apply and update (one branch
+// per group, running side by side) and ONE persistent tensor-core launch with the four
+// preconditioner GEMMs of all groups (tc_multi_launch), then a control kernel that keeps
+// the loop going while any instance of any group is active.  The refinement steps are
+// taken in lockstep too; a group whose instances have all converged keeps zero residuals,
+// so its kernels return at once.
+void fused_free(FusedState* f) {
+    if (!f) return;
+    if (f->loop) cudaGraphExecDestroy(f->loop);
+    tc_multi_free(&f->mc);
+    for (auto s : f->br) cudaStreamDestroy(s);
+    for (auto e : f->ev) cudaEventDestroy(e);
+    if (f->cap) cudaStreamDestroy(f->cap);
+    cudaFree(f->d_scs);
+    cudaFree(f->d_bat);
+    *f = FusedState{};
+}
+
+mofem_status launch_set_cond_any(PcgScalars* const* scs, const int* batch, int ngroups, cudaGraphConditionalHandle h,
+                                 cudaStream_t st);
+
+static mofem_status build_fused_graph(mofem_ctx* const* cs, int G, mofem_precision pe, int max_iter, bool fixed,
+                                      FusedState* f) {
+    if (f->loop && f->pe == (int)pe && f->max_iter == max_iter && f->fixed == fixed) return MOFEM_OK;
+    if (f->loop) {
+        cudaGraphExecDestroy(f->loop);
+        f->loop = nullptr;
+    }
+    if (!f->cap) MOFEM_CUDA_TRY(cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking));
+    while ((int)f->br.size() < G) {
+        cudaStream_t s2;
+        MOFEM_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+        f->br.push_back(s2);
+    }
+    while ((int)f->ev.size() < G + 2) {
+        cudaEvent_t e;
+        MOFEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        f->ev.push_back(e);
+    }
+    cudaGraph_t g;
+    MOFEM_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    MOFEM_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    MOFEM_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    MOFEM_CUDA_TRY(cudaStreamBeginCaptureToGraph(f->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    mofem_status st = MOFEM_OK;
+    for (int it = 0; it < 2 && st == MOFEM_OK; ++it) {
+        // fork: every group's apply and update on its own branch
+        if (cudaEventRecord(f->ev[G], f->cap) != cudaSuccess) st = MOFEM_ERR_CUDA;
+        for (int gi = 0; gi < G && st == MOFEM_OK; ++gi) {
+            if (cudaStreamWaitEvent(f->br[gi], f->ev[G], 0) != cudaSuccess) st = MOFEM_ERR_CUDA;
+            if (st == MOFEM_OK) st = pcg_iteration(cs[gi], pe, it, max_iter, fixed, nullptr, f->br[gi], false);
+            if (st == MOFEM_OK && cudaEventRecord(f->ev[gi], f->br[gi]) != cudaSuccess) st = MOFEM_ERR_CUDA;
+            if (st == MOFEM_OK && cudaStreamWaitEvent(f->cap, f->ev[gi], 0) != cudaSuccess) st = MOFEM_ERR_CUDA;
+        }
+        // join, then the preconditioner of every group in one launch
+        if (st == MOFEM_OK) st = tc_multi_launch(f->mc, f->cap);
+    }
+    if (st == MOFEM_OK) st = launch_set_cond_any(f->d_scs, f->d_bat, G, h, f->cap);
+    cudaGraph_t out = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(f->cap, &out);
+    if (st != MOFEM_OK || ce != cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (st == MOFEM_OK) mofem_set_last_error(cudaGetErrorString(ce), __FILE__, __LINE__);
+        return st != MOFEM_OK ? st : MOFEM_ERR_CUDA;
+    }
+    f->body_kernels = count_kernel_nodes(body);
+    cudaGraphExec_t ex;
+    MOFEM_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+    cudaGraphDestroy(g);
+    f->loop = ex;
+    f->pe = (int)pe;
+    f->max_iter = max_iter;
+    f->fixed = fixed;
+    return MOFEM_OK;
+}
+
+mofem_status solve_fused(mofem_ctx* const* cs, int G, const double* const* F, double* const* U, double rtol,
+                         int max_iter, mofem_precision prec, FusedState* f, mofem_solve_info* infos, cudaStream_t st) {
+    if (G < 1 || prec == MOFEM_FP64) return MOFEM_ERR_UNSUPPORTED;
+    const mofem_precision pe = prec;
+    const int which = plan_of(pe);
+    for (int gi = 0; gi < G; ++gi)
+        if (cs[gi]->div_product && pe == MOFEM_MIXED_FP16) return MOFEM_ERR_UNSUPPORTED;
+    const bool fixed = (cs[0]->opts.flags & MOFEM_FLAG_FIXED_ITERS) != 0;
+    const bool trace = getenv("MOFEM_TRACE") != nullptr;
+    // ---- per-group set-up (first call allocates) and the multi-group descriptors
+    for (int gi = 0; gi < G; ++gi) {
+        mofem_ctx* c = cs[gi];
+        MOFEM_TRY(ensure_common(c, st));
+        MOFEM_TRY(ensure_w32(c, st));
+        MOFEM_TRY(tc_prepare(c, which, st));
+        MOFEM_TRY(ensure_apply_maps(c, false));
+    }
+    if (f->mc.ngroups != G || f->mc.which != which) {
+        tc_multi_free(&f->mc);
+        std::vector<TcGroupArgs> ga(G);
+        for (int gi = 0; gi < G; ++gi)
+            ga[gi] = TcGroupArgs{cs[gi], w32(cs[gi], W32_R), w32(cs[gi], W32_Z), extras()[cs[gi]].rz_slots[0]};
+        MOFEM_TRY(tc_multi_build(ga.data(), G, which, &f->mc));
+        cudaFree(f->d_scs);
+        cudaFree(f->d_bat);
+        f->d_scs = nullptr;
+        f->d_bat = nullptr;
+        std::vector<PcgScalars*> scs(G);
+        std::vector<int> bat(G);
+        for (int gi = 0; gi < G; ++gi) {
+            scs[gi] = cs[gi]->d_sc;
+            bat[gi] = cs[gi]->batch;
+        }
+        MOFEM_CUDA_TRY(cudaMalloc(&f->d_scs, sizeof(PcgScalars*) * G));
+        MOFEM_CUDA_TRY(cudaMalloc(&f->d_bat, sizeof(int) * G));
+        MOFEM_CUDA_TRY(cudaMemcpy(f->d_scs, scs.data(), sizeof(PcgScalars*) * G, cudaMemcpyHostToDevice));
+        MOFEM_CUDA_TRY(cudaMemcpy(f->d_bat, bat.data(), sizeof(int) * G, cudaMemcpyHostToDevice));
+        if (f->loop) {
+            cudaGraphExecDestroy(f->loop);
+            f->loop = nullptr;
+        }
+    }
+    MOFEM_TRY(build_fused_graph(cs, G, pe, max_iter, fixed, f));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MOFEM_CUDA_TRY(cudaEventCreate(&e0));
+    MOFEM_CUDA_TRY(cudaEventCreate(&e1));
+    MOFEM_CUDA_TRY(cudaEventRecord(e0, st));
+    // ---- right-hand sides, norms, first residuals (as solve_core, per group)
+    struct GS {
+        std::vector<double> bb, rr, ref2;
+        double rel = 0.0;
+        bool zero_guess = true, df_update = true, stalled = false, done = false;
+        int total_it = 0, outer = 0;
+        long long launches = 0;
+        int status = 0;
+    };
+    std::vector<GS> gs(G);
+    auto rel_max = [&](const GS& g, const std::vector<double>& r) {
+        double m = 0.0;
+        for (size_t i = 0; i < r.size(); ++i) {
+            double v;
+            if (!std::isfinite(g.ref2[i]) || !std::isfinite(r[i])) v = NAN;
+            else v = g.ref2[i] > 0 ? std::sqrt(r[i] / g.ref2[i]) : (r[i] > 0 ? INFINITY : 0.0);
+            if (!(v <= m)) m = v;
+        }
+        return m;
+    };
+    for (int gi = 0; gi < G; ++gi) {
+        mofem_ctx* c = cs[gi];
+        Extra& e = extras()[c];
+        GS& g = gs[gi];
+        const int B = c->batch, q = c->q;
+        const long long bs = (long long)per(c);
+        MOFEM_CUDA_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+        MOFEM_TRY(op_rhs(c, F[gi], c->Bm64, bs, c->ld, st));
+        std::vector<double> both, uu;
+        MOFEM_TRY(launch_dot_partials(c->Bm64, c->Bm64, true, bs, bs, B, e.bb_part, c->part.n_rz, st));
+        MOFEM_TRY(launch_dot_partials(U[gi], U[gi], true, (long long)q * q, (long long)q * q, B,
+                                      e.bb_part + (size_t)B * c->part.n_rz, c->part.n_rz, st));
+        MOFEM_TRY(sum_partials(e.bb_part, c->part.n_rz, 2 * B, both, st));
+        g.bb.assign(both.begin(), both.begin() + B);
+        uu.assign(both.begin() + B, both.end());
+        for (int i = 0; i < B; ++i) g.zero_guess = g.zero_guess && uu[i] == 0.0;
+        if (g.zero_guess) {
+            MOFEM_CUDA_TRY(cudaMemcpyAsync(c->R64, c->Bm64, sizeof(double) * bs * B, cudaMemcpyDeviceToDevice, st));
+            g.rr = g.bb;
+        } else {
+            MOFEM_TRY(op_residual64(c, U[gi], (long long)q * q, q, c->R64, e.res_part, st));
+            MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, g.rr, st));
+        }
+        g.ref2 = g.bb;
+        g.rel = rel_max(g, g.rr);
+        g.launches = 1 + 2 + (g.zero_guess ? 0 : 1) + 1;
+        const double floor_est = std::max(1e-11, 2.0 * 0x1p-53 * (double)q * q / (M_PI * M_PI));
+        g.df_update = (c->opts.flags & MOFEM_FLAG_TRUE_RESIDUAL) == 0;
+        for (int i = 0; i < B; ++i) g.df_update = g.df_update && rtol * rtol * g.ref2[i] >= floor_est * floor_est * g.bb[i];
+        MOFEM_TRY(launch_convert(U[gi], 1, (long long)q * q, q, c->U64m, 1, bs, c->ld, q, q, B, st));
+        g.done = g.rel <= rtol || !std::isfinite(g.rel);
+    }
+    const int max_outer = cs[0]->opts.max_outer > 0 ? cs[0]->opts.max_outer : 20;
+    const double eta0 = cs[0]->opts.inner_rtol > 0 ? cs[0]->opts.inner_rtol : 1e-5;
+    std::vector<PcgScalars> sc;
+    int outer = 0;
+    long long shared_launches = 0;
+    auto any_open = [&]() {
+        for (auto& g : gs)
+            if (!g.done) return true;
+        return false;
+    };
+    while (any_open() && outer < max_outer) {
+        // ---- inner start of every group (converged groups get zero residuals: inactive)
+        for (int gi = 0; gi < G; ++gi) {
+            mofem_ctx* c = cs[gi];
+            GS& g = gs[gi];
+            const int B = c->batch, q = c->q;
+            const long long bs = (long long)per(c);
+            double eta = std::max(g.outer == 0 ? eta0 : 0.1 * eta0, 0.3 * rtol / std::max(g.rel, 1e-300));
+            if (eta >= 1.0) eta = 0.5;
+            MOFEM_TRY(launch_convert(c->R64, 1, bs, c->ld, w32(c, W32_R), 0, bs, c->ld, q, q, B, st));
+            for (int i = 0; i < B; ++i) {
+                const double ri = g.ref2[i] > 0 ? std::sqrt(g.rr[i] / g.ref2[i]) : 0.0;
+                if (g.done || ri <= rtol)
+                    MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_R) + bs * i, 0, sizeof(float) * bs, st));
+            }
+            MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_U), 0, sizeof(float) * bs * B, st));
+            MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_ULO), 0, sizeof(float) * bs * B, st));
+            MOFEM_CUDA_TRY(cudaMemsetAsync(w32(c, W32_QB), 0, sizeof(float) * bs * B, st));
+            MOFEM_TRY(launch_dot_partials(w32(c, W32_R), w32(c, W32_R), false, bs, bs, B, c->part.rr, c->part.n_upd, st));
+            MOFEM_TRY(launch_pcg_init(c, c->part.rr, c->part.n_upd, nullptr, eta, st));
+            if (which == 2)
+                MOFEM_TRY(launch_convert_scaled_f16(w32(c, W32_R), bs, c->ld, c->tc[2].Rop, bs, c->ld, q, q, B, c->d_sc,
+                                                    st));
+            else
+                MOFEM_TRY(launch_convert(w32(c, W32_R), 0, bs, c->ld, c->tc[which].Rop, conv_kind_of_plan(which), bs,
+                                         c->ld, q, q, B, st));
+        }
+        MOFEM_TRY(tc_multi_launch(f->mc, st));   // Z0 and <R0, Z0> of every group
+        MOFEM_CUDA_TRY(cudaGraphLaunch(f->loop, st));
+        // ---- fold, residual update and norms of every open group
+        int max_it = 0;
+        for (int gi = 0; gi < G; ++gi) {
+            mofem_ctx* c = cs[gi];
+            Extra& e = extras()[c];
+            GS& g = gs[gi];
+            const int B = c->batch, q = c->q;
+            const long long bs = (long long)per(c);
+            MOFEM_TRY(read_scalars(c, sc, st));
+            int it = 0;
+            bool bad = false;
+            for (auto& x : sc) {
+                it = std::max(it, x.iters);
+                bad = bad || (x.status & DEV_ERR_NONFINITE) || !std::isfinite(x.rr);
+            }
+            max_it = std::max(max_it, it);
+            if (g.done) continue;
+            if (bad && pe == MOFEM_MIXED_FP16) {   // FP16 range exceeded: the caller solves the groups one by one
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return MOFEM_ERR_UNSUPPORTED;
+            }
+            const bool from_zero = g.outer == 0 && g.zero_guess;
+            const bool upd = g.df_update && (!from_zero || residual_update_dfd_ok(c));
+            const int dmode = !upd ? 0 : (from_zero ? 2 : 1);
+            MOFEM_TRY(launch_fold_df(c->U64m, w32(c, W32_U), w32(c, W32_ULO), bs, B, c->d_sc, w32(c, W32_QA), dmode, st));
+            g.total_it += it;
+            g.launches += 8 + 3;   // convert, zeroing, dot, init, operand copy; fold, residual
+            int nblk = 0;
+            mofem_status du = MOFEM_ERR_UNSUPPORTED;
+            if (upd)
+                du = from_zero ? launch_residual_update_dfd(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, e.res_part, &nblk, st)
+                               : launch_residual_update_df(c, w32(c, W32_U), w32(c, W32_ULO), c->R64, e.res_part, &nblk, st);
+            if (du == MOFEM_OK) {
+                MOFEM_TRY(sum_partials(e.res_part, nblk, B, g.rr, st));
+            } else {
+                if (du != MOFEM_ERR_UNSUPPORTED) return du;
+                MOFEM_TRY(op_residual64(c, c->U64m, bs, c->ld, c->R64, e.res_part, st));
+                MOFEM_TRY(sum_partials(e.res_part, e.n_res, B, g.rr, st));
+            }
+            const double prev = g.rel;
+            g.rel = rel_max(g, g.rr);
+            ++g.outer;
+            if (std::isfinite(g.rel) && g.rel > 0.5 * prev) g.stalled = true;
+            g.done = g.rel <= rtol || !std::isfinite(g.rel) || g.stalled || fixed;
+            (void)q;
+        }
+        // one tensor-core launch and one graph per inner solve, plus the bodies of two iterations
+        shared_launches += 1 + (long long)std::max(1, (max_it + 1) / 2) * f->body_kernels;
+        if (trace) fprintf(stderr, "[mofem] fused outer %d: inner iterations %d\n", outer + 1, max_it);
+        ++outer;
+    }
+    MOFEM_CUDA_TRY(cudaEventRecord(e1, st));
+    std::vector<int> dev_status(G, 0);
+    for (int gi = 0; gi < G; ++gi) {
+        mofem_ctx* c = cs[gi];
+        const int q = c->q;
+        MOFEM_TRY(launch_convert(c->U64m, 1, (long long)per(c), c->ld, U[gi], 1, (long long)q * q, q, q, q, c->batch, st));
+        MOFEM_CUDA_TRY(cudaMemcpyAsync(&dev_status[gi], c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    MOFEM_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mofem_status worst = MOFEM_OK;
+    for (int gi = 0; gi < G; ++gi) {
+        GS& g = gs[gi];
+        mofem_status code = MOFEM_OK;
+        if (dev_status[gi] & DEV_ERR_TIMEOUT) code = MOFEM_ERR_TIMEOUT;
+        else if (!std::isfinite(g.rel)) code = MOFEM_ERR_NONFINITE;
+        else if (!(g.rel <= rtol) && !fixed) code = MOFEM_ERR_NOT_CONVERGED;
+        if (infos) {
+            mofem_solve_info& in = infos[gi];
+            in.status = code;
+            in.iterations = g.total_it;
+            in.outer_steps = g.outer;
+            in.batch = cs[gi]->batch;
+            in.rel_residual = g.rel;
+            in.ms_total = ms;
+            in.kernel_launches = g.launches + shared_launches;   // the shared launches counted in every group
+        }
+        if (code != MOFEM_OK && (worst == MOFEM_OK || worst == MOFEM_ERR_NOT_CONVERGED)) worst = code;
+    }
+    return worst;
+}
+
 mofem_status solve_elliptic(mofem_ctx* c, const double* F, double* U, double rtol, int max_iter, mofem_precision prec,
                             mofem_solve_info* info, cudaStream_t st) {
     MOFEM_TRY(ensure_common(c, st));
@@ -877,8 +1192,7 @@ mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const do
     MOFEM_TRY(make_row_map(&mQ, Qp, esz, c->q, c->q, B, ld, WCT, HR));
     const bool packed = apply_pcg_packed(c->K, c->NT, fp64);
     if (packed)
-        MOFEM_TRY(make_row_map(&mS, c->S2dup, 4, c->s2_row, c->q, B, c->s2_row, c->s2_row,
-                               apply_pcg_rows_per_cta(c->K, c->NT, false)));
+        MOFEM_TRY(make_row_map(&mS, c->S2dup, 4, c->s2_row, c->q, B, c->s2_row, c->s2_row, apply_pcg_s_box_rows()));
     std::vector<PcgScalars> h(B);
     for (int i = 0; i < B; ++i) {
         h[i] = PcgScalars{};
