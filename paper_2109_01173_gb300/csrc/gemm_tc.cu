@@ -359,17 +359,20 @@ struct GemmChain {
     int ngroups;
 };
 
-// One unit (pair tile) of a launch, resolved to its group's chain.
+// One unit (pair tile) of a launch, resolved to its group's chain (C: the group's
+// descriptor in global memory; unused by a single-chain launch, which reads its own
+// parameters directly).
 struct UnitRef {
     const GemmChain* C;
     int stg, inst, r, ntn, ntm, per_inst;
 };
 
+template <bool MULTI>
 __device__ __forceinline__ UnitRef resolve_unit(const GemmChain& ch, int u) {
     UnitRef x;
     int t;
-    if (ch.ngroups == 0) {
-        x.C = &ch;
+    if constexpr (!MULTI) {
+        x.C = nullptr;
         x.ntn = (ch.g[0].N + 255) / 256;
         x.ntm = (ch.g[0].M + 255) / 256;
         x.per_inst = x.ntn * x.ntm;
@@ -393,6 +396,14 @@ __device__ __forceinline__ UnitRef resolve_unit(const GemmChain& ch, int u) {
     x.inst = t / x.per_inst;
     x.r = t - x.inst * x.per_inst;
     return x;
+}
+
+// The chain a unit belongs to: the launch's own parameters (constant bank) for a single
+// chain, the group's descriptor otherwise.
+template <bool MULTI>
+__device__ __forceinline__ const GemmChain& chain_of(const GemmChain& ch, const UnitRef& x) {
+    if constexpr (MULTI) return *x.C;
+    else return ch;
 }
 
 // Chain launches in flight on this device (all handles).  A launch walks the static
@@ -442,7 +453,7 @@ __device__ __noinline__ bool panel_wait(const unsigned* c, unsigned need, volati
     return true;
 }
 
-template <int KIND>
+template <int KIND, bool MULTI>
 __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant__ GemmChain ch) {
     const GemmArgs& g0 = ch.g[0];
     extern __shared__ uint8_t smem_raw[];
@@ -453,12 +464,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
     const int cr = (int)cluster_rank();
     const bool leader = cr == 0;
     const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
-    const int units = ch.ngroups ? ch.ubase[ch.ns * ch.ngroups]
-                                 : ((g0.N + 255) / 256) * ((g0.M + 255) / 256) * g0.batch * ch.ns;
+    const int units = MULTI ? ch.ubase[ch.ns * ch.ngroups]
+                            : ((g0.N + 255) / 256) * ((g0.M + 255) / 256) * g0.batch * ch.ns;
     constexpr int BK = 128 / (KIND == 0 ? 4 : 2);
     auto bar_addr = [&](uint64_t* b) { return smem_u32(b); };
 
-    auto active = [&](const UnitRef& x) { return !x.C->g[0].sc || x.C->g[0].sc[x.inst].active; };
+    auto active = [&](const UnitRef& x) {
+        const GemmArgs& a0 = chain_of<MULTI>(ch, x).g[0];
+        return !a0.sc || a0.sc[x.inst].active;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST2; ++s) {
@@ -513,7 +527,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
 
     if (warp == 4) {
         if (lane == 0) {   // ---- TMA producer (both CTAs): own halves of A and B
-            if (!ch.ngroups)
+            if constexpr (!MULTI)
                 for (int st = 0; st < ch.ns; ++st) {
                     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mA[st])) : "memory");
                     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ch.mB[st])) : "memory");
@@ -556,8 +570,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
                     u = cid + j * ncl;
                 }
                 if (u >= units || *abort_flag) break;
-                const UnitRef x = resolve_unit(ch, u);
-                const GemmChain& C = *x.C;
+                const UnitRef x = resolve_unit<MULTI>(ch, u);
+                const GemmChain& C = chain_of<MULTI>(ch, x);
                 const int stg = x.stg, inst = x.inst, r = x.r, ntn = x.ntn;
                 const GemmArgs& g = C.g[stg];
                 if (!active(x)) continue;
@@ -597,9 +611,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
                     u = cid + j * ncl;
                 }
                 if (u >= units || *abort_flag) break;
-                const UnitRef x = resolve_unit(ch, u);
+                const UnitRef x = resolve_unit<MULTI>(ch, u);
                 if (!active(x)) continue;
-                const int nk = x.C->g[0].nk;
+                const int nk = chain_of<MULTI>(ch, x).g[0].nk;
                 const int b = tl & 1;
                 const uint32_t use = (uint32_t)(tl >> 1);
                 if (tl >= 2 && !pwait(bar_addr(&pb->tempty[b]), (use - 1u) & 1u, abort_flag)) break;
@@ -647,8 +661,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
                 u = cid + j * ncl;
             }
             if (u >= units) break;
-            const UnitRef x = resolve_unit(ch, u);
-            const GemmChain& C = *x.C;
+            const UnitRef x = resolve_unit<MULTI>(ch, u);
+            const GemmChain& C = chain_of<MULTI>(ch, x);
             const int stg = x.stg, inst = x.inst, r = x.r, ntn = x.ntn;
             const GemmArgs& g = C.g[stg];
             if (!active(x)) continue;
@@ -731,7 +745,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
     __syncthreads();
     cluster_sync_all();   // the peer's copies, commits and arrivals have all landed
     if (threadIdx.x == 0 && pb->abort) {
-        if (ch.ngroups)
+        if (MULTI)
             for (int gi = 0; gi < ch.ngroups; ++gi) {
                 if (ch.groups[gi].g[0].status) atomicOr(ch.groups[gi].g[0].status, DEV_ERR_TIMEOUT);
             }
@@ -742,9 +756,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
         __threadfence();
         const unsigned tk = atomicAdd(ch.end_ticket, 1u);
         if (tk == gridDim.x - 1) {   // every CTA is done with the counters: reset them
-            const int ng = ch.ngroups ? ch.ngroups : 1;
+            const int ng = MULTI ? ch.ngroups : 1;
             for (int gi = 0; gi < ng; ++gi) {
-                const GemmChain& C = ch.ngroups ? ch.groups[gi] : ch;
+                const GemmChain& C = MULTI ? ch.groups[gi] : ch;
                 if (!C.panel_cnt) continue;
                 const int ncnt = (C.ns - 1) * C.g[0].batch * ((C.g[0].M + 255) / 256);
                 for (int i = 0; i < ncnt; ++i) C.panel_cnt[i] = 0u;
@@ -852,10 +866,10 @@ int num_sms() {
 
 constexpr int GEMM_CM = 2;   // CTAs per cluster: one tcgen05 CTA pair
 
-template <int KIND>
+template <int KIND, bool MULTI>
 mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
     constexpr int CM = GEMM_CM;
-    auto kern = k_gemm_2sm<KIND>;
+    auto kern = k_gemm_2sm<KIND, MULTI>;
     static std::atomic<int> max_pairs_dev[MOFEM_MAX_DEV];   // per device: co-resident pairs
     std::atomic<int>& max_pairs_slot = max_pairs_dev[dev_slot()];
     int max_pairs = max_pairs_slot.load(std::memory_order_acquire);
@@ -884,7 +898,8 @@ mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
         max_pairs_slot.store(n, std::memory_order_release);
     }
     GemmChain ch = ch0;
-    if (ch.ngroups > 0) {   // heterogeneous launch: descriptors validated when they were built
+    if (MULTI != (ch.ngroups > 0)) return MOFEM_ERR_INVALID_ARG;
+    if (MULTI) {   // heterogeneous launch: descriptors validated when they were built
         if (!ch.groups || !ch.ubase || !ch.end_ticket || !ch.unit_ctr || !ch.mode || batch <= 0)
             return MOFEM_ERR_INVALID_ARG;
         const int pairs = batch < max_pairs ? batch : max_pairs;   // batch = the launch's unit count
@@ -915,9 +930,14 @@ mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
 }
 
 mofem_status launch_chain_kind(int which, const GemmChain& ch, int batch, cudaStream_t st) {
-    if (which == 1) return launch_chain<1>(ch, batch, st);
-    if (which == 2) return launch_chain<2>(ch, batch, st);
-    return launch_chain<0>(ch, batch, st);
+    if (ch.ngroups > 0) {
+        if (which == 1) return launch_chain<1, true>(ch, batch, st);
+        if (which == 2) return launch_chain<2, true>(ch, batch, st);
+        return launch_chain<0, true>(ch, batch, st);
+    }
+    if (which == 1) return launch_chain<1, false>(ch, batch, st);
+    if (which == 2) return launch_chain<2, false>(ch, batch, st);
+    return launch_chain<0, false>(ch, batch, st);
 }
 
 // One GEMM: a chain of one stage.
