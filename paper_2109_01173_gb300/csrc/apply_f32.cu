@@ -92,22 +92,28 @@ int apply_pcg_rows_per_cta(int K, int nt, bool fp64) {
 // Rows of one TMA box of Z / Q_prev: a staged chunk of the streaming apply, or the tile
 // with its K-row halo of the tiled one.
 int apply_pcg_box_rows(int K, int nt, bool fp64) {
-    if (apply_pcg_packed(K, nt, fp64)) return Geo3<2, 5>::CR;
+    if (apply_pcg_packed(K, nt, fp64)) return Geo3<2, 5, 1>::CR;
     return apply_pcg_rows_per_cta(K, nt, fp64) + 2 * K;
 }
 
 // Rows of one TMA box of the duplicated S rows (streaming apply).
-int apply_pcg_s_box_rows() { return Geo3<2, 5>::CR; }
+int apply_pcg_s_box_rows() { return Geo3<2, 5, 1>::CR; }
 
 // 2 * SR2 of Geo3: the duplicated S row, a multiple of 4 float2 (32-byte rows)
 int apply_s2_row_floats(int K, int nt) { return 2 * (((nt * (2 * K + 1) + 3) / 4) * 4); }
 
+template <int K, int NT>
+static int segs_k(int q, int strips, int batch) {
+    constexpr int NS = packed_streams(K, NT);
+    return apply3_segments(q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>(), K, NS);
+}
+
 template <int K>
-static int ctas_k(int nt) {
+static int segs_kn(int nt, int q, int strips, int batch) {
     if constexpr (packed_apply_ok(K, 8)) {
-        if (nt == 8) return apply3_ctas_wanted_t<K, 8>();
+        if (nt == 8) return segs_k<K, 8>(q, strips, batch);
     }
-    if constexpr (packed_apply_ok(K, 5)) return apply3_ctas_wanted_t<K, 5>();
+    if constexpr (packed_apply_ok(K, 5)) return segs_k<K, 5>(q, strips, batch);
     return 1;
 }
 
@@ -119,12 +125,10 @@ int apply_pcg_ctas_per_instance(int K, int nt, bool fp64, int q, int batch) {
         const int TA = apply_pcg_rows_per_cta(K, nt, fp64);
         return strips * ((q + TA - 1) / TA);
     }
-    int want = 1;
     switch (K) {
-        case 1: want = ctas_k<1>(nt); break;
-        case 2: want = ctas_k<2>(nt); break;
-        case 3: want = ctas_k<3>(nt); break;
-        default: want = ctas_k<4>(nt); break;
+        case 1: return strips * segs_kn<1>(nt, q, strips, batch);
+        case 2: return strips * segs_kn<2>(nt, q, strips, batch);
+        case 3: return strips * segs_kn<3>(nt, q, strips, batch);
+        default: return strips * segs_kn<4>(nt, q, strips, batch);
     }
-    return strips * apply3_segments(q, strips, batch, want, K);
 }

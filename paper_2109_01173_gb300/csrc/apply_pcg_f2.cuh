@@ -32,13 +32,19 @@
 
 namespace mofem_apply_impl {
 
-template <int K, int NT>
+template <int K, int NT, int NS>
 struct Geo3 {
     static constexpr int P = 2 * K + 1;
     static constexpr int NTH = 64;                       // threads = column pairs per CTA
     static constexpr int CR = 4;                         // rows per staged chunk
-    static constexpr int D = 4;                          // chunks in the ring
-    static constexpr int RING = CR * D;                  // staged rows (power of two)
+    static constexpr int D = 4;                          // chunks in each stream's ring
+    static constexpr int RING = CR * D;                  // staged rows per stream (power of two)
+    static constexpr int RELEASE = 1;                    // chunks released (and refilled) together
+    // register-ring slots of t-pass rows: one more than the stencil needs (2K + 1), so that
+    // the t-pass of the next row writes a slot the current row's s-pass does not read and
+    // the two can overlap; rows are unrolled by RSLOT.  Where the chunk ring is too short
+    // for the longer block, the stencil's own 2K + 1.
+    static constexpr int RSLOT = (D - RELEASE) * CR >= 4 * K + 1 ? P + 1 : P;
     static constexpr int SR2 = ((NT * P + 3) / 4) * 4;   // float2 per duplicated S row (a chunk of S rows
                                                          // stays a 128-byte multiple)
     static constexpr bool TREG = NT * P <= 25;           // T coefficients in registers, else shared
@@ -46,20 +52,29 @@ struct Geo3 {
     static constexpr int ZCH = CR * WCT;                 // floats per chunk of Z (and of Q_prev)
     static constexpr int SCH = CR * SR2;                 // float2 per chunk of S rows
     static constexpr uint32_t CHUNK_BYTES = 2u * ZCH * 4u + (uint32_t)SCH * 8u;
-    static constexpr size_t SMEM = (size_t)D * CHUNK_BYTES + (TREG ? 0 : (size_t)NT * P * NTH * 8) + 128;
-    // register budget: 6 resident CTAs (168 registers) with T in registers; with T in shared
-    // memory the staging caps residency lower, which leaves room for the longer ring
-    static constexpr int MINB = TREG ? 6 : 4;
+    static constexpr uint32_t STREAM_BYTES = (uint32_t)D * CHUNK_BYTES;
+    static constexpr size_t SMEM = (size_t)NS * STREAM_BYTES + (TREG ? 0 : (size_t)NT * P * NTH * 8) + 128;
+    // register budget: the T coefficients (in registers when TREG) serve every stream of
+    // the thread; one stream with the extra slot fits 204 registers (5 resident CTAs), two
+    // streams 255 (4 CTAs)
+    static constexpr int MINB = NS == 1 ? (TREG ? 5 : 4) : 4;
     static_assert((RING & (RING - 1)) == 0, "ring rows must be a power of two");
     static_assert((ZCH * 4) % 128 == 0 && (SCH * 8) % 128 == 0, "TMA destinations stay 128-byte aligned");
-    // a chunk is refilled only after its last row is done; the rows that wait for it must
-    // not be the ones that release it: (D - 1) CR >= 2K (t-pass reach) + 2K (unrolled block)
-    static_assert((D - 1) * CR >= 4 * K, "ring too short for the stencil reach");
+    // a chunk is refilled only after its last row is done, RELEASE chunks at a time; the rows
+    // that wait for it must not be the ones that release it:
+    // (D - RELEASE) CR >= 2K (t-pass reach) + RSLOT - 1 (unrolled block)
+    static_assert((D - RELEASE) * CR >= 2 * K + RSLOT - 1, "ring too short for the stencil reach");
+    static_assert(NS == 1 || TREG, "two streams per thread only with the T coefficients in registers");
 };
 
 // Operator forms served by the packed kernel (the ring and, if TREG, the T
 // coefficients live in registers); the others use k_apply_pcg.
 __host__ __device__ constexpr bool packed_apply_ok(int K, int NT) { return NT * (2 * K + 1) <= 40; }
+// Row streams per thread of the packed kernel.  Two streams share the T coefficients and
+// cut the instructions by 17% (P2 2049 x 4), but at 255 registers only 8 warps fit per SM
+// and the launch took 100.8 us against 98.6 for one stream: the shared-memory pipe (66% of
+// peak in both) is what the two forms share; one stream is kept.
+__host__ __device__ constexpr int packed_streams(int, int) { return 1; }
 
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -67,32 +82,37 @@ __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(
 // a - c, one rounding (fma with an exact -1 product)
 __device__ __forceinline__ float2 f2sub(float2 a, float2 c) { return __ffma2_rn(c, make_float2(-1.f, -1.f), a); }
 
-// Rows of one segment and the number of segments per strip: at most one wave of resident
-// CTAs over all strips and instances (a partial second wave would double the time of the
-// SMs that run it), at least 8 (2K + 8) rows per segment.
-__host__ __device__ inline int apply3_segments(int q, int strips, int batch, int ctas_wanted, int K) {
-    const int min_rows = 8 * (2 * K + 8);
+// Number of segments per strip: at most one wave of resident CTAs over all strips and
+// instances (a partial second wave would double the time of the SMs that run it), at
+// least 8 (2K + 8) rows per stream.
+__host__ __device__ inline int apply3_segments(int q, int strips, int batch, int ctas_wanted, int K, int ns) {
+    const int min_rows = 8 * (2 * K + 8) * ns;
     int segs = ctas_wanted / (strips * batch);
     const int max_segs = (q + min_rows - 1) / min_rows;
     if (segs > max_segs) segs = max_segs;
     return segs < 1 ? 1 : segs;
 }
 
-template <int K, int NT>
-__global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
+// One CTA: a strip of 128 columns (64 column pairs, one per thread) of one instance and a
+// segment of rows, split into NS row streams of `srows` rows that the thread advances in
+// lockstep (independent instruction streams for the scheduler; the T coefficients are
+// loaded once and serve all of them).  Each stream has its own TMA chunk ring.
+template <int K, int NT, int NS>
+__global__ void __launch_bounds__(Geo3<K, NT, NS>::NTH, Geo3<K, NT, NS>::MINB)
     k_apply_pcg3(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mQ,
-                 const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a, int seg_rows) {
-    using G = Geo3<K, NT>;
+                 const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a, int srows) {
+    using G = Geo3<K, NT, NS>;
     constexpr int P = G::P, SR2 = G::SR2, KE = G::KE, CR = G::CR, D = G::D, RING = G::RING, NTH = G::NTH;
     constexpr unsigned DM = DiffMask<NT>::value;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sbase =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-    float* Zs = reinterpret_cast<float*>(sbase);               // [RING][WCT]
-    float* Qs = Zs + RING * WCT;                                // [RING][WCT]
-    float2* S2s = reinterpret_cast<float2*>(Qs + RING * WCT);   // [RING][SR2]
-    float2* T2s = S2s + RING * SR2;                             // [NT*P][NTH] (!TREG)
-    __shared__ __align__(8) unsigned long long bar[D];
+    // stream s: Z ring [RING][WCT], Q_prev ring [RING][WCT], S ring [RING][SR2]
+    auto Zs = [&](int st) { return reinterpret_cast<float*>(sbase + st * G::STREAM_BYTES); };
+    auto Qs = [&](int st) { return Zs(st) + RING * WCT; };
+    auto S2s = [&](int st) { return reinterpret_cast<float2*>(Qs(st) + RING * WCT); };
+    float2* T2s = reinterpret_cast<float2*>(sbase + NS * G::STREAM_BYTES);   // [NT*P][NTH] (!TREG)
+    __shared__ __align__(8) unsigned long long bar[NS][D];
     __shared__ double red[NTH / 32];
     __shared__ float beta_s;
     __shared__ int fail_s, last_s;
@@ -100,45 +120,54 @@ __global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
     PcgScalars* sc = a.sc + inst;
     if (a.use_sc && !sc->active) return;
     const int b0 = blockIdx.x * TB;
-    const int a_lo = blockIdx.y * seg_rows;
-    const int L = max(0, min(a.q, a_lo + seg_rows) - a_lo);   // output rows of this segment
-    // rows are computed in whole blocks of P (straight-line code, stores guarded): the
-    // last block may run past L into zero-filled or neighbouring rows, never stored
-    const int nblk_rows = (L + P - 1) / P;
-    const int LP = nblk_rows * P;
-    const int nch = (LP + 2 * K + CR - 1) / CR;                 // chunks of input rows a_lo - K ...
+    int a_lo[NS], L[NS];
+    int Lmax = 0;
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+        a_lo[st] = (blockIdx.y * NS + st) * srows;
+        L[st] = max(0, min(a.q, a_lo[st] + srows) - a_lo[st]);   // output rows of stream st
+        Lmax = max(Lmax, L[st]);
+    }
+    // rows are computed in whole blocks of RSLOT (straight-line code, stores guarded): a
+    // block may run past L into zero-filled or neighbouring rows, never stored
+    constexpr int RS = G::RSLOT;
+    const int nblk_rows = (Lmax + RS - 1) / RS;
+    const int nch = (nblk_rows * RS + 2 * K + CR - 1) / CR;   // chunks of each stream: input rows a_lo - K ...
     if (tid == 0) {
-        for (int i = 0; i < D; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[i])) : "memory");
+        for (int st = 0; st < NS; ++st)
+            for (int i = 0; i < D; ++i)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[st][i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail_s = 0;
         beta_s = (a.use_sc && sc->iters > 0) ? (float)sc->beta : 0.f;
     }
     __syncthreads();
-    // chunk c -> ring slot c % D: input rows a_lo - K + c CR .. (Z, Q_prev) and S rows a_lo + c CR ..
-    auto issue = [&](int c) {
+    // chunk c of stream st -> its ring slot c % D: input rows a_lo - K + c CR .. (Z, Q_prev)
+    // and S rows a_lo + c CR ..
+    auto issue = [&](int st, int c) {
         const int slot = c % D;
-        const uint32_t b = smem_u32(&bar[slot]);
+        const uint32_t bb = smem_u32(&bar[st][slot]);
         const uint64_t pz = reinterpret_cast<uint64_t>(&mZ), pq = reinterpret_cast<uint64_t>(&mQ),
                        ps = reinterpret_cast<uint64_t>(&mS);
-        const int x0 = b0 - XPAD, y0 = a_lo - K + c * CR;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(G::CHUNK_BYTES)
+        const int x0 = b0 - XPAD, y0 = a_lo[st] - K + c * CR;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(G::CHUNK_BYTES)
                      : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(S2s + slot * G::SCH)), "l"(ps), "r"(b), "r"(0), "r"(a_lo + c * CR), "r"(inst)
+            ::"r"(smem_u32(S2s(st) + slot * G::SCH)), "l"(ps), "r"(bb), "r"(0), "r"(a_lo[st] + c * CR), "r"(inst)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(Zs + slot * G::ZCH)), "l"(pz), "r"(b), "r"(x0), "r"(y0), "r"(inst)
+            ::"r"(smem_u32(Zs(st) + slot * G::ZCH)), "l"(pz), "r"(bb), "r"(x0), "r"(y0), "r"(inst)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(Qs + slot * G::ZCH)), "l"(pq), "r"(b), "r"(x0), "r"(y0), "r"(inst)
+            ::"r"(smem_u32(Qs(st) + slot * G::ZCH)), "l"(pq), "r"(bb), "r"(x0), "r"(y0), "r"(inst)
             : "memory");
     };
     if (tid == 0)
-        for (int c = 0; c < D && c < nch; ++c) issue(c);
+        for (int c = 0; c < D && c < nch; ++c)
+            for (int st = 0; st < NS; ++st) issue(st, c);
     const int cp = tid;
     const int b = b0 + 2 * cp;
     const float* Tt = reinterpret_cast<const float*>(a.T);
@@ -179,20 +208,24 @@ __global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
     float* LQ = reinterpret_cast<float*>(a.LQ) + (size_t)inst * a.bs;
     const bool col_ok = b < a.ld;   // pad columns [q, ld) receive zeros
     bool failed = false;
-    int waited = 0, released = 0;
-    auto wait_upto = [&](int need) {   // chunks 0 .. need-1 resident
+    int waited = 0, released = 0;   // chunks, the same count in every stream (lockstep)
+    auto wait_upto = [&](int need) {   // chunks 0 .. need-1 resident in every stream
         while (waited < need) {
-            if (!failed) failed = !mbar_wait_bounded(smem_u32(&bar[waited % D]), (uint32_t)((waited / D) & 1));
+#pragma unroll
+            for (int st = 0; st < NS; ++st)
+                if (!failed)
+                    failed = !mbar_wait_bounded(smem_u32(&bar[st][waited % D]), (uint32_t)((waited / D) & 1));
             ++waited;
         }
     };
-    float2 ring[NT][P];
-    float2 xr0[P];
-    // t-pass of input index i (input row a_lo - K + i) into ring slot `slot`
-    auto tpass = [&](int i, int slot) {
-        const int rr = (i & (RING - 1)) * WCT + XPAD + 2 * cp - KE;
-        const float2* z2 = reinterpret_cast<const float2*>(Zs + rr);
-        const float2* q2 = reinterpret_cast<const float2*>(Qs + rr);
+    float2 ring[NS][NT][RS];
+    float2 xr0[NS][RS];
+    // t-pass of input index i (input row a_lo - K + i, staged at ring row ri) of stream st
+    // into register-ring slot `slot`
+    auto tpass = [&](int st, int i, int ri, int slot) {
+        const int rr = ri * WCT + XPAD + 2 * cp - KE;
+        const float2* z2 = reinterpret_cast<const float2*>(Zs(st) + rr);
+        const float2* q2 = reinterpret_cast<const float2*>(Qs(st) + rr);
         float xs[2 * KE + 2];
 #pragma unroll
         for (int m = 0; m <= KE; ++m) {
@@ -201,10 +234,10 @@ __global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
             xs[2 * m + 1] = v.y;
         }
         const float2 xc = make_float2(xs[KE], xs[KE + 1]);
-        xr0[slot] = xc;
-        const int orow = i - K;   // segment output row whose centre this is
-        if (orow >= 0 && orow < L && col_ok)
-            *reinterpret_cast<float2*>(Qn + (size_t)(a_lo + orow) * a.ld + b) = xc;
+        xr0[st][slot] = xc;
+        const int orow = i - K;   // stream output row whose centre this is
+        if (orow >= 0 && orow < L[st] && col_ok)
+            *reinterpret_cast<float2*>(Qn + (size_t)(a_lo[st] + orow) * a.ld + b) = xc;
         float2 d[P];
 #pragma unroll
         for (int l = 0; l < P; ++l)
@@ -214,7 +247,7 @@ __global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
 #pragma unroll
             for (int l = 0; l < P; ++l)
                 if (l != K) w = f2fma(n0[l], d[l], w);
-            ring[0][slot] = w;
+            ring[st][0][slot] = w;
         }
 #pragma unroll
         for (int t = 1; t < NT; ++t) {
@@ -222,88 +255,98 @@ __global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
 #pragma unroll
             for (int l = 0; l < P; ++l)
                 if (l != K) w = f2fma(tcoef(t, l), d[l], w);
-            ring[t][slot] = w;
+            ring[st][t][slot] = w;
+        }
+    };
+    float2 acc = make_float2(0.f, 0.f), acz = make_float2(0.f, 0.f);
+    // s-pass of stream output row j (register-ring slots of input rows j .. j + 2K at
+    // (u + jj) % RSLOT; its S row staged at ring row rs, the Z centre at ring row rc)
+    auto spass = [&](int st, int j, int u, int rs, int rc) {
+        const float4* srow4 = reinterpret_cast<const float4*>(S2s(st) + rs * SR2);
+        auto sc2 = [&](int e) -> float2 {   // float4 e/2 holds coefficients e, e+1 (SR2 even)
+            const float4 v = srow4[e >> 1];
+            return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+        };
+        float2 yt[NT];
+        {
+            const float2 xc = xr0[st][(u + K) % RS], wc = ring[st][0][(u + K) % RS];
+            float2 ya = f2mul(sc2(K), xc), yb = f2mul(sc2(K), wc);
+#pragma unroll
+            for (int jj = 0; jj < P; ++jj)
+                if (jj != K) {
+                    ya = f2fma(sc2(jj), f2sub(xr0[st][(u + jj) % RS], xc), ya);
+                    yb = f2fma(sc2(jj), f2sub(ring[st][0][(u + jj) % RS], wc), yb);
+                }
+            yt[0] = f2mul(d0, f2add(ya, yb));
+        }
+#pragma unroll
+        for (int t = 1; t < NT; ++t) {
+            const float2 wc = ring[st][t][(u + K) % RS];
+            float2 y = f2mul(sc2(t * P + K), wc);
+#pragma unroll
+            for (int jj = 0; jj < P; ++jj)
+                if (jj != K) {
+                    if ((DM >> t) & 1u) y = f2fma(sc2(t * P + jj), f2sub(ring[st][t][(u + jj) % RS], wc), y);
+                    else y = f2fma(sc2(t * P + jj), ring[st][t][(u + jj) % RS], y);
+                }
+            yt[t] = y;
+        }
+        // pairwise sum of the term results (independent chains above)
+#pragma unroll
+        for (int s2 = 1; s2 < NT; s2 *= 2)
+#pragma unroll
+            for (int t = 0; t + s2 < NT; t += 2 * s2) yt[t] = f2add(yt[t], yt[t + s2]);
+        const float2 y = yt[0];
+        if (col_ok && j < L[st]) {
+            *reinterpret_cast<float2*>(LQ + (size_t)(a_lo[st] + j) * a.ld + b) = y;
+            acc = f2fma(xr0[st][(u + K) % RS], y, acc);
+            const float2 zc = *reinterpret_cast<const float2*>(Zs(st) + rc * WCT + XPAD + 2 * cp);
+            acz = f2fma(zc, y, acz);
         }
     };
     wait_upto(min(nch, (2 * K - 1) / CR + 1));
 #pragma unroll
-    for (int r = 0; r < 2 * K; ++r) tpass(r, r);
-    float2 acc = make_float2(0.f, 0.f), acz = make_float2(0.f, 0.f);
+    for (int r = 0; r < 2 * K; ++r)
+#pragma unroll
+        for (int st = 0; st < NS; ++st) tpass(st, r, r, r);
 #pragma unroll 1
     for (int m = 0; m < nblk_rows; ++m) {
-        const int j0 = m * P;
-        const int jend = j0 + P;
+        const int j0 = m * RS;
+        const int jend = j0 + RS;
         wait_upto(min(nch, (jend - 1 + 2 * K) / CR + 1));
 #pragma unroll
-        for (int u = 0; u < P; ++u) {
-            const int j = j0 + u;   // segment output row
-            {
-                tpass(j + 2 * K, (u + P - 1) % P);
-                // row coefficients as 16-byte broadcasts: float4 e/2 holds coefficients e, e+1 (SR2 even)
-                const float4* srow4 = reinterpret_cast<const float4*>(S2s + (j & (RING - 1)) * SR2);
-                auto sc2 = [&](int e) -> float2 {
-                    const float4 v = srow4[e >> 1];
-                    return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
-                };
-                float2 yt[NT];
-                {
-                    const float2 xc = xr0[(u + K) % P], wc = ring[0][(u + K) % P];
-                    float2 ya = f2mul(sc2(K), xc), yb = f2mul(sc2(K), wc);
+        for (int u = 0; u < RS; ++u) {
+            const int j = j0 + u;   // stream output row
+            // staged ring rows of the t-pass input (j + 2K), the S row (j), the Z centre (j + K)
+            const int zr = (j + 2 * K) & (RING - 1), sr = j & (RING - 1), cr = (j + K) & (RING - 1);
 #pragma unroll
-                    for (int jj = 0; jj < P; ++jj)
-                        if (jj != K) {
-                            ya = f2fma(sc2(jj), f2sub(xr0[(u + jj) % P], xc), ya);
-                            yb = f2fma(sc2(jj), f2sub(ring[0][(u + jj) % P], wc), yb);
-                        }
-                    yt[0] = f2mul(d0, f2add(ya, yb));
-                }
+            for (int st = 0; st < NS; ++st) tpass(st, j + 2 * K, zr, (u + 2 * K) % RS);
 #pragma unroll
-                for (int t = 1; t < NT; ++t) {
-                    const float2 wc = ring[t][(u + K) % P];
-                    float2 y = f2mul(sc2(t * P + K), wc);
-#pragma unroll
-                    for (int jj = 0; jj < P; ++jj)
-                        if (jj != K) {
-                            if ((DM >> t) & 1u) y = f2fma(sc2(t * P + jj), f2sub(ring[t][(u + jj) % P], wc), y);
-                            else y = f2fma(sc2(t * P + jj), ring[t][(u + jj) % P], y);
-                        }
-                    yt[t] = y;
-                }
-                // pairwise sum of the term results (independent chains above)
-#pragma unroll
-                for (int s = 1; s < NT; s *= 2)
-#pragma unroll
-                    for (int t = 0; t + s < NT; t += 2 * s) yt[t] = f2add(yt[t], yt[t + s]);
-                const float2 y = yt[0];
-                if (col_ok && j < L) {
-                    *reinterpret_cast<float2*>(LQ + (size_t)(a_lo + j) * a.ld + b) = y;
-                    acc = f2fma(xr0[(u + K) % P], y, acc);
-                    const float2 zc = *reinterpret_cast<const float2*>(
-                        Zs + ((j + K) & (RING - 1)) * WCT + XPAD + 2 * cp);
-                    acz = f2fma(zc, y, acz);
-                }
-            }
+            for (int st = 0; st < NS; ++st) spass(st, j, u, sr, cr);
         }
-        // chunks whose last row (its S rows end at output row (c + 1) CR - 1) is done: refill
-        const int can = min(nch, jend / CR);
+        // chunks whose last row (its S rows end at output row (c + 1) CR - 1) is done: refill,
+        // RELEASE chunks at a time (fewer barriers)
+        int can = min(nch, jend / CR);
+        if (can < nch) can -= (can - released) % G::RELEASE;
         if (can > released) {
             __syncthreads();   // every thread is past the rows of those slots
             if (tid == 0)
                 for (int c = released; c < can; ++c)
-                    if (c + D < nch) issue(c + D);
+                    if (c + D < nch)
+                        for (int st = 0; st < NS; ++st) issue(st, c + D);
             released = can;
         }
     }
     wait_upto(nch);   // every issued copy has landed before the CTA exits
     if (failed) atomicOr(&fail_s, 1);
-    double s = block_sum<NTH>((double)acc.x + (double)acc.y, red);
+    double sacc = block_sum<NTH>((double)acc.x + (double)acc.y, red);
     __syncthreads();   // red[] is reused
-    const double s2 = a.partial2 ? block_sum<NTH>((double)acz.x + (double)acz.y, red) : 0.0;
+    const double s2v = a.partial2 ? block_sum<NTH>((double)acz.x + (double)acz.y, red) : 0.0;
     const int nblk = gridDim.x * gridDim.y;
     if (tid == 0) {
         if (fail_s) atomicOr(a.status, DEV_ERR_TIMEOUT);
-        a.partial[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s;
-        if (a.partial2) a.partial2[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s2;
+        a.partial[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = sacc;
+        if (a.partial2) a.partial2[(size_t)inst * nblk + blockIdx.y * gridDim.x + blockIdx.x] = s2v;
         __threadfence();
         const unsigned t = atomicAdd(a.counter + inst, 1u);
         last_s = (t == (unsigned)nblk - 1) ? 1 : 0;
@@ -329,10 +372,10 @@ __global__ void __launch_bounds__(Geo3<K, NT>::NTH, Geo3<K, NT>::MINB)
     }
 }
 
-// Resident CTAs of the streaming apply on the current device (one wave), per (K, NT).
-template <int K, int NT>
+// Resident CTAs of the streaming apply on the current device (one wave), per form.
+template <int K, int NT, int NS>
 int apply3_ctas_wanted_t() {
-    using G = Geo3<K, NT>;
+    using G = Geo3<K, NT, NS>;
     static std::atomic<int> cache[MOFEM_MAX_DEV];
     const int slot = dev_slot();
     int n = cache[slot].load(std::memory_order_relaxed);
@@ -341,8 +384,8 @@ int apply3_ctas_wanted_t() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
-        smem_attr_once(k_apply_pcg3<K, NT>, (int)G::SMEM, attr_done);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_pcg3<K, NT>, G::NTH, G::SMEM) !=
+        smem_attr_once(k_apply_pcg3<K, NT, NS>, (int)G::SMEM, attr_done);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_pcg3<K, NT, NS>, G::NTH, G::SMEM) !=
                 cudaSuccess ||
             per < 1)
             per = 1;
@@ -355,16 +398,17 @@ int apply3_ctas_wanted_t() {
 template <int K, int NT>
 mofem_status launch_pcg3_t(const CUtensorMap& mZ, const CUtensorMap& mQ, const CUtensorMap& mS,
                            const ApplyPcgArgs& a, int batch, cudaStream_t st) {
-    using G = Geo3<K, NT>;
-    auto kern = k_apply_pcg3<K, NT>;
+    constexpr int NS = packed_streams(K, NT);
+    using G = Geo3<K, NT, NS>;
+    auto kern = k_apply_pcg3<K, NT, NS>;
     static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
     MOFEM_CUDA_TRY(smem_attr_once(kern, (int)G::SMEM, attr_done));
     const int strips = (a.q + TB - 1) / TB;
-    const int segs = apply3_segments(a.q, strips, batch, apply3_ctas_wanted_t<K, NT>(), K);
-    constexpr int P = 2 * K + 1;   // segments of whole row blocks: only the last one is ragged
-    const int seg_rows = ((a.q + segs - 1) / segs + P - 1) / P * P;
+    const int segs = apply3_segments(a.q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>(), K, NS);
+    constexpr int P = 2 * K + 1;   // streams of whole row blocks: only the last one is ragged
+    const int srows = ((a.q + segs * NS - 1) / (segs * NS) + P - 1) / P * P;
     dim3 grid(strips, segs, batch);
-    kern<<<grid, G::NTH, G::SMEM, st>>>(mZ, mQ, mS, a, seg_rows);
+    kern<<<grid, G::NTH, G::SMEM, st>>>(mZ, mQ, mS, a, srows);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }
