@@ -268,6 +268,7 @@ def measure_batching(full=False):
     t0 = time.perf_counter()
     chosen = g.autotune(F, U, rtol=1e-10)
     t_tune = time.perf_counter() - t0
+    apply_tile_div = g.tuning()[1]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record()
@@ -279,7 +280,10 @@ def measure_batching(full=False):
     g.close()
     return {"workload": f"{count} Dirichlet elliptic problems, n in {list(nch)} (k = 3: n adjusted), k in 1..4, "
                         f"gamma ~ U[0,10], g2 = 1 + a sin(2 pi b x), Fourier f, rtol 1e-10",
-            "groups": n_groups, "concurrency_chosen": chosen, "status": code, "setup_s": t_setup,
+            "groups": n_groups, "concurrency_chosen": chosen,
+            "mode": "lockstep (one graph, one tensor-core launch per iteration for all groups)" if chosen == -1
+                    else f"groups apart, {chosen} in flight",
+            "apply_tile_div_chosen": apply_tile_div, "status": code, "setup_s": t_setup,
             "autotune_s": t_tune, "solve_ms": ms, "problems_per_s": count / (ms / 1e3),
             "max_rel_residual": max(i.rel_residual for i in infos),
             "check": "per-problem solutions vs the FP64 oracle: tests/test_gpu_group.py"}

@@ -350,17 +350,23 @@ mofem_status mofem_group_solve(mofem_group g, const double* const* F, double* co
                                int max_iter, mofem_precision prec, mofem_solve_info* infos, cudaStream_t stream);
 
 /* Run-time tuning of how the groups run: one warm-up solve of each way, then one
- * timed solve per candidate (lockstep for the mixed forms; apart with 1, 2, 4, 8,
- * 16 or all groups in flight), each from the caller's initial guesses; the fastest
- * is kept for later solves and written to *chosen (may be NULL): -1 lockstep, else
- * the number of groups in flight.  U holds the caller's initial guesses again on
- * return. */
+ * timed solve per candidate (lockstep for the mixed forms, with the operator-apply
+ * tiles one wave of CTAs high or half of that; apart with 1, 2, 4, 8, 16 or all
+ * groups in flight), each from the caller's initial guesses; the fastest is kept for
+ * later solves and written to *chosen (may be NULL): -1 lockstep, else the number of
+ * groups in flight (mofem_group_get_tuning also reports the tile height).  U holds
+ * the caller's initial guesses again on return. */
 mofem_status mofem_group_autotune(mofem_group g, const double* const* F, double* const* U, double rtol,
                                   int max_iter, mofem_precision prec, int* chosen);
 
 /* Choose how later solves run: -1 lockstep (the default), 0 apart with all groups in
  * flight, m > 0 apart with m groups in flight. */
 mofem_status mofem_group_set_mode(mofem_group g, int mode);
+
+/* The way later solves run (as mofem_group_set_mode) and the operator-apply tile height
+ * the autotuner chose: rows per CTA of one wave of resident CTAs divided by
+ * *apply_tile_div (1 or 2).  Either pointer may be NULL. */
+mofem_status mofem_group_get_tuning(mofem_group g, int* mode, int* apply_tile_div);
 
 mofem_status mofem_group_destroy(mofem_group g);
 

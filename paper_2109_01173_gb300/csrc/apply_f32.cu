@@ -102,10 +102,13 @@ int apply_pcg_s_box_rows() { return Geo3<2, 5, 1>::CR; }
 // 2 * SR2 of Geo3: the duplicated S row, a multiple of 4 float2 (32-byte rows)
 int apply_s2_row_floats(int K, int nt) { return 2 * (((nt * (2 * K + 1) + 3) / 4) * 4); }
 
+// (the largest tile-height divisor the handles use: partial slots are sized for it)
+constexpr int APPLY_SEG_DIV_MAX = 2;
+
 template <int K, int NT>
 static int segs_k(int q, int strips, int batch) {
     constexpr int NS = packed_streams(K, NT);
-    return apply3_segments(q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>(), K, NS);
+    return apply3_segments(q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>() * APPLY_SEG_DIV_MAX, K, NS);
 }
 
 template <int K>

@@ -404,7 +404,7 @@ mofem_status launch_pcg3_t(const CUtensorMap& mZ, const CUtensorMap& mQ, const C
     static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
     MOFEM_CUDA_TRY(smem_attr_once(kern, (int)G::SMEM, attr_done));
     const int strips = (a.q + TB - 1) / TB;
-    const int segs = apply3_segments(a.q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>(), K, NS);
+    const int segs = apply3_segments(a.q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>() * max(1, a.seg_div), K, NS);
     constexpr int P = 2 * K + 1;   // streams of whole row blocks: only the last one is ragged
     const int srows = ((a.q + segs * NS - 1) / (segs * NS) + P - 1) / P * P;
     dim3 grid(strips, segs, batch);

@@ -27,6 +27,7 @@ struct mofem_group_ctx {
     int count = 0;
     int concurrency = -1;             // -1: all groups in lockstep (one graph, one GEMM launch per
                                       // iteration); else groups solved apart, this many at once (0: all)
+    int apply_tile_div = 1;           // operator-apply tile height of every group: one wave of CTAs / this
     std::vector<Group> groups;
     FusedState fused;                 // lockstep graph and descriptors, kept between solves
     cudaStream_t st = nullptr;        // the lockstep solve's stream
@@ -237,11 +238,25 @@ extern "C" mofem_status mofem_group_autotune(mofem_group g, const double* const*
                                              int max_iter, mofem_precision prec, int* chosen) {
     if (!g) return MOFEM_ERR_INVALID_ARG;
     const int ng = (int)g->groups.size();
-    std::vector<int> cand;
-    if (prec != MOFEM_FP64) cand.push_back(-1);   // lockstep: one graph, one GEMM launch per iteration
+    // candidates (mode, apply tile divisor): lockstep with one-wave or half-height apply tiles
+    // (the mixed forms), then the groups apart, 1 .. all in flight
+    std::vector<std::pair<int, int>> cand;
+    if (prec != MOFEM_FP64) {
+        cand.push_back({-1, 1});
+        cand.push_back({-1, 2});
+    }
     for (int c : {1, 2, 4, 8, 16})
-        if (c < ng) cand.push_back(c);
-    cand.push_back(ng);
+        if (c < ng) cand.push_back({c, 1});
+    cand.push_back({ng, 1});
+    auto set_tile = [&](int div) {
+        if (div == g->apply_tile_div) return;
+        g->apply_tile_div = div;
+        for (auto& gr : g->groups) set_apply_seg_div(gr.h, div);
+        if (g->fused.loop) {   // the lockstep graph holds the old apply grids
+            cudaGraphExecDestroy(g->fused.loop);
+            g->fused.loop = nullptr;
+        }
+    };
     // every candidate starts from the caller's initial guesses (saved here)
     std::vector<size_t> off(g->count + 1, 0);
     for (auto& gr : g->groups)
@@ -265,10 +280,16 @@ extern "C" mofem_status mofem_group_autotune(mofem_group g, const double* const*
         s = mofem_group_solve(g, F, U, rtol, max_iter, prec, nullptr, nullptr);
     }
     double best = 1e300;
-    int best_c = ng;
+    std::pair<int, int> best_c{ng, 1};
     for (size_t ci = 0; ci < cand.size() && (s == MOFEM_OK || s == MOFEM_ERR_NOT_CONVERGED); ++ci) {
         copy_all(false);
-        g->concurrency = cand[ci];
+        g->concurrency = cand[ci].first;
+        set_tile(cand[ci].second);
+        if (cand[ci].second != 1) {   // a new tile height: one untimed solve builds its graphs
+            s = mofem_group_solve(g, F, U, rtol, max_iter, prec, nullptr, nullptr);
+            copy_all(false);
+            if (s != MOFEM_OK && s != MOFEM_ERR_NOT_CONVERGED) break;
+        }
         const auto t0 = std::chrono::steady_clock::now();
         s = mofem_group_solve(g, F, U, rtol, max_iter, prec, nullptr, nullptr);
         const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -279,14 +300,22 @@ extern "C" mofem_status mofem_group_autotune(mofem_group g, const double* const*
     }
     copy_all(false);
     cudaFree(save);
-    g->concurrency = best_c;
-    if (chosen) *chosen = best_c;
+    g->concurrency = best_c.first;
+    set_tile(best_c.second);
+    if (chosen) *chosen = best_c.first;
     return (s == MOFEM_OK || s == MOFEM_ERR_NOT_CONVERGED) ? MOFEM_OK : s;
 }
 
 extern "C" mofem_status mofem_group_set_mode(mofem_group g, int mode) {
     if (!g || mode < -1) return MOFEM_ERR_INVALID_ARG;
     g->concurrency = mode;
+    return MOFEM_OK;
+}
+
+extern "C" mofem_status mofem_group_get_tuning(mofem_group g, int* mode, int* apply_tile_div) {
+    if (!g) return MOFEM_ERR_INVALID_ARG;
+    if (mode) *mode = g->concurrency;
+    if (apply_tile_div) *apply_tile_div = g->apply_tile_div;
     return MOFEM_OK;
 }
 

@@ -66,6 +66,7 @@ struct mofem_ctx {
     mofem_opts opts{};
     int ld = 0;                  // leading dimension of internal q x q matrices (multiple of 64)
     int div_product = 0;         // preconditioner divisor: lambda_a * mu_b (product form) instead of lambda_a + mu_b
+    int apply_seg_div = 1;       // operator-apply tile height: rows per CTA of one wave / apply_seg_div (tuned)
     int off = 1;                 // node index of trimmed row 0 (1 Dirichlet, 0 Neumann)
     std::vector<double> gamma;   // per instance
     int dev = 0;
@@ -174,6 +175,7 @@ struct ApplyPcgArgs {
     double* partial2;   // packed FP32 apply: per-CTA <L(Q), Z>, finalised into rzo = rz - alpha <L(Q), Z> (or null)
     PcgScalars* sc; int use_sc;
     int* status;
+    int seg_div;   // streaming apply: segments per strip x seg_div (1: one wave of CTAs; 0 reads as 1)
 };
 mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const double* beta, const double* rz,
                            void* Q, void* LQ, int ld, double* alpha, bool fp64, cudaStream_t st);
@@ -317,6 +319,7 @@ struct FusedState {
     bool fixed = false;
 };
 void fused_free(FusedState* f);
+mofem_status set_apply_seg_div(mofem_ctx* c, int div);
 // Solve the problems of G handles (one right-hand side and one U per handle, layouts as
 // mofem_pcg_solve) in lockstep; mixed forms only (MOFEM_ERR_UNSUPPORTED otherwise, and when
 // an FP16 inner solve needs the TF32 retry: the caller then solves the groups apart).

@@ -347,6 +347,7 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     a.partial2 = packed ? c->part.lqz : nullptr;
     a.sc = c->d_sc; a.use_sc = 1;
     a.status = c->d_status;
+    a.seg_div = c->apply_seg_div;
     MOFEM_TRY(launch_apply_pcg(c->K, c->NT, fp64, *mZ, *mQp, fp64 ? nullptr : &e.mS32, a, c->batch, st));
     // 2) R -= alpha LQ ; U += alpha Q (mixed: lazily, two iterations at a time) ; convergence
     //    (last CTA) ; graph condition
@@ -753,6 +754,22 @@ static mofem_status solve_core(mofem_ctx* c, double* U, long long u_bs, int u_ld
 }
 
 mofem_status solver_init(mofem_ctx* c, cudaStream_t st) { return ensure_common(c, st); }
+
+// Operator-apply tile height (rows per CTA of one wave / div, div in 1..2).  The captured
+// iteration graphs hold the old grid, so they are dropped and rebuilt on next use.
+mofem_status set_apply_seg_div(mofem_ctx* c, int div) {
+    if (div < 1 || div > 2) return MOFEM_ERR_INVALID_ARG;
+    if (c->apply_seg_div == div) return MOFEM_OK;
+    c->apply_seg_div = div;
+    for (int i = 0; i < 4; ++i) {
+        if (c->it_graph[i]) cudaGraphExecDestroy(c->it_graph[i]);
+        if (c->loop_graph[i]) cudaGraphExecDestroy(c->loop_graph[i]);
+        c->it_graph[i] = nullptr;
+        c->loop_graph[i] = nullptr;
+        c->it_graph_max_iter[i] = 0;
+    }
+    return MOFEM_OK;
+}
 
 // ---- heterogeneous batches in lockstep ------------------------------------------------
 // Groups of different (k, n, bc) iterate together: one CUDA graph per inner solve whose
@@ -1212,6 +1229,7 @@ mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const do
     a.partial = c->part.qlq; a.counter = c->d_ctr + 3 * B;
     a.sc = e.dir_sc; a.use_sc = 1;
     a.status = c->d_status;
+    a.seg_div = c->apply_seg_div;
     MOFEM_TRY(launch_apply_pcg(c->K, c->NT, fp64, mZ, mQ, packed ? &mS : nullptr, a, B, st));
     MOFEM_CUDA_TRY(cudaMemcpyAsync(h.data(), e.dir_sc, sizeof(PcgScalars) * B, cudaMemcpyDeviceToHost, st));
     int dev_status = 0;
@@ -1256,6 +1274,7 @@ mofem_status bench_kernel(mofem_ctx* c, int kernel, mofem_precision prec, int re
         a.partial = c->part.qlq; a.counter = c->d_ctr + 3 * c->batch;
         a.sc = c->d_sc; a.use_sc = 0;
         a.status = c->d_status;
+        a.seg_div = c->apply_seg_div;
         for (int r = 0; r < reps; ++r)
             MOFEM_TRY(launch_apply_pcg(c->K, c->NT, false, e.mZ32, e.mQB32, &e.mS32, a, c->batch, st));
         return MOFEM_OK;

@@ -88,6 +88,7 @@ def _load():
         "mofem_group_autotune": [vp, P(vp), P(vp), c_double, c_int, c_int, P(c_int)],
         "mofem_group_destroy": [vp],
         "mofem_group_set_mode": [vp, c_int],
+        "mofem_group_get_tuning": [vp, P(c_int), P(c_int)],
         "mofem_dib_run": [vp, P(DibParams), c_double, c_double, c_int, vp, c_double, c_int, P(c_double),
                           P(SolveInfo), vp],
         "mofem_imex_adjoint_step": [vp, c_double, c_double, vp, vp, vp, vp, P(c_double), c_double, c_int, P(SolveInfo),
@@ -119,7 +120,7 @@ EXPORTED = ["mofem_setup", "mofem_setup_batched", "mofem_get_dims", "mofem_apply
             "mofem_pcg_direction", "mofem_imex_step_tol", "mofem_imex_adjoint_step", "mofem_rds_step",
             "mofem_dib_kinetics", "mofem_dib_run", "mofem_dib_equilibrium", "mofem_group_layout",
             "mofem_group_setup", "mofem_group_solve", "mofem_group_autotune", "mofem_group_destroy",
-            "mofem_group_set_mode",
+            "mofem_group_set_mode", "mofem_group_get_tuning",
             "mofem_pcg_solve", "mofem_imex_step", "mofem_destroy", "mofem_status_string", "mofem_last_error",
             "mofem_host_tables", "mofem_host_dd_tables", "mofem_bench_kernel", "mofem_get_eigen",
             "mofem_imex_step_src", "mofem_imex_adjoint_step_src"]
@@ -424,6 +425,12 @@ class Group:
         """-1: lockstep (one graph, one tensor-core launch per iteration for all groups);
         0: groups apart, all in flight; m > 0: apart, m in flight."""
         _check("mofem_group_set_mode", LIB.mofem_group_set_mode(self.g, int(mode)))
+
+    def tuning(self):
+        """(mode, operator-apply tile divisor) the later solves use."""
+        m, d = ctypes.c_int(), ctypes.c_int()
+        _check("mofem_group_get_tuning", LIB.mofem_group_get_tuning(self.g, ctypes.byref(m), ctypes.byref(d)))
+        return m.value, d.value
 
     def autotune(self, F, U, rtol=1e-10, max_iter=500, precision="fp16"):
         chosen = ctypes.c_int()
