@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MO-PCG solves/s and ms/iter, P2 N=2049 (mixed vs FP64 GPU form, rel.err<=1e-8)"
 # DRAM bytes per chained preconditioner launch (G1..G4) at P2 2049 x 4 (ncu capture of the
 # current kernel; None whenever k_gemm_2sm changes until it is captured again)
-CHAIN_DRAM_BYTES = 329.1e6
+CHAIN_DRAM_BYTES = None
 UNIT = "solves/s"
 
 
@@ -622,7 +622,7 @@ def run_mofem(a):
                                     + (" / 2 for TF32" if prec_k == "tf32" else ""),
                      "per_gemm_us": [round(t * 1e6, 2) for t in t_gemm],
                      "per_gemm_tflops": [round(x, 1) for x in gemm_tflops]},
-        "roofline_apply": {"bound": "hbm", "kernel": (f"k_apply_pcg2<K={k},NT=5> (packed FP32, PCG form)" if k <= 3 else
+        "roofline_apply": {"bound": "hbm", "kernel": (f"k_apply_pcg3<K={k},NT=5> (streaming packed FP32, PCG form)" if k <= 3 else
                                       f"k_apply_pcg<float,K={k},NT=5> (scalar FP32, PCG form)"),
                            "achieved": apply_bytes / t_apply / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                            "frac": apply_bytes / t_apply / 1e9 / peaks["hbm_gbs"], "us": t_apply * 1e6},

@@ -252,6 +252,132 @@ __device__ __forceinline__ void epi_chunk(const GemmArgs& g, int inst, int m, in
 }
 
 // ---------------------------------------------------------------------------
+// TMA-store epilogue.  Each epilogue warp owns 32 output rows of the CTA's 128; it stages
+// one block of 128-byte rows (32 FP32 or 64 16-bit columns) in a shared-memory buffer
+// whose 16-byte chunks are XOR-swizzled by (row & 7) (the SWIZZLE_128B layout of the
+// store's tensor map, so the writes of 8 consecutive rows hit all 32 banks), and one lane
+// stores the block with cp.async.bulk.tensor: full 128-byte lines instead of 32 scattered
+// 16-byte row pieces per warp store; the map clips rows and columns past the matrix.  Two
+// buffers per warp alternate; a buffer is rewritten only after the store issued from it
+// two blocks earlier has read it.
+constexpr int EPI_STAGE_BYTES = 4096;   // 32 rows x 128 bytes per warp and buffer
+constexpr int EPI_STAGE_TOTAL = 4 * 2 * EPI_STAGE_BYTES;
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Epilogue arithmetic of one 32-column chunk of row m (no store): divide (G2), unscale
+// and <R, Z> accumulation (G4).  Same operations and order as epi_chunk.
+template <int EPI>
+__device__ __forceinline__ void epi_math(const GemmArgs& g, int inst, int m, int nb, float (&v)[32], float mu_m,
+                                         float inv_scale, double& acc) {
+    if constexpr (EPI == EPI_DIV) {
+        const float4* lam4 = reinterpret_cast<const float4*>(g.lam + (size_t)inst * g.lam_bs + nb);
+        float lam[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 t = __ldg(lam4 + j);
+            lam[4 * j] = t.x; lam[4 * j + 1] = t.y; lam[4 * j + 2] = t.z; lam[4 * j + 3] = t.w;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __fdividef(v[j], g.div_product ? lam[j] * mu_m : lam[j] + mu_m);
+    }
+    if constexpr (EPI == EPI_Z) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] *= inv_scale;
+        if (g.R) {
+            const float* r = g.R + (size_t)inst * g.r_bs + (size_t)m * g.r_ld + nb;
+            float a32 = 0.f;   // FP32 within the 32-column chunk, FP64 across chunks
+            if (nb + 32 <= g.N && (g.r_ld % 4) == 0) {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 rv = *reinterpret_cast<const float4*>(r + j);
+                    a32 = fmaf(v[j], rv.x, a32);
+                    a32 = fmaf(v[j + 1], rv.y, a32);
+                    a32 = fmaf(v[j + 2], rv.z, a32);
+                    a32 = fmaf(v[j + 3], rv.w, a32);
+                }
+            } else {
+                for (int j = 0; j < 32 && nb + j < g.N; ++j) a32 = fmaf(v[j], r[j], a32);
+            }
+            acc += (double)a32;
+        }
+    }
+}
+
+// Row `lane` of a staged block: the half-th 32-column chunk of it (half = 0 for FP32
+// blocks, 0 or 1 for 16-bit ones), 16-byte pieces swizzled by (lane & 7).
+template <int OUTK>
+__device__ __forceinline__ void stage_chunk(uint8_t* buf, int lane, int half, const float (&v)[32]) {
+    uint4* row = reinterpret_cast<uint4*>(buf + lane * 128);
+    const int sw = lane & 7;
+    if constexpr (OUTK == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            row[k ^ sw] = make_uint4(__float_as_uint(v[4 * k]), __float_as_uint(v[4 * k + 1]),
+                                     __float_as_uint(v[4 * k + 2]), __float_as_uint(v[4 * k + 3]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float a = v[8 * k + 2 * e], b = v[8 * k + 2 * e + 1];
+                if constexpr (OUTK == 2) {   // FP16 intermediates: saturate instead of overflowing to inf
+                    a = fminf(fmaxf(a, -65504.f), 65504.f);
+                    b = fminf(fmaxf(b, -65504.f), 65504.f);
+                    __half2 t = __floats2half2_rn(a, b);
+                    w[e] = *reinterpret_cast<uint32_t*>(&t);
+                } else {
+                    __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+                    w[e] = *reinterpret_cast<uint32_t*>(&t);
+                }
+            }
+            row[(half * 4 + k) ^ sw] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// The whole 256-column tile row block of this warp through the staging buffers.
+template <int EPI, int OUTK>
+__device__ __forceinline__ void epi_tile_tma(const GemmArgs& g, const CUtensorMap* omap, uint32_t tm, int inst,
+                                             int m, bool m_ok, int m_warp0, int n0, float mu_m, float inv_scale,
+                                             double& acc, uint8_t* stage, int warp, int lane, int& nst) {
+    constexpr int W = OUTK == 0 ? 32 : 64;   // columns per 128-byte staged row
+#pragma unroll 1
+    for (int blk = 0; blk < 256 / W; ++blk) {
+        if (nst >= 2) {   // the store issued from this buffer two blocks ago has read it
+            if (lane == 0) bulk_wait_read1();
+            __syncwarp();
+        }
+        uint8_t* buf = stage + (warp * 2 + (nst & 1)) * EPI_STAGE_BYTES;
+#pragma unroll
+        for (int h = 0; h < W / 32; ++h) {
+            const int c = blk * (W / 32) + h;
+            float v[32];
+            tmem_ld32(tm + (uint32_t)(c * 32), v);
+            const int nb = n0 + c * 32;
+            if (m_ok && nb < g.N) epi_math<EPI>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+            stage_chunk<OUTK>(buf, lane, h, v);
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            tma_store_3d(omap, smem_u32(buf), n0 + blk * W, m_warp0, inst);
+            bulk_commit();
+        }
+        ++nst;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_gemm_2sm: each 2-CTA cluster computes one 256 x 256 tile with
 // tcgen05.mma.cta_group::2 (M = 256 across the pair, N = 256).  CTA r holds rows
 // 128 r .. 128 r + 127 of the A slice and of the B slice of every K step in its
@@ -341,6 +467,8 @@ __device__ __forceinline__ void commit2_mc(uint32_t mbar, uint16_t mask) {
 constexpr int CHAIN_MAX = 4;
 struct GemmChain {
     CUtensorMap mA[CHAIN_MAX], mB[CHAIN_MAX];
+    CUtensorMap mO[CHAIN_MAX];   // output maps of the TMA-store epilogue (128-byte swizzled rows)
+    int ostore[CHAIN_MAX];       // 1: the stage's output leaves through shared memory by TMA stores
     GemmArgs g[CHAIN_MAX];   // per stage; M, N, nk, batch, sc and status are the same in all
     int dep[CHAIN_MAX];      // operand from stage s-1: 0 none, 1 the A rows (panel = tile row),
                              // 2 the B rows (panel = tile column)
@@ -641,6 +769,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
         }
     } else {   // ---- epilogue warps 0-3 (both CTAs): thread = TMEM lane = output row
         int tl = 0;
+        int nst = 0;   // TMA stores this warp has issued (staging buffers alternate)
+        uint8_t* stage = reinterpret_cast<uint8_t*>(
+            (reinterpret_cast<uintptr_t>(smem + ST2 * STAGE2_BYTES + sizeof(PBars2)) + 1023) & ~(uintptr_t)1023);
         for (int j = 0;; ++j) {
             int u;
             if (dyn) {
@@ -682,15 +813,31 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
             if (epi == EPI_DIV && m_ok) mu_m = g.mu[m];
             const float inv_scale = (epi == EPI_Z && g.scl) ? (float)(1.0 / g.scl[inst].rscale) : 1.f;
             double acc = 0.0;
+            const uint32_t tm = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256);
+            const bool tma_out = C.ostore[stg] != 0;
+            if (tma_out) {
+                const CUtensorMap* om = &C.mO[stg];
+                const int mw = m0 + warp * 32;
+                if (epi == EPI_DIV)
+                    epi_tile_tma<EPI_DIV, KIND>(g, om, tm, inst, m, m_ok, mw, n0, mu_m, inv_scale, acc, stage, warp,
+                                                lane, nst);
+                else if (epi == EPI_Z)
+                    epi_tile_tma<EPI_Z, 0>(g, om, tm, inst, m, m_ok, mw, n0, mu_m, inv_scale, acc, stage, warp, lane,
+                                           nst);
+                else
+                    epi_tile_tma<EPI_STORE, KIND>(g, om, tm, inst, m, m_ok, mw, n0, mu_m, inv_scale, acc, stage,
+                                                  warp, lane, nst);
+            } else {
 #pragma unroll 1
-            for (int c = 0; c < 256 / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 256 + c * 32), v);
-                const int nb = n0 + c * 32;
-                if (m_ok && nb < g.N) {
-                    if (epi == EPI_DIV) epi_chunk<EPI_DIV, KIND>(g, inst, m, nb, v, mu_m, inv_scale, acc);
-                    else if (epi == EPI_Z) epi_chunk<EPI_Z, 0>(g, inst, m, nb, v, mu_m, inv_scale, acc);
-                    else epi_chunk<EPI_STORE, KIND>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                for (int c = 0; c < 256 / 32; ++c) {
+                    float v[32];
+                    tmem_ld32(tm + (uint32_t)(c * 32), v);
+                    const int nb = n0 + c * 32;
+                    if (m_ok && nb < g.N) {
+                        if (epi == EPI_DIV) epi_chunk<EPI_DIV, KIND>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                        else if (epi == EPI_Z) epi_chunk<EPI_Z, 0>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                        else epi_chunk<EPI_STORE, KIND>(g, inst, m, nb, v, mu_m, inv_scale, acc);
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -698,7 +845,12 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
             if (lane == 0) mbar_arrive_cluster(mapa_shared(bar_addr(&pb->tempty[b]), 0));
             if (stg + 1 < C.ns && C.dep[stg + 1] && C.panel_cnt) {
                 // publish this warp's 32 rows of the tile to the next stage's TMA reads
-                // (4 warps x 2 CTAs per tile: a panel of ntn tiles is complete at 8 ntn)
+                // (4 warps x 2 CTAs per tile: a panel of ntn tiles is complete at 8 ntn);
+                // TMA-stored rows first complete their stores
+                if (tma_out) {
+                    if (lane == 0) bulk_wait_all();
+                    __syncwarp();
+                }
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __threadfence();
                 __syncwarp();
@@ -741,6 +893,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_gemm_2sm(const __grid_constant
             }
             ++tl;
         }
+        if (lane == 0) bulk_wait_all();   // staged rows stored before the shared memory is released
     }
     __syncthreads();
     cluster_sync_all();   // the peer's copies, commits and arrivals have all landed
@@ -873,7 +1026,7 @@ mofem_status launch_chain(const GemmChain& ch0, int batch, cudaStream_t st) {
     static std::atomic<int> max_pairs_dev[MOFEM_MAX_DEV];   // per device: co-resident pairs
     std::atomic<int>& max_pairs_slot = max_pairs_dev[dev_slot()];
     int max_pairs = max_pairs_slot.load(std::memory_order_acquire);
-    const int smem = ST2 * STAGE2_BYTES + 1024 + (int)sizeof(PBars2) + 64;
+    const int smem = ST2 * STAGE2_BYTES + 1024 + (int)sizeof(PBars2) + 1024 + EPI_STAGE_TOTAL;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1016,6 +1169,10 @@ mofem_status tc_prepare(mofem_ctx* c, int which, cudaStream_t st) {
     MOFEM_TRY(make_map(&p.mB[2], p.WT, es, q, q, B, ld, BN / 2, f16));
     MOFEM_TRY(make_map(&p.mA[3], p.Y, es, q, q, B, ld, BM, f16));
     MOFEM_TRY(make_map(&p.mB[3], p.Q2, es, q, q, 1, ld, BN / 2, f16));
+    // output maps of the TMA-store epilogue: 32-row boxes of one 128-byte swizzled row block
+    MOFEM_TRY(make_map(&p.mO[0], p.X1T, es, q, q, B, ld, 32, f16));
+    MOFEM_TRY(make_map(&p.mO[1], p.WT, es, q, q, B, ld, 32, f16));
+    MOFEM_TRY(make_map(&p.mO[2], p.Y, es, q, q, B, ld, 32, f16));
     p.ready = true;
     return MOFEM_OK;
 }
@@ -1088,6 +1245,14 @@ static GemmChain tc_chain(const mofem_ctx* c, int which, const float* R32, long 
     ch.unit_ctr = p.panel_cnt + p.n_panel_cnt + 1;
     ch.mode = p.panel_cnt + p.n_panel_cnt + 2;
     for (int s = 0; s < 4; ++s) ch.g[s].batch = c->batch;
+    // TMA-store epilogue: the intermediates always; Z where its rows are 16-byte aligned
+    for (int s = 0; s < 3; ++s) {
+        ch.mO[s] = p.mO[s];
+        ch.ostore[s] = 1;
+    }
+    const bool z_aligned = (reinterpret_cast<uintptr_t>(Z) % 16) == 0 && ((long long)z_ld * 4) % 16 == 0 &&
+                           (z_bs * 4) % 16 == 0 && z_bs == (long long)z_ld * q;
+    ch.ostore[3] = (z_aligned && make_map(&ch.mO[3], Z, 4, q, q, c->batch, z_ld, 32) == MOFEM_OK) ? 1 : 0;
     return ch;
 }
 

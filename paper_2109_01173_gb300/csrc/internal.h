@@ -58,6 +58,7 @@ struct TcPlan {                 // one tensor-core precision (BF16 or TF32)
     unsigned* panel_cnt = nullptr;  // GEMM-chain panel counters [3][batch][panels] + end ticket
     int n_panel_cnt = 0;
     CUtensorMap mA[4], mB[4];
+    CUtensorMap mO[3];          // TMA-store maps of the intermediates X1T, WT, Y
 };
 
 struct mofem_ctx {
