@@ -96,11 +96,11 @@ int apply_pcg_box_rows(int K, int nt, bool fp64) {
     return apply_pcg_rows_per_cta(K, nt, fp64) + 2 * K;
 }
 
-// Rows of one TMA box of the duplicated S rows (streaming apply).
+// Rows of one TMA box of the S rows (streaming apply).
 int apply_pcg_s_box_rows() { return Geo3<2, 5, 1>::CR; }
 
-// 2 * SR2 of Geo3: the duplicated S row, a multiple of 4 float2 (32-byte rows)
-int apply_s2_row_floats(int K, int nt) { return 2 * (((nt * (2 * K + 1) + 3) / 4) * 4); }
+// SR of Geo3: floats per S row, the NT (2K + 1) coefficients padded to a multiple of 8
+int apply_s_row_floats(int K, int nt) { return ((nt * (2 * K + 1) + 7) / 8) * 8; }
 
 // (the largest tile-height divisor the handles use: partial slots are sized for it)
 constexpr int APPLY_SEG_DIV_MAX = 2;

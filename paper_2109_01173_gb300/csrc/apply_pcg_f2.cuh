@@ -20,8 +20,10 @@
 //     X = Z + beta Q_prev is formed on the fly from both staged rows and the owned
 //     rows of the new direction are written from registers;
 //   * the s-pass coefficients come from a copy of the S tables laid out per row
-//     with every coefficient duplicated into both lanes of a float2, so a
-//     shared-memory broadcast feeds a paired FMA directly.
+//     (the NT (2K + 1) coefficients of a row contiguous, the row padded to a
+//     multiple of 8 floats); a shared-memory read delivers 128 bytes per
+//     wavefront whether or not the lanes share the address, so each lane reads
+//     every coefficient once and pairs it in registers for the paired FMAs.
 //
 // Fused epilogue: per-CTA FP64 partials of <X, L(X)> and <L(X), Z> and, in the
 // last CTA of each instance, alpha = <R, Z> / <Q, L(Q)> and the flexible-beta
@@ -45,13 +47,13 @@ struct Geo3 {
     // the two can overlap; rows are unrolled by RSLOT.  Where the chunk ring is too short
     // for the longer block, the stencil's own 2K + 1.
     static constexpr int RSLOT = (D - RELEASE) * CR >= 4 * K + 1 ? P + 1 : P;
-    static constexpr int SR2 = ((NT * P + 3) / 4) * 4;   // float2 per duplicated S row (a chunk of S rows
+    static constexpr int SR = ((NT * P + 7) / 8) * 8;    // floats per S row (a chunk of CR = 4 S rows
                                                          // stays a 128-byte multiple)
     static constexpr bool TREG = NT * P <= 25;           // T coefficients in registers, else shared
     static constexpr int KE = K + (K & 1);               // left reach rounded to an even column
     static constexpr int ZCH = CR * WCT;                 // floats per chunk of Z (and of Q_prev)
-    static constexpr int SCH = CR * SR2;                 // float2 per chunk of S rows
-    static constexpr uint32_t CHUNK_BYTES = 2u * ZCH * 4u + (uint32_t)SCH * 8u;
+    static constexpr int SCH = CR * SR;                  // floats per chunk of S rows
+    static constexpr uint32_t CHUNK_BYTES = 2u * ZCH * 4u + (uint32_t)SCH * 4u;
     static constexpr uint32_t STREAM_BYTES = (uint32_t)D * CHUNK_BYTES;
     static constexpr size_t SMEM = (size_t)NS * STREAM_BYTES + (TREG ? 0 : (size_t)NT * P * NTH * 8) + 128;
     // register budget: the T coefficients (in registers when TREG) serve every stream of
@@ -59,7 +61,7 @@ struct Geo3 {
     // streams 255 (4 CTAs)
     static constexpr int MINB = NS == 1 ? (TREG ? 5 : 4) : 4;
     static_assert((RING & (RING - 1)) == 0, "ring rows must be a power of two");
-    static_assert((ZCH * 4) % 128 == 0 && (SCH * 8) % 128 == 0, "TMA destinations stay 128-byte aligned");
+    static_assert((ZCH * 4) % 128 == 0 && (SCH * 4) % 128 == 0, "TMA destinations stay 128-byte aligned");
     // a chunk is refilled only after its last row is done, RELEASE chunks at a time; the rows
     // that wait for it must not be the ones that release it:
     // (D - RELEASE) CR >= 2K (t-pass reach) + RSLOT - 1 (unrolled block)
@@ -102,15 +104,15 @@ __global__ void __launch_bounds__(Geo3<K, NT, NS>::NTH, Geo3<K, NT, NS>::MINB)
     k_apply_pcg3(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mQ,
                  const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a, int srows) {
     using G = Geo3<K, NT, NS>;
-    constexpr int P = G::P, SR2 = G::SR2, KE = G::KE, CR = G::CR, D = G::D, RING = G::RING, NTH = G::NTH;
+    constexpr int P = G::P, SR = G::SR, KE = G::KE, CR = G::CR, D = G::D, RING = G::RING, NTH = G::NTH;
     constexpr unsigned DM = DiffMask<NT>::value;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sbase =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-    // stream s: Z ring [RING][WCT], Q_prev ring [RING][WCT], S ring [RING][SR2]
+    // stream s: Z ring [RING][WCT], Q_prev ring [RING][WCT], S ring [RING][SR]
     auto Zs = [&](int st) { return reinterpret_cast<float*>(sbase + st * G::STREAM_BYTES); };
     auto Qs = [&](int st) { return Zs(st) + RING * WCT; };
-    auto S2s = [&](int st) { return reinterpret_cast<float2*>(Qs(st) + RING * WCT); };
+    auto Ss = [&](int st) { return Qs(st) + RING * WCT; };
     float2* T2s = reinterpret_cast<float2*>(sbase + NS * G::STREAM_BYTES);   // [NT*P][NTH] (!TREG)
     __shared__ __align__(8) unsigned long long bar[NS][D];
     __shared__ double red[NTH / 32];
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(Geo3<K, NT, NS>::NTH, Geo3<K, NT, NS>::MINB)
                      : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(S2s(st) + slot * G::SCH)), "l"(ps), "r"(bb), "r"(0), "r"(a_lo[st] + c * CR), "r"(inst)
+            ::"r"(smem_u32(Ss(st) + slot * G::SCH)), "l"(ps), "r"(bb), "r"(0), "r"(a_lo[st] + c * CR), "r"(inst)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
@@ -262,10 +264,11 @@ __global__ void __launch_bounds__(Geo3<K, NT, NS>::NTH, Geo3<K, NT, NS>::MINB)
     // s-pass of stream output row j (register-ring slots of input rows j .. j + 2K at
     // (u + jj) % RSLOT; its S row staged at ring row rs, the Z centre at ring row rc)
     auto spass = [&](int st, int j, int u, int rs, int rc) {
-        const float4* srow4 = reinterpret_cast<const float4*>(S2s(st) + rs * SR2);
-        auto sc2 = [&](int e) -> float2 {   // float4 e/2 holds coefficients e, e+1 (SR2 even)
-            const float4 v = srow4[e >> 1];
-            return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+        const float4* srow4 = reinterpret_cast<const float4*>(Ss(st) + rs * SR);
+        auto sc2 = [&](int e) -> float2 {   // coefficient e in both lanes (float4 e/4 holds e .. e+3)
+            const float4 v = srow4[e >> 2];
+            const float s = (e & 3) == 0 ? v.x : (e & 3) == 1 ? v.y : (e & 3) == 2 ? v.z : v.w;
+            return make_float2(s, s);
         };
         float2 yt[NT];
         {

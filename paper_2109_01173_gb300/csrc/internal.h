@@ -74,7 +74,7 @@ struct mofem_ctx {
 
     // banded tables, diagonal-major: tab[term][j][row] = S_term[row][row + j - K]
     double* S64 = nullptr;  float* S32 = nullptr;   // [batch][NT][P][q]
-    float* S2dup = nullptr;   // [batch][q][2*SR2] FP32 S rows, each coefficient twice (packed apply)
+    float* Srow32 = nullptr;   // [batch][q][s_row] FP32 S rows, coefficient t*P + j at t*P + j (packed apply)
     float* Sdf = nullptr;     // plain S tables as double-float: hi plane then lo plane, each [batch][NT][P][q]
     float* Tdf = nullptr;     // plain T tables as double-float: hi plane then lo plane, each [NT][P][q]
     // difference-form tables as double-float (same planes and shapes): off the diagonal slot the
@@ -84,7 +84,7 @@ struct mofem_ctx {
     float* Tdd = nullptr;
     float* Srdf = nullptr;    // right-hand-side mass factors as double-float: [hi | lo] of [batch][P][q]
     float* Trdf = nullptr;    // and [hi | lo] of [P][q]
-    int s2_row = 0;           // floats per S2dup row
+    int s_row = 0;             // floats per Srow32 row
     double* T64 = nullptr;  float* T32 = nullptr;   // [NT][P][q]
     double* Sr64 = nullptr; double* Tr64 = nullptr; // RHS mass factors: [batch][P][q], [P][q] (offset off)
     double* Smf64 = nullptr; double* Tmf64 = nullptr; // untrimmed masses M_s[h], M_t: [batch][P][n], [P][n]
@@ -216,13 +216,13 @@ mofem_status launch_apply_pcg(int K, int nt, bool fp64, const CUtensorMap& mZ, c
                               const CUtensorMap* mS,
                               const ApplyPcgArgs& a, int batch, cudaStream_t st);
 // Geometry of the PCG-form apply launched for (K, nt, precision): output rows
-// per CTA, rows per staging box (TMA map), floats per duplicated S row.
+// per CTA, rows per staging box (TMA map), floats per S row of the streaming apply.
 int apply_pcg_rows_per_cta(int K, int nt, bool fp64);
 int apply_pcg_box_rows(int K, int nt, bool fp64);
 int apply_pcg_s_box_rows();
 int apply_pcg_ctas_per_instance(int K, int nt, bool fp64, int q, int batch);
 bool apply_pcg_packed(int K, int nt, bool fp64);
-int apply_s2_row_floats(int K, int nt);
+int apply_s_row_floats(int K, int nt);
 mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
                           int box_cols, int box_rows);
 

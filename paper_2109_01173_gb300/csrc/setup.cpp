@@ -507,21 +507,20 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
     MOFEM_TRY(up64(&c->Sr64, Srh));
     MOFEM_TRY(up64(&c->Smf64, H.Smf));
     MOFEM_TRY(up64(&c->Tmf64, H.Tmf));
-    {   // FP32 S rows for the packed apply: [batch][q][W], coefficient e = t*P + j at 2e and 2e+1
+    {   // FP32 S rows for the packed apply: [batch][q][W], coefficient e = t*P + j at e
         const int ntp = c->NT * c->P;
-        const int W = apply_s2_row_floats(c->K, c->NT);
-        c->s2_row = W;
+        const int W = apply_s_row_floats(c->K, c->NT);
+        c->s_row = W;
         std::vector<float> s2((size_t)B * q * W, 0.f);
         for (int i = 0; i < B; ++i)
             for (int e = 0; e < ntp; ++e)
                 for (int r = 0; r < q; ++r) {
                     const float v = (float)Sh[((size_t)i * ntp + e) * q + r];
                     float* row = s2.data() + ((size_t)i * q + r) * W;
-                    row[2 * e] = v;
-                    row[2 * e + 1] = v;
+                    row[e] = v;
                 }
-        MOFEM_TRY(dev_alloc(&c->S2dup, s2.size()));
-        MOFEM_CUDA_TRY(cudaMemcpy(c->S2dup, s2.data(), s2.size() * sizeof(float), cudaMemcpyHostToDevice));
+        MOFEM_TRY(dev_alloc(&c->Srow32, s2.size()));
+        MOFEM_CUDA_TRY(cudaMemcpy(c->Srow32, s2.data(), s2.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
     MOFEM_TRY(up64(&c->Tr64, Trh));
 
@@ -620,7 +619,7 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
 }
 
 void mofem_free(mofem_ctx* c) {
-    void* ptrs[] = {c->Smf64, c->Tmf64, c->U64m, c->S64, c->S32, c->S2dup, c->Sdf, c->Tdf, c->Sdd, c->Tdd, c->Srdf, c->Trdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
+    void* ptrs[] = {c->Smf64, c->Tmf64, c->U64m, c->S64, c->S32, c->Srow32, c->Sdf, c->Tdf, c->Sdd, c->Tdd, c->Srdf, c->Trdf, c->T64, c->T32, c->Sr64, c->Tr64, c->Q1_64, c->Q2_64, c->lam64, c->mu64,
                     c->lam32, c->mu32, c->w64, c->w32, c->Bm64, c->R64, c->d_part, c->d_sc, c->d_status,
                     c->d_red};
     for (void* p : ptrs) cudaFree(p);

@@ -180,8 +180,8 @@ static mofem_status ensure_apply_maps(mofem_ctx* c, bool fp64) {
         MOFEM_TRY(make_row_map(&e.mQA32, w32(c, W32_QA), 4, c->q, c->q, c->batch, c->ld, WCT, HR));
         MOFEM_TRY(make_row_map(&e.mQB32, w32(c, W32_QB), 4, c->q, c->q, c->batch, c->ld, WCT, HR));
         if (apply_pcg_packed(c->K, c->NT, false)) {
-            const int w = c->s2_row;
-            MOFEM_TRY(make_row_map(&e.mS32, c->S2dup, 4, w, c->q, c->batch, w, w, apply_pcg_s_box_rows()));
+            const int w = c->s_row;
+            MOFEM_TRY(make_row_map(&e.mS32, c->Srow32, 4, w, c->q, c->batch, w, w, apply_pcg_s_box_rows()));
         }
         e.maps32 = true;
     }
@@ -1209,7 +1209,7 @@ mofem_status pcg_direction(mofem_ctx* c, const void* Z, const void* Qp, const do
     MOFEM_TRY(make_row_map(&mQ, Qp, esz, c->q, c->q, B, ld, WCT, HR));
     const bool packed = apply_pcg_packed(c->K, c->NT, fp64);
     if (packed)
-        MOFEM_TRY(make_row_map(&mS, c->S2dup, 4, c->s2_row, c->q, B, c->s2_row, c->s2_row, apply_pcg_s_box_rows()));
+        MOFEM_TRY(make_row_map(&mS, c->Srow32, 4, c->s_row, c->q, B, c->s_row, c->s_row, apply_pcg_s_box_rows()));
     std::vector<PcgScalars> h(B);
     for (int i = 0; i < B; ++i) {
         h[i] = PcgScalars{};
