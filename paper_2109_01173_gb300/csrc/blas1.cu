@@ -25,6 +25,7 @@
 namespace {
 
 constexpr int UPD_THREADS = 256;
+constexpr int UPD_EVEN_MINB = 3;   // resident CTAs of the even-phase update (registers for 3 x 256 threads)
 
 // RMS of the residual operand in the FP16 preconditioner GEMMs.  The largest
 // spectral coefficient of a smooth residual, (Q1^T R Q2)_00, is about q^2 RMS(R)
@@ -176,8 +177,13 @@ __device__ __forceinline__ double dot32(const double2& a, const double2& b) { re
 // alpha is read from the scalar state (set by the apply kernel's last CTA).
 // Dot products: working precision within a thread (a few dozen terms), FP64
 // across threads and CTAs (fixed order).
-template <typename T, bool MIXED, int ROP>
-__global__ void __launch_bounds__(UPD_THREADS, 2) k_update(UpdArgs g) {
+// PH: the lazy phase fixed at compile time (0 even, 1 odd; the iteration graphs hold an even
+// and an odd iteration), or -1 to take it from the scalar state.  The even form keeps no
+// registers for the correction of U and runs at a higher occupancy.
+template <typename T, bool MIXED, int ROP, int PH>
+__global__ void __launch_bounds__(UPD_THREADS, PH == 0 ? UPD_EVEN_MINB : 2) k_update(UpdArgs g) {
+    static_assert(PH < 0 || MIXED, "a fixed lazy phase belongs to the mixed form");
+    constexpr bool HAS_EVEN = PH != 1, HAS_ODD = PH != 0;
     using V = typename Vec<T>::type;
     static_assert(ROP == 0 || Vec<T>::W == 4, "operand copies are produced by the FP32 update only");
     __shared__ double sh[UPD_THREADS / 32];
@@ -214,8 +220,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_update(UpdArgs g) {
         long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
         // Lazy correction (mixed form): an even iteration only updates R and leaves
         // alpha Q pending; the odd one adds alpha_prev Q_prev + alpha Q in one pass.
-        const bool lazy = MIXED && g.lazy && (g.use_sc || g.lazy_phase >= 0);
-        const bool pair = lazy && (g.lazy_phase >= 0 ? g.lazy_phase == 1 : (sc->iters & 1) != 0);
+        const bool lazy = PH >= 0 || (MIXED && g.lazy && (g.use_sc || g.lazy_phase >= 0));
+        const bool pair = PH >= 0 ? PH == 1 : lazy && (g.lazy_phase >= 0 ? g.lazy_phase == 1 : (sc->iters & 1) != 0);
         if constexpr (MIXED) {
             if (lazy) {
                 const float4* Qp4 = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(g.Qprev) +
@@ -231,6 +237,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_update(UpdArgs g) {
                 };
                 // batches of independent 16-byte loads in flight per thread (memory-level parallelism)
                 if (!pair) {
+                  if constexpr (HAS_EVEN) {
                     constexpr int UE = 4;
                     for (; i0 + (UE - 1) * stride < g.nvec; i0 += UE * stride) {
                         float4 r[UE], lq[UE], zo[UE];
@@ -244,7 +251,9 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_update(UpdArgs g) {
 #pragma unroll
                         for (int k = 0; k < UE; ++k) rbody(i0 + k * stride, r[k], lq[k], zo[k]);
                     }
+                  }
                 } else {
+                  if constexpr (HAS_ODD) {
                     constexpr int UO = 2;
                     for (; i0 + (UO - 1) * stride < g.nvec; i0 += UO * stride) {
                         float4 r[UO], lq[UO], zo[UO], qp[UO], qc[UO];
@@ -268,12 +277,13 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_update(UpdArgs g) {
                             rbody(i, r[k], lq[k], zo[k]);
                         }
                     }
+                  }
                 }
                 for (; i0 < g.nvec; i0 += stride) {
                     float4 r = R[i0];
                     const float4 lq = LQ[i0];
                     const float4 zo = g.flex ? Zo[i0] : lq;
-                    if (pair) {
+                    if (HAS_ODD && pair) {
                         DF u{U.ph[i0], U.pl[i0]};
                         df_axpy2(u, Qp4[i0], ap, Q[i0], alpha);
                         U.ph[i0] = u.h;
@@ -283,7 +293,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 2) k_update(UpdArgs g) {
                 }
             }
         }
-        if (!lazy) {
+        if constexpr (PH < 0) if (!lazy) {
         using UV = typename UVec<T, MIXED>::Val;
         auto body = [&](long long i, UV u, V r, const V& qv, const V& lq, const V& zo) {
             U.axpy_store(i, u, qv, alpha);
@@ -433,8 +443,31 @@ __global__ void __launch_bounds__(UPD_THREADS) k_dot(const T* A, const T* B, lon
     A += (size_t)inst * bs;
     B += (size_t)inst * bs;
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        acc += (double)A[i] * (double)B[i];
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 within a thread (a few dozen terms, 16-byte loads where aligned), FP64 across
+        // threads: a conversion per element would run on the FP64 pipe (a small fraction of
+        // the FP32 rate on this GPU)
+        float a32 = 0.f;
+        const bool vec = (n % 4) == 0 && (bs % 4) == 0 && (reinterpret_cast<uintptr_t>(A) % 16) == 0 &&
+                         (reinterpret_cast<uintptr_t>(B) % 16) == 0;
+        if (vec) {
+            const float4* A4 = reinterpret_cast<const float4*>(A);
+            const float4* B4 = reinterpret_cast<const float4*>(B);
+            for (long long i = t0; i < n / 4; i += stride) {
+                const float4 a = A4[i], b = B4[i];
+                a32 = fmaf(a.x, b.x, a32);
+                a32 = fmaf(a.y, b.y, a32);
+                a32 = fmaf(a.z, b.z, a32);
+                a32 = fmaf(a.w, b.w, a32);
+            }
+        } else {
+            for (long long i = t0; i < n; i += stride) a32 = fmaf(A[i], B[i], a32);
+        }
+        acc = (double)a32;
+    } else {
+        for (long long i = t0; i < n; i += stride) acc += (double)A[i] * (double)B[i];
+    }
     double s = block_sum<UPD_THREADS>(acc, sh);
     if (threadIdx.x == 0) {
         part[(size_t)inst * nblk + blockIdx.x] = s;
@@ -710,10 +743,20 @@ mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo
     g.cond = cond ? *cond : 0;
     dim3 grid(c->part.n_upd, c->batch);
     g.count = (double)c->q * c->q;
-    if (fp64) k_update<double, false, 0><<<grid, UPD_THREADS, 0, st>>>(g);
-    else if (rop_kind == 1) k_update<float, true, 1><<<grid, UPD_THREADS, 0, st>>>(g);
-    else if (rop_kind == 2) k_update<float, true, 2><<<grid, UPD_THREADS, 0, st>>>(g);
-    else k_update<float, true, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+    if (fp64) k_update<double, false, 0, -1><<<grid, UPD_THREADS, 0, st>>>(g);
+    else if (g.lazy && lazy_phase >= 0) {   // the phase is known when the iteration is recorded
+        if (lazy_phase == 0) {
+            if (rop_kind == 1) k_update<float, true, 1, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+            else if (rop_kind == 2) k_update<float, true, 2, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+            else k_update<float, true, 0, 0><<<grid, UPD_THREADS, 0, st>>>(g);
+        } else {
+            if (rop_kind == 1) k_update<float, true, 1, 1><<<grid, UPD_THREADS, 0, st>>>(g);
+            else if (rop_kind == 2) k_update<float, true, 2, 1><<<grid, UPD_THREADS, 0, st>>>(g);
+            else k_update<float, true, 0, 1><<<grid, UPD_THREADS, 0, st>>>(g);
+        }
+    } else if (rop_kind == 1) k_update<float, true, 1, -1><<<grid, UPD_THREADS, 0, st>>>(g);
+    else if (rop_kind == 2) k_update<float, true, 2, -1><<<grid, UPD_THREADS, 0, st>>>(g);
+    else k_update<float, true, 0, -1><<<grid, UPD_THREADS, 0, st>>>(g);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }

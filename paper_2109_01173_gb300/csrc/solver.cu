@@ -353,7 +353,7 @@ static mofem_status pcg_iteration(mofem_ctx* c, mofem_precision prec, int s, int
     //    (last CTA) ; graph condition
     MOFEM_TRY(launch_pcg_update(c, fp64, U, Ulo, R, Qn, LQ, Z, fp64 ? nullptr : c->tc[which].Rop,
                                 fp64 ? 0 : (which == 1 ? 1 : (which == 2 ? 2 : 0)), (fp64 || packed) ? 0 : 1,
-                                max_iter, fixed, cond, st, true, fp64 ? nullptr : Qp));
+                                max_iter, fixed, cond, st, true, fp64 ? nullptr : Qp, fp64 ? -1 : (s & 1)));
     // 3) Z = P^{-1}(R) ; rz and beta (last CTA)
     if (!with_precond) {   // heterogeneous lockstep: one GEMM launch for every group (solve_fused)
         if (!fp64 && which == 0)
