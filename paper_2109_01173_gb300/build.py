@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
           "-diag-suppress", "177"]
 SOURCES = ["apply_f32.cu", "apply_f64.cu", "apply_df.cu", "blas1.cu", "gemm_tc.cu", "solver.cu", "noalloc.cu", "dib.cu", "setup.cpp", "capi.cpp", "group.cpp"]
-HEADERS = ["internal.h", "apply_impl.cuh", "apply_pcg_f2.cuh", os.path.join("..", "..", "include", "mofem.h")]
+HEADERS = ["internal.h", "apply_impl.cuh", "apply_pcg_f2.cuh", "apply_pcg_push.cuh", os.path.join("..", "..", "include", "mofem.h")]
 
 
 def _newest_header():

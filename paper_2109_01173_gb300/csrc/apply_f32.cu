@@ -1,5 +1,6 @@
 // FP32 instantiations of the banded operator apply (mixed-precision inner solve).
 #include "apply_pcg_f2.cuh"
+#include "apply_pcg_push.cuh"
 
 using namespace mofem_apply_impl;
 
@@ -44,12 +45,18 @@ int apply_rows_per_cta(int K) {
     }
 }
 
+// The streaming FP32 apply with the s-pass in push form (k_apply_pcg4) or over a register
+// window of t-pass rows (k_apply_pcg3); the coefficient table of the handle follows.
+constexpr bool kApplyPush = true;
+bool apply_push_layout() { return kApplyPush; }
+
 template <int K, int NT>
 static mofem_status pcg_f32(const CUtensorMap& mZ, const CUtensorMap& mQ, const CUtensorMap* mS,
                            const ApplyPcgArgs& a, int batch, cudaStream_t st) {
     if constexpr (packed_apply_ok(K, NT)) {
         if (!mS) return MOFEM_ERR_INVALID_ARG;
-        return launch_pcg3_t<K, NT>(mZ, mQ, *mS, a, batch, st);
+        if constexpr (kApplyPush) return launch_pcg4_t<K, NT>(mZ, mQ, *mS, a, batch, st);
+        else return launch_pcg3_t<K, NT>(mZ, mQ, *mS, a, batch, st);
     } else {
         return launch_pcg_t<float, K, NT, false>(mZ, mQ, a, batch, st);
     }
@@ -99,7 +106,7 @@ int apply_pcg_box_rows(int K, int nt, bool fp64) {
 // Rows of one TMA box of the S rows (streaming apply).
 int apply_pcg_s_box_rows() { return Geo3<2, 5, 1>::CR; }
 
-// SR of Geo3: floats per S row, the NT (2K + 1) coefficients padded to a multiple of 8
+// SR of Geo3 / Geo4: floats per coefficient row, NT (2K + 1) padded to a multiple of 8
 int apply_s_row_floats(int K, int nt) { return ((nt * (2 * K + 1) + 7) / 8) * 8; }
 
 // (the largest tile-height divisor the handles use: partial slots are sized for it)
@@ -107,8 +114,12 @@ constexpr int APPLY_SEG_DIV_MAX = 2;
 
 template <int K, int NT>
 static int segs_k(int q, int strips, int batch) {
-    constexpr int NS = packed_streams(K, NT);
-    return apply3_segments(q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>() * APPLY_SEG_DIV_MAX, K, NS);
+    if constexpr (kApplyPush) {
+        return apply3_segments(q, strips, batch, apply4_ctas_wanted_t<K, NT>() * APPLY_SEG_DIV_MAX, K, 1);
+    } else {
+        constexpr int NS = packed_streams(K, NT);
+        return apply3_segments(q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>() * APPLY_SEG_DIV_MAX, K, NS);
+    }
 }
 
 template <int K>

@@ -223,6 +223,10 @@ int apply_pcg_s_box_rows();
 int apply_pcg_ctas_per_instance(int K, int nt, bool fp64, int q, int batch);
 bool apply_pcg_packed(int K, int nt, bool fp64);
 int apply_s_row_floats(int K, int nt);
+// Coefficient rows of the streaming apply in push form (per input row: the partial sums
+// and row sum of each difference term, the matrix column of each plain term) instead of
+// the S rows themselves.
+bool apply_push_layout();
 mofem_status make_row_map(CUtensorMap* m, const void* base, int esize, int cols, int rows, int batch, int ld,
                           int box_cols, int box_rows);
 

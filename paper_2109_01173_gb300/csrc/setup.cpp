@@ -507,18 +507,53 @@ mofem_status mofem_build(mofem_ctx* c, const mofem_profile* g1, const mofem_prof
     MOFEM_TRY(up64(&c->Sr64, Srh));
     MOFEM_TRY(up64(&c->Smf64, H.Smf));
     MOFEM_TRY(up64(&c->Tmf64, H.Tmf));
-    {   // FP32 S rows for the packed apply: [batch][q][W], coefficient e = t*P + j at e
-        const int ntp = c->NT * c->P;
+    {   // FP32 coefficient rows of the packed apply: [batch][q][W]
+        const int ntp = c->NT * c->P, K = c->K, P = c->P;
         const int W = apply_s_row_floats(c->K, c->NT);
         c->s_row = W;
         std::vector<float> s2((size_t)B * q * W, 0.f);
-        for (int i = 0; i < B; ++i)
-            for (int e = 0; e < ntp; ++e)
-                for (int r = 0; r < q; ++r) {
-                    const float v = (float)Sh[((size_t)i * ntp + e) * q + r];
-                    float* row = s2.data() + ((size_t)i * q + r) * W;
-                    row[e] = v;
+        if (!apply_push_layout()) {   // S rows: coefficient e = t*P + j of row r at e
+            for (int i = 0; i < B; ++i)
+                for (int e = 0; e < ntp; ++e)
+                    for (int r = 0; r < q; ++r) s2[((size_t)i * q + r) * W + e] = (float)Sh[((size_t)i * ntp + e) * q + r];
+        } else {
+            // push form, row g = input row g.  Difference term t: slot p < 2K is the
+            // coefficient of delta[g-1] = W[g] - W[g-1] in output row j = g - K + p,
+            // a_j(d) = sum_{m > d} S[j][j+m] (d >= 0) or -sum_{m <= d} S[j][j+m] (d < 0) with
+            // d = K - 1 - p; slot 2K the row sum of row g.  Plain term: slot p is S[j][g].
+            // Sums in FP64, one rounding.
+            for (int i = 0; i < B; ++i)
+                for (int t = 0; t < c->NT; ++t) {
+                    const double* St = Sh.data() + ((size_t)i * c->NT + t) * P * q;   // [slot][row]
+                    auto s = [&](int j, int m) -> double {   // entry (j, j + m) of the banded matrix
+                        if (j < 0 || j >= q || j + m < 0 || j + m >= q) return 0.0;
+                        return St[(size_t)(m + K) * q + j];
+                    };
+                    const bool diff = (smask >> t) & 1u;
+                    for (int g = 0; g < q; ++g) {
+                        float* row = s2.data() + ((size_t)i * q + g) * W + t * P;
+                        if (diff) {
+                            for (int p = 0; p < 2 * K; ++p) {
+                                const int j = g - K + p, dd = K - 1 - p;
+                                double a = 0.0;
+                                if (j >= 0 && j < q) {
+                                    if (dd >= 0)
+                                        for (int m = dd + 1; m <= K; ++m) a += s(j, m);
+                                    else
+                                        for (int m = -K; m <= dd; ++m) a -= s(j, m);
+                                }
+                                row[p] = (float)a;
+                            }
+                            row[2 * K] = (float)St[(size_t)K * q + g];
+                        } else {
+                            for (int p = 0; p <= 2 * K; ++p) {
+                                const int j = g - K + p;
+                                row[p] = (float)s(j, g - j);
+                            }
+                        }
+                    }
                 }
+        }
         MOFEM_TRY(dev_alloc(&c->Srow32, s2.size()));
         MOFEM_CUDA_TRY(cudaMemcpy(c->Srow32, s2.data(), s2.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
