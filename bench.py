@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MO-PCG solves/s and ms/iter, P2 N=2049 (mixed vs FP64 GPU form, rel.err<=1e-8)"
 # DRAM bytes per chained preconditioner launch (G1..G4) at P2 2049 x 4 (ncu capture of the
 # current kernel; None whenever k_gemm_2sm changes until it is captured again)
-CHAIN_DRAM_BYTES = None
+CHAIN_DRAM_BYTES = 352.5e6
 UNIT = "solves/s"
 
 
