@@ -743,20 +743,40 @@ mofem_status launch_pcg_update(const mofem_ctx* c, bool fp64, void* U, void* Ulo
     g.cond = cond ? *cond : 0;
     dim3 grid(c->part.n_upd, c->batch);
     g.count = (double)c->q * c->q;
-    if (fp64) k_update<double, false, 0, -1><<<grid, UPD_THREADS, 0, st>>>(g);
+    void (*kern)(UpdArgs) = nullptr;
+    int wave_slot = -1;
+    if (fp64) kern = k_update<double, false, 0, -1>;
     else if (g.lazy && lazy_phase >= 0) {   // the phase is known when the iteration is recorded
-        if (lazy_phase == 0) {
-            if (rop_kind == 1) k_update<float, true, 1, 0><<<grid, UPD_THREADS, 0, st>>>(g);
-            else if (rop_kind == 2) k_update<float, true, 2, 0><<<grid, UPD_THREADS, 0, st>>>(g);
-            else k_update<float, true, 0, 0><<<grid, UPD_THREADS, 0, st>>>(g);
-        } else {
-            if (rop_kind == 1) k_update<float, true, 1, 1><<<grid, UPD_THREADS, 0, st>>>(g);
-            else if (rop_kind == 2) k_update<float, true, 2, 1><<<grid, UPD_THREADS, 0, st>>>(g);
-            else k_update<float, true, 0, 1><<<grid, UPD_THREADS, 0, st>>>(g);
+        const int rk = rop_kind == 1 ? 1 : (rop_kind == 2 ? 2 : 0);
+        wave_slot = rk * 2 + (lazy_phase ? 1 : 0);
+        if (lazy_phase == 0)
+            kern = rk == 1 ? k_update<float, true, 1, 0> : (rk == 2 ? k_update<float, true, 2, 0> : k_update<float, true, 0, 0>);
+        else
+            kern = rk == 1 ? k_update<float, true, 1, 1> : (rk == 2 ? k_update<float, true, 2, 1> : k_update<float, true, 0, 1>);
+    } else {
+        kern = rop_kind == 1 ? k_update<float, true, 1, -1>
+                             : (rop_kind == 2 ? k_update<float, true, 2, -1> : k_update<float, true, 0, -1>);
+    }
+    if (wave_slot >= 0) {
+        // phase-specialised forms: one wave of resident CTAs over all instances (the partial
+        // slots, n_upd per instance, are the upper bound)
+        static std::atomic<int> wave[6][MOFEM_MAX_DEV];
+        std::atomic<int>& w = wave[wave_slot][dev_slot()];
+        int n = w.load(std::memory_order_relaxed);
+        if (!n) {
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, UPD_THREADS, 0) != cudaSuccess || per < 1)
+                per = 1;
+            n = (sms > 0 ? sms : 1) * per;
+            w.store(n, std::memory_order_relaxed);
         }
-    } else if (rop_kind == 1) k_update<float, true, 1, -1><<<grid, UPD_THREADS, 0, st>>>(g);
-    else if (rop_kind == 2) k_update<float, true, 2, -1><<<grid, UPD_THREADS, 0, st>>>(g);
-    else k_update<float, true, 0, -1><<<grid, UPD_THREADS, 0, st>>>(g);
+        const int nx = std::max(1, std::min(c->part.n_upd, n / c->batch));
+        grid.x = nx;
+        g.n_upd = nx;
+    }
+    kern<<<grid, UPD_THREADS, 0, st>>>(g);
     MOFEM_CUDA_TRY(cudaGetLastError());
     return MOFEM_OK;
 }
