@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-heat", action="store_true", help="skip the differentiation workload (heat IMEX + adjoint)")
     ap.add_argument("--no-dib", action="store_true", help="skip the reaction-diffusion (DIB) workload")
     ap.add_argument("--no-batching", action="store_true", help="skip the heterogeneous-batch workload")
+    ap.add_argument("--no-batch-sweep", action="store_true",
+                    help="skip the uniform batch sweep (P2 n=2049, B in 1, 4, 16, 64 instances)")
     ap.add_argument("--batching-small", action="store_true",
                     help="heterogeneous batch of 64 problems with n <= 513 (default: the configured 256 problems, "
                          "n up to 2049)")
@@ -571,6 +573,25 @@ def run_mofem(a):
             h2.close()
             del F2, U2
 
+    # ---- uniform batches of the precision form: instance i with gamma ~ U[0,10] and its own
+    # top profile 1 + a sin(2 pi b x), B in 1, 4, 16, 64 (one handle per B, one warm-up solve,
+    # median of two timed solves) ------------------------------------------------------------
+    batch_sweep = {}
+    if not a.no_batch_sweep and a.n == 2049 and a.k == 2 and rank == 0 and world == 1:
+        from paper_2109_01173_gb300.inputs import batch_instances
+        for B2 in (1, 4, 16, 64):
+            ins2 = batch_instances(B2, n=a.n, k=a.k, seed0=1000)
+            t0 = time.perf_counter()
+            h2 = mf.Handle([i["g1"] for i in ins2], [i["g2"] for i in ins2], a.k, a.n, [i["gamma"] for i in ins2])
+            F2 = torch.tensor(np.stack([i["F"] for i in ins2]), dtype=torch.float64, device="cuda")
+            U2 = torch.zeros((B2, h2.q, h2.q), dtype=torch.float64, device="cuda")
+            r = timed_solves(h2, F2, U2, a.precision, a.rtol, B2, stream, samples=2)
+            r["wall_s"] = time.perf_counter() - t0   # setup, warm-up and the timed solves
+            batch_sweep[f"B{B2}"] = r
+            h2.close()
+            del F2, U2
+            torch.cuda.empty_cache()
+
     # ---- CPU baseline: the oracle on a bounded sample ----------------------------------
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -643,6 +664,7 @@ def run_mofem(a):
         "rel_err_vs_oracle": rel_err_oracle,
         "precision_matrix": precisions or None,
         "other_sizes": other_sizes or None,
+        "batch_sweep": batch_sweep or None,
         "cpu_baseline": cpu,
     }
     if not a.no_heat and rank == 0:

@@ -255,6 +255,24 @@ def test_batched_solve(mf):
     h.close()
 
 
+def test_uniform_batch_sixteen_instances(mf):
+    """The uniform-batch form at 16 instances (gamma ~ U[0,10], top 1 + a sin(2 pi b x), each
+    with its own seeded Fourier f; the generator of the bench's batch sweep) at P2, 65 x 65
+    nodes: every instance of one mixed FP16 solve against its own FP64 oracle solve."""
+    from paper_2109_01173_gb300.inputs import batch_instances
+    torch = torch_()
+    ins = batch_instances(16, n=65, k=2, seed0=1000)
+    h = mf.Handle([i["g1"] for i in ins], [i["g2"] for i in ins], 2, 65, [i["gamma"] for i in ins])
+    U = torch.zeros((16, h.q, h.q), dtype=torch.float64, device="cuda")
+    F = torch.tensor(np.stack([i["F"] for i in ins]), dtype=torch.float64, device="cuda")
+    info, code = h.pcg_solve(F, U, rtol=1e-10, max_iter=400, precision="fp16")
+    assert code == 0 and info.rel_residual <= 1e-10
+    for i, I in enumerate(ins):
+        Uo, _ = pcg.solve(Problem(I["g1"], I["g2"], 2, 65, I["gamma"]), I["F"], rtol=1e-13)
+        assert np.linalg.norm(U[i].cpu().numpy() - Uo) <= 1e-8 * np.linalg.norm(Uo), i
+    h.close()
+
+
 @pytest.mark.parametrize("prec", ["fp16", "fp64"])
 def test_zero_right_hand_side(mf, prec):
     """F = 0 gives U = 0 at once (the initialisation marks the instance inactive), alone
