@@ -37,6 +37,7 @@ METRIC = "MO-PCG solves/s and ms/iter, P2 N=2049 (mixed vs FP64 GPU form, rel.er
 # current kernel; None whenever k_gemm_2sm changes until it is captured again)
 CHAIN_DRAM_BYTES = 352.5e6
 UNIT = "solves/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # non-tensor FP32 FMA pipes at the maximum SM clock
 
 
 def parse():
@@ -643,10 +644,16 @@ def run_mofem(a):
                                     + (" / 2 for TF32" if prec_k == "tf32" else ""),
                      "per_gemm_us": [round(t * 1e6, 2) for t in t_gemm],
                      "per_gemm_tflops": [round(x, 1) for x in gemm_tflops]},
-        "roofline_apply": {"bound": "hbm", "kernel": (f"k_apply_pcg3<K={k},NT=5> (streaming packed FP32, PCG form)" if k <= 3 else
+        "roofline_apply": {"bound": "hbm", "kernel": (f"k_apply_pcg4<K={k},NT=5> (streaming packed FP32, push-form s-pass, PCG form)" if k <= 3 else
                                       f"k_apply_pcg<float,K={k},NT=5> (scalar FP32, PCG form)"),
                            "achieved": apply_bytes / t_apply / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                           "frac": apply_bytes / t_apply / 1e9 / peaks["hbm_gbs"], "us": t_apply * 1e6},
+                           "frac": apply_bytes / t_apply / 1e9 / peaks["hbm_gbs"], "us": t_apply * 1e6,
+                           # the same launch against the FP32 pipes: 2 passes x NT x (2k+1) multiply-adds per
+                           # element; peak = 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (unit counts, max clock)
+                           "fp32_pipe": {"flop_per_element": 4 * 5 * (2 * k + 1),
+                                         "achieved_tflops": 4 * 5 * (2 * k + 1) * B * q * q / t_apply / 1e12,
+                                         "peak_tflops": FP32_PEAK_TFLOPS,
+                                         "frac": 4 * 5 * (2 * k + 1) * B * q * q / t_apply / 1e12 / FP32_PEAK_TFLOPS}},
         "roofline_update": {"bound": "hbm", "kernel": f"k_update<float, lazy double-float U, {a.precision} operand copy> (mean of the even and odd forms)",
                             "achieved": upd_bytes / t_upd / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                             "frac": upd_bytes / t_upd / 1e9 / peaks["hbm_gbs"], "us": t_upd * 1e6,
