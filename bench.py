@@ -259,14 +259,14 @@ def measure_batching(full=False):
     and tuning reported apart from the timed solve (CUDA events, rtol 1e-10, FP16 GEMMs)."""
     import torch
     import paper_2109_01173_gb300.mofem as mf
-    from paper_2109_01173_gb300.inputs import hetero_instances
+    from paper_2109_01173_gb300.inputs import hetero_instances, fourier_f_device
     count, nch = (256, (129, 257, 513, 1025, 2049)) if full else (64, (129, 257, 513))
-    probs = hetero_instances(count, n_choices=nch, k_choices=(1, 2, 3, 4), seed=0)
+    probs = hetero_instances(count, n_choices=nch, k_choices=(1, 2, 3, 4), seed=0, with_f=False)
     t0 = time.perf_counter()
     g = mf.Group(probs)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
-    F = [torch.tensor(p["F"], device="cuda") for p in probs]
+    F = [fourier_f_device(p["g1"], p["g2"], p["n"], p["f_seed"], "cuda") for p in probs]
     U = [torch.zeros((p["n"] - 2, p["n"] - 2), dtype=torch.float64, device="cuda") for p in probs]
     t0 = time.perf_counter()
     chosen = g.autotune(F, U, rtol=1e-10)
@@ -579,12 +579,12 @@ def run_mofem(a):
     # median of two timed solves) ------------------------------------------------------------
     batch_sweep = {}
     if not a.no_batch_sweep and a.n == 2049 and a.k == 2 and rank == 0 and world == 1:
-        from paper_2109_01173_gb300.inputs import batch_instances
+        from paper_2109_01173_gb300.inputs import batch_instances, fourier_f_device
         for B2 in (1, 4, 16, 64):
-            ins2 = batch_instances(B2, n=a.n, k=a.k, seed0=1000)
+            ins2 = batch_instances(B2, n=a.n, k=a.k, seed0=1000, with_f=False)
             t0 = time.perf_counter()
             h2 = mf.Handle([i["g1"] for i in ins2], [i["g2"] for i in ins2], a.k, a.n, [i["gamma"] for i in ins2])
-            F2 = torch.tensor(np.stack([i["F"] for i in ins2]), dtype=torch.float64, device="cuda")
+            F2 = torch.stack([fourier_f_device(i["g1"], i["g2"], a.n, i["f_seed"], "cuda") for i in ins2])
             U2 = torch.zeros((B2, h2.q, h2.q), dtype=torch.float64, device="cuda")
             r = timed_solves(h2, F2, U2, a.precision, a.rtol, B2, stream, samples=2)
             r["wall_s"] = time.perf_counter() - t0   # setup, warm-up and the timed solves

@@ -92,8 +92,7 @@ def manufactured_sin_f(g1, g2, n, gamma):
     return -(uxx + uyy) + gamma * u, u
 
 
-def fourier_f(g1, g2, n, seed, modes=32, mmax=8):
-    """Seeded sum of random Fourier modes evaluated at the physical nodes."""
+def _fourier_modes(seed, modes, mmax):
     rng = np.random.Generator(np.random.PCG64(seed))
     a = rng.standard_normal(modes)
     m = np.zeros((modes, 2), dtype=np.int64)
@@ -104,10 +103,32 @@ def fourier_f(g1, g2, n, seed, modes=32, mmax=8):
                 m[j] = cand
                 break
     phi = rng.uniform(0.0, 2 * np.pi, size=modes)
+    return a, m, phi
+
+
+def fourier_f(g1, g2, n, seed, modes=32, mmax=8):
+    """Seeded sum of random Fourier modes evaluated at the physical nodes."""
+    a, m, phi = _fourier_modes(seed, modes, mmax)
     X, Y = nodal_xy(g1, g2, n)
     F = np.zeros((n, n))
     for j in range(modes):
         F += a[j] / (1.0 + float(m[j] @ m[j])) * np.cos(2 * np.pi * (m[j, 0] * X + m[j, 1] * Y) + phi[j])
+    return F
+
+
+def fourier_f_device(g1, g2, n, seed, device, modes=32, mmax=8):
+    """fourier_f evaluated with torch in FP64 on `device` (the same modes and nodes; the
+    cosines of the device library may differ from numpy's in the last bit): for large
+    workloads whose right-hand sides only the GPU path reads."""
+    import torch
+    a, m, phi = _fourier_modes(seed, modes, mmax)
+    X, Y = nodal_xy(g1, g2, n)
+    Xd = torch.tensor(X, dtype=torch.float64, device=device)
+    Yd = torch.tensor(Y, dtype=torch.float64, device=device)
+    F = torch.zeros((n, n), dtype=torch.float64, device=device)
+    for j in range(modes):
+        F += float(a[j] / (1.0 + float(m[j] @ m[j]))) * torch.cos(
+            2 * np.pi * (float(m[j, 0]) * Xd + float(m[j, 1]) * Yd) + float(phi[j]))
     return F
 
 
@@ -130,8 +151,9 @@ def metric_instance(n=2049, k=2, seed=0, gamma=1.0):
                 F=fourier_f(ZERO, SIN_TOP, n, seed))
 
 
-def batch_instances(B, n=2049, k=2, seed0=0):
-    """B instances at fixed (n, k): gamma ~ U[0,10], g2 = 1 + a sin(2 pi b x), f seeded."""
+def batch_instances(B, n=2049, k=2, seed0=0, with_f=True):
+    """B instances at fixed (n, k): gamma ~ U[0,10], g2 = 1 + a sin(2 pi b x), f seeded
+    (with_f = False: only its seed, "f_seed", for fourier_f_device)."""
     out = []
     for i in range(B):
         rng = np.random.Generator(np.random.PCG64(1000 + seed0 + i))
@@ -139,8 +161,8 @@ def batch_instances(B, n=2049, k=2, seed0=0):
         a = float(rng.uniform(0.0, 0.3))
         b = int(rng.integers(1, 4))
         g2 = Profile(c0=1.0, sa=a, sf=b)
-        out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet',
-                        F=fourier_f(ZERO, g2, n, seed0 + i)))
+        out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet', f_seed=seed0 + i,
+                        F=fourier_f(ZERO, g2, n, seed0 + i) if with_f else None))
     return out
 
 
@@ -182,11 +204,11 @@ def dib_initial(n, eta_e, theta_e, seed=0, amplitude=1e-3):
                      theta_e + rng.uniform(-amplitude, amplitude, (n, n))])
 
 
-def hetero_instances(count, n_choices=(129, 257, 513, 1025, 2049), k_choices=(1, 2, 3, 4), seed=0):
+def hetero_instances(count, n_choices=(129, 257, 513, 1025, 2049), k_choices=(1, 2, 3, 4), seed=0, with_f=True):
     """Heterogeneous batch: per instance n ~ U(n_choices), k ~ U(k_choices) (n adjusted to
     3 floor((n-1)/3) + 1 when k = 3 does not divide n - 1), gamma ~ U[0, 10],
     g2 = 1 + a sin(2 pi b x) with a ~ U[0, 0.3], b ~ U{1, 2, 3}, Dirichlet, seeded
-    32-mode Fourier f."""
+    32-mode Fourier f (with_f = False: only its seed, "f_seed", for fourier_f_device)."""
     rng = np.random.Generator(np.random.PCG64(5000 + seed))
     out = []
     for i in range(count):
@@ -196,8 +218,9 @@ def hetero_instances(count, n_choices=(129, 257, 513, 1025, 2049), k_choices=(1,
             n = k * ((n - 1) // k) + 1
         gamma = float(rng.uniform(0.0, 10.0))
         g2 = Profile(c0=1.0, sa=float(rng.uniform(0.0, 0.3)), sf=int(rng.integers(1, 4)))
-        out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet',
-                        F=fourier_f(ZERO, g2, n, seed * 100000 + i)))
+        fs = seed * 100000 + i
+        out.append(dict(g1=ZERO, g2=g2, k=k, n=n, gamma=gamma, bc='dirichlet', f_seed=fs,
+                        F=fourier_f(ZERO, g2, n, fs) if with_f else None))
     return out
 
 
