@@ -382,6 +382,14 @@ def run_reference(a):
 
 
 # ----------------------------------------------------------------------------------
+T_START = time.perf_counter()
+
+
+def phase(name):
+    """Progress on stderr: the part of the run that starts now and the seconds so far."""
+    print(f"[bench] {name} at {time.perf_counter() - T_START:.1f} s", file=sys.stderr, flush=True)
+
+
 def run_mofem(a):
     import torch
     rank, world, local = dist_env()
@@ -391,7 +399,9 @@ def run_mofem(a):
     torch.cuda.set_device(local)
     import paper_2109_01173_gb300.mofem as mf
     B, n, k = a.batch, a.n, a.k
+    phase("inputs")
     insts = make_inputs(B, n, k, rank)
+    phase("setup")
     t0 = time.perf_counter()
     opts = mf.make_opts(flags=mf.FLAG_HOST_LOOP) if a.host_loop else None
     h = mf.Handle([i["g1"] for i in insts], [i["g2"] for i in insts], k, n, [i["gamma"] for i in insts], opts=opts)
@@ -461,6 +471,7 @@ def run_mofem(a):
     ms_step = elapsed / a.steps * 1e3
     ms_iter = elapsed * 1e3 / max(sum(iters), 1)
 
+    phase("end to end through the C ABI with host buffers")
     # ---- end to end through the C ABI with host buffers ----------------------------
     F_host = F.cpu().pin_memory()
     U_host = torch.empty((B, q, q), dtype=torch.float64).pin_memory()
@@ -479,6 +490,7 @@ def run_mofem(a):
     e2e_value = B * world * a.steps / max_over_ranks(e2e_elapsed, world)
     err_e2e = float((U_host.cuda() - U).abs().max().item())
 
+    phase("hot-kernel timing")
     # ---- hot-kernel timing (CUDA events on the launching stream) ---------------------
     peaks, peak_src = measured_peaks()
     reps = 20
@@ -517,6 +529,7 @@ def run_mofem(a):
     # even iteration: read R, L(Q); write R, FP16 R (14 B); odd: + read/write dU hi/lo, read Q_prev, Q (38 B)
     upd_bytes = 26.0 * B * q * q
 
+    phase("the oracle's reference solution of instance 0")
     # ---- the oracle's reference solution of instance 0 (spawned process, overlaps the GPU work) --
     oracle_job = None
     if rank == 0 and world == 1 and not a.no_oracle_check:
@@ -526,6 +539,7 @@ def run_mofem(a):
         oracle_job = ctx.Process(target=oracle_solution_job, args=(a.n, a.k, oracle_q), daemon=True)
         oracle_job.start()
 
+    phase("FP64 form")
     # ---- FP64 form (same instances, same stopping rule): one untimed warm-up solve, then
     # CUDA-event samples; the achieved FP64 rate of its cuBLAS DGEMM preconditioner
     fp64 = None
@@ -553,6 +567,7 @@ def run_mofem(a):
                 "timing": f"1 warm-up solve, median of {a.fp64_samples} CUDA-event samples; the preconditioner "
                           f"(4 cuBLAS DGEMMs per instance + division) timed alone on the same stream"}
 
+    phase("the same workload with the other operand precisions")
     # ---- the same workload with the other operand precisions (solves/s, inner iterations) --
     precisions = {}
     if not a.no_precision_matrix and a.precision != "fp64":
@@ -574,6 +589,7 @@ def run_mofem(a):
             h2.close()
             del F2, U2
 
+    phase("uniform batches of the precision form")
     # ---- uniform batches of the precision form: instance i with gamma ~ U[0,10] and its own
     # top profile 1 + a sin(2 pi b x), B in 1, 4, 16, 64 (one handle per B, one warm-up solve,
     # median of two timed solves) ------------------------------------------------------------
@@ -593,6 +609,7 @@ def run_mofem(a):
             del F2, U2
             torch.cuda.empty_cache()
 
+    phase("CPU baseline")
     # ---- CPU baseline: the oracle on a bounded sample ----------------------------------
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -675,11 +692,15 @@ def run_mofem(a):
         "cpu_baseline": cpu,
     }
     if not a.no_heat and rank == 0:
+        phase("differentiation workload")
         line["heat_adjoint"] = measure_heat()
     if not a.no_dib and rank == 0:
+        phase("reaction-diffusion workload")
         line["reaction_diffusion"] = measure_dib()
     if not a.no_batching and rank == 0:
+        phase("heterogeneous batch")
         line["heterogeneous_batch"] = measure_batching(not a.batching_small)
+    phase("done")
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
