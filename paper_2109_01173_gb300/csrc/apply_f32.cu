@@ -115,7 +115,8 @@ constexpr int APPLY_SEG_DIV_MAX = 2;
 template <int K, int NT>
 static int segs_k(int q, int strips, int batch) {
     if constexpr (kApplyPush) {
-        return apply3_segments(q, strips, batch, apply4_ctas_wanted_t<K, NT>() * APPLY_SEG_DIV_MAX, K, 1);
+        constexpr int NS = push_streams(K, NT);
+        return apply3_segments(q, strips, batch, apply4_ctas_wanted_t<K, NT, NS>() * APPLY_SEG_DIV_MAX, K, NS);
     } else {
         constexpr int NS = packed_streams(K, NT);
         return apply3_segments(q, strips, batch, apply3_ctas_wanted_t<K, NT, NS>() * APPLY_SEG_DIV_MAX, K, NS);

@@ -35,7 +35,7 @@
 
 namespace mofem_apply_impl {
 
-template <int K, int NT>
+template <int K, int NT, int NS = 1>
 struct Geo4 {
     static constexpr int P = 2 * K + 1;
     static constexpr int NTH = 64;                       // threads = column pairs per CTA
@@ -47,8 +47,10 @@ struct Geo4 {
     static constexpr int ZCH = CR * WCT;                 // floats per chunk of Z (and of Q_prev)
     static constexpr int SCH = CR * SR;                  // floats per chunk of coefficient rows
     static constexpr uint32_t CHUNK_BYTES = 2u * ZCH * 4u + (uint32_t)SCH * 4u;
-    static constexpr size_t SMEM = (size_t)D * CHUNK_BYTES + 128;
-    static constexpr int MINB = NT * P <= 25 ? 8 : 5;   // 128 registers (16 warps per SM) where they suffice
+    static constexpr size_t SMEM = (size_t)NS * D * CHUNK_BYTES + 128;   // one ring per row stream
+    // one stream: 128 registers (16 warps per SM) where they suffice; two: the shared memory of
+    // five CTAs per SM
+    static constexpr int MINB = NS == 1 ? (NT * P <= 25 ? 8 : 5) : 5;
     static_assert((RING & (RING - 1)) == 0, "ring rows must be a power of two");
     static_assert((ZCH * 4) % 128 == 0 && (SCH * 4) % 128 == 0, "TMA destinations stay 128-byte aligned");
     // one block of P input rows reads rows back to K before its first: those rows and the
@@ -60,25 +62,27 @@ struct Geo4 {
 template <int P>
 __device__ __forceinline__ constexpr int pslot(int x) { return ((x % P) + P) % P; }
 
-// One CTA: a strip of 128 columns (64 column pairs, one per thread) of one instance and a
-// segment of `srows` output rows a_lo .. a_lo + L - 1.  Input rows a_lo - K .. a_lo + L + K - 1
-// are processed in blocks of P (one turn of the accumulator ring, straight-line code).
-template <int K, int NT>
-__global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
+// One CTA: a strip of 128 columns (64 column pairs, one per thread) of one instance and NS
+// row streams of `srows` output rows each (stream st: rows a_lo[st] .. a_lo[st] + L[st] - 1,
+// input rows from a_lo[st] - K), advanced in lockstep with a chunk ring each: independent
+// instruction streams for the scheduler that share the T coefficients.  Input rows are
+// processed in blocks of P (one turn of the accumulator rings, straight-line code).
+template <int K, int NT, int NS>
+__global__ void __launch_bounds__(Geo4<K, NT, NS>::NTH, Geo4<K, NT, NS>::MINB)
     k_apply_pcg4(const __grid_constant__ CUtensorMap mZ, const __grid_constant__ CUtensorMap mQ,
                  const __grid_constant__ CUtensorMap mS, ApplyPcgArgs a, int srows) {
-    using G = Geo4<K, NT>;
+    using G = Geo4<K, NT, NS>;
     constexpr int P = G::P, SR = G::SR, KE = G::KE, CR = G::CR, D = G::D, RING = G::RING, NTH = G::NTH;
     constexpr unsigned DM = DiffMask<NT>::value;
     static_assert(DM & 1u, "term 0 is a difference term (exact mass split)");
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sbase =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-    // rings: Z [RING][WCT], Q_prev [RING][WCT], coefficient rows [RING][SR]
-    float* Zs = reinterpret_cast<float*>(sbase);
-    float* Qs = Zs + RING * WCT;
-    float* Ss = Qs + RING * WCT;
-    __shared__ __align__(8) unsigned long long bar[D];
+    // rings of stream st: Z [RING][WCT], Q_prev [RING][WCT], coefficient rows [RING][SR]
+    auto Zs = [&](int st) { return reinterpret_cast<float*>(sbase + (size_t)st * D * G::CHUNK_BYTES); };
+    auto Qs = [&](int st) { return Zs(st) + RING * WCT; };
+    auto Ss = [&](int st) { return Qs(st) + RING * WCT; };
+    __shared__ __align__(8) unsigned long long bar[NS][D];
     __shared__ double red[NTH / 32];
     __shared__ float beta_s;
     __shared__ int fail_s, last_s;
@@ -86,13 +90,19 @@ __global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
     PcgScalars* sc = a.sc + inst;
     if (a.use_sc && !sc->active) return;
     const int b0 = blockIdx.x * TB;
-    const int a_lo = blockIdx.y * srows;
-    const int L = max(0, min(a.q, a_lo + srows) - a_lo);   // output rows of this CTA
-    const int nblk = (L + 2 * K + P - 1) / P;                // blocks of input rows
-    const int nch = (nblk * P + CR - 1) / CR;                // chunks: input rows a_lo - K ...
+    int a_lo[NS], L[NS], Lmax = 0;
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+        a_lo[st] = (blockIdx.y * NS + st) * srows;
+        L[st] = max(0, min(a.q, a_lo[st] + srows) - a_lo[st]);   // output rows of stream st
+        Lmax = max(Lmax, L[st]);
+    }
+    const int nblk = (Lmax + 2 * K + P - 1) / P;                 // blocks of input rows
+    const int nch = (nblk * P + CR - 1) / CR;                    // chunks per stream: input rows a_lo - K ...
     if (tid == 0) {
-        for (int i = 0; i < D; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[i])) : "memory");
+        for (int st = 0; st < NS; ++st)
+            for (int i = 0; i < D; ++i)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[st][i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fail_s = 0;
         beta_s = (a.use_sc && sc->iters > 0) ? (float)sc->beta : 0.f;
@@ -100,29 +110,30 @@ __global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
     __syncthreads();
     // chunk c -> ring slot c % D: input rows a_lo - K + c CR .. of Z, Q_prev and the
     // coefficient table (rows outside [0, q) read as zeros)
-    auto issue = [&](int c) {
+    auto issue = [&](int st, int c) {
         const int slot = c % D;
-        const uint32_t bb = smem_u32(&bar[slot]);
+        const uint32_t bb = smem_u32(&bar[st][slot]);
         const uint64_t pz = reinterpret_cast<uint64_t>(&mZ), pq = reinterpret_cast<uint64_t>(&mQ),
                        ps = reinterpret_cast<uint64_t>(&mS);
-        const int x0 = b0 - XPAD, y0 = a_lo - K + c * CR;
+        const int x0 = b0 - XPAD, y0 = a_lo[st] - K + c * CR;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(G::CHUNK_BYTES)
                      : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(Ss + slot * G::SCH)), "l"(ps), "r"(bb), "r"(0), "r"(y0), "r"(inst)
+            ::"r"(smem_u32(Ss(st) + slot * G::SCH)), "l"(ps), "r"(bb), "r"(0), "r"(y0), "r"(inst)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(Zs + slot * G::ZCH)), "l"(pz), "r"(bb), "r"(x0), "r"(y0), "r"(inst)
+            ::"r"(smem_u32(Zs(st) + slot * G::ZCH)), "l"(pz), "r"(bb), "r"(x0), "r"(y0), "r"(inst)
             : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-            ::"r"(smem_u32(Qs + slot * G::ZCH)), "l"(pq), "r"(bb), "r"(x0), "r"(y0), "r"(inst)
+            ::"r"(smem_u32(Qs(st) + slot * G::ZCH)), "l"(pq), "r"(bb), "r"(x0), "r"(y0), "r"(inst)
             : "memory");
     };
     if (tid == 0)
-        for (int c = 0; c < D && c < nch; ++c) issue(c);
+        for (int c = 0; c < D && c < nch; ++c)
+            for (int st = 0; st < NS; ++st) issue(st, c);
     const int cp = tid;
     const int b = b0 + 2 * cp;
     const float* Tt = reinterpret_cast<const float*>(a.T);
@@ -150,31 +161,38 @@ __global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
     const bool col_ok = b < a.ld;   // pad columns [q, ld) receive zeros
     bool failed = false;
     int waited = 0, released = 0;
-    auto wait_upto = [&](int need) {   // chunks 0 .. need-1 resident
+    auto wait_upto = [&](int need) {   // chunks 0 .. need-1 resident in every stream
         while (waited < need) {
-            if (!failed) failed = !mbar_wait_bounded(smem_u32(&bar[waited % D]), (uint32_t)((waited / D) & 1));
+#pragma unroll
+            for (int st = 0; st < NS; ++st)
+                if (!failed)
+                    failed = !mbar_wait_bounded(smem_u32(&bar[st][waited % D]), (uint32_t)((waited / D) & 1));
             ++waited;
         }
     };
     const float2 zero2 = make_float2(0.f, 0.f);
-    float2 acc0[P], accR[P], xr[P];   // term-0 and other-term accumulators, new-direction centres
-    float2 wprev[NT];                 // previous input row's t-pass values (difference terms)
-    float2 xprev = zero2;
+    float2 acc0[NS][P], accR[NS][P], xr[NS][P];   // term-0 and other-term accumulators, new-direction centres
+    float2 wprev[NS][NT];                         // previous input row's t-pass values (difference terms)
+    float2 xprev[NS];
 #pragma unroll
-    for (int s = 0; s < P; ++s) {
-        acc0[s] = zero2;
-        accR[s] = zero2;
-        xr[s] = zero2;
+    for (int st = 0; st < NS; ++st) {
+        xprev[st] = zero2;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            acc0[st][s] = zero2;
+            accR[st][s] = zero2;
+            xr[st][s] = zero2;
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) wprev[st][t] = zero2;
     }
-#pragma unroll
-    for (int t = 0; t < NT; ++t) wprev[t] = zero2;
     float2 dacc = zero2, zacc = zero2;   // <X, L(X)>, <Z, L(X)>
     // input index i (input row a_lo - K + i, staged at ring row i mod RING; u = i mod P):
     // t-pass, push into output rows i - 2K .. i (CTA-local), then output row i - 2K is done
-    auto step = [&](int i, const int u) {
+    auto step = [&](const int st, int i, const int u) {
         const int rr = i & (RING - 1);
-        const float2* z2 = reinterpret_cast<const float2*>(Zs + rr * WCT + XPAD + 2 * cp - KE);
-        const float2* q2 = reinterpret_cast<const float2*>(Qs + rr * WCT + XPAD + 2 * cp - KE);
+        const float2* z2 = reinterpret_cast<const float2*>(Zs(st) + rr * WCT + XPAD + 2 * cp - KE);
+        const float2* q2 = reinterpret_cast<const float2*>(Qs(st) + rr * WCT + XPAD + 2 * cp - KE);
         float xs[2 * KE + 2];
 #pragma unroll
         for (int m = 0; m <= KE; ++m) {
@@ -185,8 +203,8 @@ __global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
         const float2 xc = make_float2(xs[KE], xs[KE + 1]);
         {
             const int orow = i - K;   // the new direction's row of this centre
-            if (orow >= 0 && orow < L && col_ok)
-                *reinterpret_cast<float2*>(Qn + (size_t)(a_lo + orow) * a.ld + b) = xc;
+            if (orow >= 0 && orow < L[st] && col_ok)
+                *reinterpret_cast<float2*>(Qn + (size_t)(a_lo[st] + orow) * a.ld + b) = xc;
         }
         float2 d[P];
 #pragma unroll
@@ -209,63 +227,63 @@ __global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
             w[t] = v;
         }
         // coefficients of this input row: term t at t P .. t P + 2K
-        const float4* crow4 = reinterpret_cast<const float4*>(Ss + rr * SR);
+        const float4* crow4 = reinterpret_cast<const float4*>(Ss(st) + rr * SR);
         auto cf = [&](int e) -> float2 {
             const float4 v = crow4[e >> 2];
             const float s = (e & 3) == 0 ? v.x : (e & 3) == 1 ? v.y : (e & 3) == 2 ? v.z : v.w;
             return make_float2(s, s);
         };
         {   // term 0, both parts of the split
-            const float2 dx = f2sub(xc, xprev), dw = f2sub(w[0], wprev[0]);
+            const float2 dx = f2sub(xc, xprev[st]), dw = f2sub(w[0], wprev[st][0]);
 #pragma unroll
             for (int p = 0; p < 2 * K; ++p) {
                 const float2 c = cf(p);
                 const int s = pslot<P>(u - 2 * K + p);
-                acc0[s] = f2fma(c, dx, acc0[s]);
-                acc0[s] = f2fma(c, dw, acc0[s]);
+                acc0[st][s] = f2fma(c, dx, acc0[st][s]);
+                acc0[st][s] = f2fma(c, dw, acc0[st][s]);
             }
             const float2 c = cf(2 * K);
             const int s = pslot<P>(u - K);
-            acc0[s] = f2fma(c, xc, acc0[s]);
-            acc0[s] = f2fma(c, w[0], acc0[s]);
+            acc0[st][s] = f2fma(c, xc, acc0[st][s]);
+            acc0[st][s] = f2fma(c, w[0], acc0[st][s]);
         }
 #pragma unroll
         for (int t = 1; t < NT; ++t) {
             if ((DM >> t) & 1u) {
-                const float2 dt = f2sub(w[t], wprev[t]);
+                const float2 dt = f2sub(w[t], wprev[st][t]);
 #pragma unroll
                 for (int p = 0; p < 2 * K; ++p) {
                     const int s = pslot<P>(u - 2 * K + p);
-                    accR[s] = f2fma(cf(t * P + p), dt, accR[s]);
+                    accR[st][s] = f2fma(cf(t * P + p), dt, accR[st][s]);
                 }
                 const int s = pslot<P>(u - K);
-                accR[s] = f2fma(cf(t * P + 2 * K), w[t], accR[s]);
+                accR[st][s] = f2fma(cf(t * P + 2 * K), w[t], accR[st][s]);
             } else {
 #pragma unroll
                 for (int p = 0; p <= 2 * K; ++p) {
                     const int s = pslot<P>(u - 2 * K + p);
-                    accR[s] = f2fma(cf(t * P + p), w[t], accR[s]);
+                    accR[st][s] = f2fma(cf(t * P + p), w[t], accR[st][s]);
                 }
             }
         }
-        xprev = xc;
+        xprev[st] = xc;
 #pragma unroll
         for (int t = 0; t < NT; ++t)
-            if ((DM >> t) & 1u) wprev[t] = w[t];
-        xr[pslot<P>(u - K)] = xc;
+            if ((DM >> t) & 1u) wprev[st][t] = w[t];
+        xr[st][pslot<P>(u - K)] = xc;
         {   // output row i - 2K: every input row that reaches it is in
             const int s = pslot<P>(u - 2 * K);
-            const float2 y = f2fma(d0, acc0[s], accR[s]);
+            const float2 y = f2fma(d0, acc0[st][s], accR[st][s]);
             const int jo = i - 2 * K;
-            if (col_ok && jo >= 0 && jo < L) {
-                *reinterpret_cast<float2*>(LQ + (size_t)(a_lo + jo) * a.ld + b) = y;
-                dacc = f2fma(xr[s], y, dacc);
+            if (col_ok && jo >= 0 && jo < L[st]) {
+                *reinterpret_cast<float2*>(LQ + (size_t)(a_lo[st] + jo) * a.ld + b) = y;
+                dacc = f2fma(xr[st][s], y, dacc);
                 const float2 zc =
-                    *reinterpret_cast<const float2*>(Zs + ((i - K) & (RING - 1)) * WCT + XPAD + 2 * cp);
+                    *reinterpret_cast<const float2*>(Zs(st) + ((i - K) & (RING - 1)) * WCT + XPAD + 2 * cp);
                 zacc = f2fma(zc, y, zacc);
             }
-            acc0[s] = zero2;
-            accR[s] = zero2;
+            acc0[st][s] = zero2;
+            accR[st][s] = zero2;
         }
     };
 #pragma unroll 1
@@ -274,14 +292,17 @@ __global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
         const int iend = i0 + P;
         wait_upto(min(nch, (iend - 1) / CR + 1));
 #pragma unroll
-        for (int u = 0; u < P; ++u) step(i0 + u, u);
+        for (int u = 0; u < P; ++u)
+#pragma unroll
+            for (int st = 0; st < NS; ++st) step(st, i0 + u, u);
         // chunks below the next block's oldest row (iend - K) are done: refill
         const int can = min(nch, (iend - K) / CR);
         if (can > released) {
             __syncthreads();   // every thread is past the rows of those slots
             if (tid == 0)
                 for (int c = released; c < can; ++c)
-                    if (c + D < nch) issue(c + D);
+                    if (c + D < nch)
+                        for (int st = 0; st < NS; ++st) issue(st, c + D);
             released = can;
         }
     }
@@ -321,9 +342,9 @@ __global__ void __launch_bounds__(Geo4<K, NT>::NTH, Geo4<K, NT>::MINB)
 }
 
 // Resident CTAs of the push-form apply on the current device (one wave).
-template <int K, int NT>
+template <int K, int NT, int NS>
 int apply4_ctas_wanted_t() {
-    using G = Geo4<K, NT>;
+    using G = Geo4<K, NT, NS>;
     static std::atomic<int> cache[MOFEM_MAX_DEV];
     const int slot = dev_slot();
     int n = cache[slot].load(std::memory_order_relaxed);
@@ -332,8 +353,8 @@ int apply4_ctas_wanted_t() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
-        smem_attr_once(k_apply_pcg4<K, NT>, (int)G::SMEM, attr_done);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_pcg4<K, NT>, G::NTH, G::SMEM) !=
+        smem_attr_once(k_apply_pcg4<K, NT, NS>, (int)G::SMEM, attr_done);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_apply_pcg4<K, NT, NS>, G::NTH, G::SMEM) !=
                 cudaSuccess ||
             per < 1)
             per = 1;
@@ -345,22 +366,26 @@ int apply4_ctas_wanted_t() {
 
 // Output rows per segment: the segment and its 2K halo rows fill whole blocks of P input
 // rows (only the last segment is ragged).
-inline int apply4_rows(int q, int segs, int K) {
+inline int apply4_rows(int q, int segs, int K, int ns) {
     const int P = 2 * K + 1;
-    const int per = (q + segs - 1) / segs;
+    const int per = (q + segs * ns - 1) / (segs * ns);
     return (per + 2 * K + P - 1) / P * P - 2 * K;
 }
+
+// Row streams per thread of the push-form apply.
+__host__ __device__ constexpr int push_streams(int, int) { return 1; }
 
 template <int K, int NT>
 mofem_status launch_pcg4_t(const CUtensorMap& mZ, const CUtensorMap& mQ, const CUtensorMap& mS,
                            const ApplyPcgArgs& a, int batch, cudaStream_t st) {
-    using G = Geo4<K, NT>;
-    auto kern = k_apply_pcg4<K, NT>;
+    constexpr int NS = push_streams(K, NT);
+    using G = Geo4<K, NT, NS>;
+    auto kern = k_apply_pcg4<K, NT, NS>;
     static std::atomic<bool> attr_done[MOFEM_MAX_DEV];
     MOFEM_CUDA_TRY(smem_attr_once(kern, (int)G::SMEM, attr_done));
     const int strips = (a.q + TB - 1) / TB;
-    const int segs = apply3_segments(a.q, strips, batch, apply4_ctas_wanted_t<K, NT>() * max(1, a.seg_div), K, 1);
-    const int srows = apply4_rows(a.q, segs, K);
+    const int segs = apply3_segments(a.q, strips, batch, apply4_ctas_wanted_t<K, NT, NS>() * max(1, a.seg_div), K, NS);
+    const int srows = apply4_rows(a.q, segs, K, NS);
     dim3 grid(strips, segs, batch);
     kern<<<grid, G::NTH, G::SMEM, st>>>(mZ, mQ, mS, a, srows);
     MOFEM_CUDA_TRY(cudaGetLastError());
