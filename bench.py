@@ -473,17 +473,39 @@ def run_mofem(a):
 
     phase("end to end through the C ABI with host buffers")
     # ---- end to end through the C ABI with host buffers ----------------------------
+    # every step copies its F in from pinned host memory and its U out; the copies run on a
+    # second stream with double-buffered device arrays, overlapping the neighbouring steps' solves
     F_host = F.cpu().pin_memory()
     U_host = torch.empty((B, q, q), dtype=torch.float64).pin_memory()
-    F_dev = torch.empty_like(F)
-    U_dev = torch.empty_like(U)
+    F_dev = [torch.empty_like(F) for _ in range(2)]
+    U_dev = [torch.empty_like(U) for _ in range(2)]
+    cs = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
-    for _ in range(a.steps):
-        F_dev.copy_(F_host, non_blocking=True)
-        step(U_dev, F_dev)
-        U_host.copy_(U_dev, non_blocking=True)
+    cs.wait_stream(stream)
+    with torch.cuda.stream(cs):
+        F_dev[0].copy_(F_host, non_blocking=True)
+        ev_in[0].record(cs)
+    for s_ in range(a.steps):
+        j = s_ % 2
+        if s_ + 1 < a.steps:   # the next step's input, into the other buffer (its last reader is done)
+            with torch.cuda.stream(cs):
+                F_dev[1 - j].copy_(F_host, non_blocking=True)
+                ev_in[1 - j].record(cs)
+        stream.wait_event(ev_in[j])
+        if s_ >= 2:
+            stream.wait_event(ev_out[j])   # U_dev[j]'s previous result has been read out
+        step(U_dev[j], F_dev[j])
+        ev_done[j].record(stream)
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_done[j])
+            U_host.copy_(U_dev[j], non_blocking=True)
+            ev_out[j].record(cs)
+    stream.wait_stream(cs)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_elapsed = e0.elapsed_time(e1) / 1e3
